@@ -1,0 +1,325 @@
+"""Benchmark of the two-phase Darcy LB solver (one JSON line on stdout).
+
+Workload (default): the quarter five-spot of 1024 x 1024 nodes (ln K a seeded Gaussian
+random field, sigma 1, correlation length 16 cells; no-flux walls; injector and producer
+of rate 1e-3 at opposite corners; S0 = 0.2; phi = 0.2, beta = 0.4, mu_w = 1, mu_n = 2,
+D_s = 0.01, tau_p = 1, tau_s = 0.8), each physical step sub-iterating the pressure to a
+relative increment of 1e-8.  A step = S refresh + pressure sub-iteration + saturation
+update.  The t = 0 initialisation (a cold pressure solve) is set-up, outside the timing.
+
+Metric: MLUPS = nodes x (pressure sweeps + 1 saturation update) / time, summed over the
+timed steps (and over ranks).  L2 is flushed before every timed step; each step is timed
+with CUDA events on the solver's stream.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload five_spot_1024|five_spot_4096|manufactured_64]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+BYTES_PER_SWEEP_NODE = 68      # 8 pops x (4 B read + 4 B write) + 4 B of 1/tau_f
+WORKLOADS = {
+    "five_spot_1024": dict(kind="five_spot", n=1024),
+    "five_spot_4096": dict(kind="five_spot", n=4096),
+    "manufactured_64": dict(kind="manufactured", n=64),
+}
+# DRAM bytes per pressure-sweep launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum),
+# keyed by workload; None until captured for the current kernel.
+NCU_TRAFFIC_PER_SWEEP = {"five_spot_1024": None, "five_spot_4096": None, "manufactured_64": None}
+
+
+def make_problem(name: str, rank: int = 0):
+    w = WORKLOADS[name]
+    if w["kind"] == "five_spot":
+        return W.quarter_five_spot(w["n"], seed=2 + rank)
+    return W.manufactured_periodic(w["n"])
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on the host cores, bounded sample of the same workload
+# ---------------------------------------------------------------------------------------
+def cpu_baseline(name: str, budget_s: float = 12.0):
+    import oracle as O
+    prob = make_problem(name)
+    orc = O.Oracle(prob, tol=1e-8, init_replay=0)
+    nodes = prob.nx * prob.ny
+    # calibrate: one step of 5 sweeps
+    t0 = time.perf_counter()
+    orc.step(1, replay=[5])
+    t1 = time.perf_counter()
+    per_update = (t1 - t0) / (nodes * 6)
+    sweeps = max(5, int(budget_s / (per_update * nodes)) - 1)
+    t0 = time.perf_counter()
+    orc.step(1, replay=[sweeps])
+    dt = time.perf_counter() - t0
+    orc.close()
+    updates = nodes * (sweeps + 1)
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": updates / dt / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"{name}: 1 physical step with {sweeps} pressure sweeps + 1 saturation "
+                      f"update on the {prob.nx}x{prob.ny} lattice, {dt:.1f} s",
+            "seconds": dt}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    res = []
+    for _ in range(args.steps):
+        res.append(cpu_baseline(args.workload, budget_s=max(3.0, 60.0 / max(1, args.steps))))
+    value = statistics.median(r["value"] for r in res)
+    line = {"metric": "MLUPS", "value": value, "unit": "MLUPS", "impl": "reference",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "tol": 1e-8},
+            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": res[0]["cores"],
+                             "kind": "oracle", "sample": res[0]["sample"]},
+            "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import paper_1808_07554_gb300 as pkg
+    from paper_1808_07554_gb300 import build
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0 or not os.path.exists(build.LIB):
+        build.build()
+    if dist is not None:
+        dist.barrier()
+    pkg.load_library()
+
+    prob = make_problem(args.workload, rank)
+    nodes = prob.nx * prob.ny
+    stream = torch.cuda.current_stream()
+    t_setup = time.perf_counter()
+    solver = pkg.Solver.from_problem(prob, tol=1e-8, check_every=args.check_every,
+                                     max_sub_iters=args.max_sub_iters)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t_setup
+    init_sweeps = solver.init_stats.sub_iters
+    solver.set_timing(True)
+
+    # problems with time-dependent sources get them uploaded every step (host buffers)
+    def upload(n):
+        if prob.sources_at is not None:
+            solver.set_sources(*prob.sources_at(n * prob.dt))
+
+    step_no = 0
+    for _ in range(args.warmup):
+        step_no += 1
+        upload(step_no)
+        solver.step(1)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    launches0, sweeps0 = solver.counters()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    wall0 = time.perf_counter()
+    step_ms, sweep_ms, ksub, statuses = [], [], [], []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        step_no += 1
+        upload(step_no)
+        ev0.record(stream)
+        st, stats = solver.step(1)
+        ev1.record(stream)
+        ev1.synchronize()
+        step_ms.append(ev0.elapsed_time(ev1))
+        sweep_ms.append(stats[0].sweep_ms)
+        ksub.append(stats[0].sub_iters)
+        statuses.append(st)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if dist is not None:
+        dist.barrier()
+    clk = clocks.stop()
+    launches1, sweeps1 = solver.counters()
+    gpu_launches = launches1 - launches0
+
+    # end to end: the public API with host buffers (per step: the step's source upload when
+    # the problem has one, the step, and the P and S fields read back to host memory)
+    e2e_steps = max(1, min(args.steps, 5))
+    h2d = 0 if prob.sources_at is None else 2 * 8 * nodes
+    d2h = 2 * 4 * nodes
+    torch.cuda.synchronize()
+    e2e_updates = 0
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        step_no += 1
+        upload(step_no)
+        st, stats = solver.step(1)
+        solver.fields()
+        e2e_updates += nodes * (stats[0].sub_iters + 1)
+    e2e_s = time.perf_counter() - t0
+    solver.close()
+
+    total_ms = float(np.sum(step_ms))
+    updates = nodes * (int(np.sum(ksub)) + args.steps)
+    local_val = np.array([updates, total_ms / 1e3, e2e_updates, e2e_s], dtype=np.float64)
+    if dist is not None:
+        t = torch.tensor(local_val, device="cuda")
+        sums = t.clone()
+        dist.all_reduce(sums, op=dist.ReduceOp.SUM)
+        maxs = t.clone()
+        dist.all_reduce(maxs, op=dist.ReduceOp.MAX)
+        updates_all, time_max = float(sums[0]), float(maxs[1])
+        e2e_all, e2e_max = float(sums[2]), float(maxs[3])
+    else:
+        updates_all, time_max, e2e_all, e2e_max = updates, total_ms / 1e3, e2e_updates, e2e_s
+    if rank != 0:
+        return 0
+
+    peak, peak_kind = peaks()
+    sweeps_timed = int(np.sum(ksub))
+    avg_sweep_s = float(np.sum(sweep_ms)) / 1e3 / max(1, sweeps_timed)
+    achieved = BYTES_PER_SWEEP_NODE * nodes / avg_sweep_s / 1e9
+    traffic = NCU_TRAFFIC_PER_SWEEP.get(args.workload)
+    line = {
+        "metric": "MLUPS", "value": updates_all / time_max / 1e6, "unit": "MLUPS",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "nx": prob.nx, "ny": prob.ny, "tol": 1e-8,
+                   "check_every": args.check_every, "l2": "flushed before every timed step",
+                   "sub_iters_per_step": ksub, "statuses": statuses,
+                   "init_sweeps": init_sweeps, "setup_s": round(setup_s, 2),
+                   "wall_s": round(wall, 3),
+                   "parallelism": f"{world} independent realisations (seed 2 + rank)"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "pressure sweep (fused stream + collide, Eq. 3-1)",
+                     "bytes_per_launch": BYTES_PER_SWEEP_NODE * nodes,
+                     "avg_launch_us": avg_sweep_s * 1e6, "peak_kind": peak_kind},
+        "e2e": {"value": e2e_all / e2e_max / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(gpu_launches),
+        "clocks": clk,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = {k: v for k, v in cpu_baseline(args.workload).items()
+                                if k != "seconds"}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="five_spot_1024")
+    ap.add_argument("--check-every", type=int, default=10)
+    ap.add_argument("--max-sub-iters", type=int, default=4_000_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

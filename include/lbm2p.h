@@ -1,0 +1,202 @@
+/*
+ * lbm2p — GPU solver for the double-distribution lattice Boltzmann model of two-phase
+ * Darcy flow of Chai, Liang, Du and Shi (arXiv 1808.07554).  C ABI.
+ *
+ * The model (Sec. 2, Eqs. 2-15 and 2-18) couples a Poisson equation for the global
+ * pressure P and a convection-diffusion equation for the wetting saturation S:
+ *     div(D_p grad P) + F_p = 0,   D_p = K lambda_t(S)
+ *     phi dS/dt = div(D_s grad S) + F_s + div(lambda_w K grad P)
+ * P is carried by a D2Q9 distribution f relaxed in pseudo time until steady (Eq. 3-1,
+ * Eq. 3-3); grad P and the Darcy velocity u = -K lambda_t grad P are read locally from
+ * f's first moment (Eq. 3-10); S is carried by a second D2Q9 distribution g (Eq. 3-2,
+ * Eq. 3-4, Eq. 3-8).  One physical step (Sec. 3):
+ *   1. stream g, S^n (Eq. 3-9b), tau_f(x) from D_p(S^n, K) (Eq. 3-11a, Remark IV);
+ *   2. sweep f (stream + collide, Eq. 3-1) until the pressure increment satisfies the
+ *      stopping rule below, or replay a given number of sweeps;
+ *   3. stream f once more for grad P (Eq. 3-10a); stream g, collide it with both sources
+ *      (Eq. 3-2) and keep the post-collision populations.
+ *
+ * Units and layout.  All host arrays are row-major [ny][nx] (node (i, j) at index
+ * j*nx + i), cell centred: node (i, j) sits at ((i + 1/2) dx, (j + 1/2) dx) and walls
+ * lie half-way between a boundary node and its missing neighbour.  Host inputs are FP64
+ * and are copied (the caller keeps ownership); the library computes in FP32 on the GPU
+ * and accumulates the residual in FP64.  Device outputs are FP32.
+ *
+ * Memory.  The handle owns all device memory.  It is obtained through params.alloc /
+ * params.release when given (for instance a framework's caching allocator), otherwise
+ * with cudaMalloc / cudaFree.  All work is enqueued on params.stream (a cudaStream_t;
+ * NULL is the legacy default stream); calls that return host data synchronise that
+ * stream.  A handle must be used by one host thread at a time.
+ *
+ * Errors.  Every call returns an lbm2p_status; lbm2p_last_error(handle) (or
+ * lbm2p_last_error(NULL) after a failed create) gives a one-line description.
+ * LBM2P_ENOTCONVERGED still advances the state; LBM2P_ENONFINITE leaves the state as
+ * the failing sweep produced it (the caller may restore a checkpoint).
+ */
+#ifndef LBM2P_H
+#define LBM2P_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM2P_ABI_VERSION 1
+/* Sparse wells passed to the sweep kernels as launch arguments (more wells: error). */
+#define LBM2P_MAX_WELLS 16
+
+typedef struct lbm2p lbm2p;
+
+typedef enum {
+    LBM2P_OK = 0,
+    LBM2P_EINVAL = 1,          /* bad argument; nothing was changed */
+    LBM2P_ENOMEM = 2,          /* device or host allocation failed */
+    LBM2P_ECUDA = 3,           /* a CUDA call failed; the handle should be destroyed */
+    LBM2P_ENOTCONVERGED = 4,   /* max_sub_iters reached before the residual met tol */
+    LBM2P_ENONFINITE = 5,      /* the pressure residual became NaN (e.g. NaN sources) */
+    LBM2P_ENOTIMPL = 6         /* requested option is not available in this build */
+} lbm2p_status;
+
+/* Wall kinds of Sec. 4: bounce-back for no-flux, anti-bounce-back for Dirichlet. */
+typedef enum { LBM2P_BC_PERIODIC = 0, LBM2P_BC_NOFLUX = 1, LBM2P_BC_DIRICHLET = 2 } lbm2p_bc_kind;
+typedef enum { LBM2P_XMIN = 0, LBM2P_XMAX = 1, LBM2P_YMIN = 2, LBM2P_YMAX = 3 } lbm2p_side;
+
+/* Mobility laws lambda_w(S), lambda_t(S):
+ *   QUADRATIC: k_rw = S^2, k_rn = (1-S)^2, lambda_a = k_ra / mu_a (Eq. 2-9, Sec. 4.3);
+ *   DECOUPLED: lambda_t = lambda_w = 1/mu_w, independent of S (Sec. 4.1);
+ *   RATIONAL:  lambda_t = 1/(0.5 - 0.2 S), lambda_w = S lambda_t (Eq. 4-4, K = 1). */
+typedef enum { LBM2P_MOB_QUADRATIC = 0, LBM2P_MOB_DECOUPLED = 1, LBM2P_MOB_RATIONAL = 2 } lbm2p_mobility;
+
+/* Pressure pseudo-time scale s (Eq. 3-1 is iterated in a pseudo time of its own, Sec. 3):
+ * tau_f(x) = 1/2 + 3 s D_p(x) (Eq. 3-11a), and the source enters as s dx^2 F_p.
+ *   REFERENCE:   s = (tau_p - 1/2) / (3 D_ref); D_ref = params.D_ref when > 0, else the
+ *                geometric mean of D_p(K, S0) over the grid at t = 0 (fixed for the run);
+ *   PHYSICAL_DT: s = dt / dx^2 (pseudo step equal to the physical step, as in Sec. 4). */
+typedef enum { LBM2P_TAU_REFERENCE = 0, LBM2P_TAU_PHYSICAL_DT = 1 } lbm2p_tau_mode;
+
+/* Population storage.  FP16_DEV (FP16 deviations from equilibrium) is reserved. */
+typedef enum { LBM2P_STORE_FP32 = 0, LBM2P_STORE_FP16_DEV = 1 } lbm2p_storage;
+
+/* A point well at node (i, j) with total rate q >= 0 (per unit depth): the node's cell
+ * receives F_p = +q/dx^2 and F_s = +q/dx^2 (injector) or F_p = -q/dx^2 and
+ * F_s = -f_w(S*) q/dx^2 (producer), f_w = lambda_w/lambda_t, S* = sum_i g_i / phi. */
+typedef struct {
+    int i, j;
+    double q;
+    int is_producer;
+} lbm2p_well;
+
+typedef struct {
+    int nx, ny;                 /* lattice size, >= 1 each (Dirichlet sides need >= 3 nodes) */
+    double dx, dt;              /* lattice spacing and physical time step */
+    double phi, beta;           /* porosity; Eq. 3-4 parameter, phi/2 <= beta <= 2 phi */
+    int mobility;               /* lbm2p_mobility */
+    double mu_w, mu_n;          /* viscosities of the mobility law */
+    double D_s;                 /* saturation diffusivity (constant): Eq. 3-11b gives tau_g */
+    int tau_mode;               /* lbm2p_tau_mode */
+    double tau_p, D_ref;        /* REFERENCE mode: typical tau_f and its diffusivity */
+    double tol;                 /* pressure stopping tolerance on r (see lbm2p_step) */
+    int max_sub_iters;          /* cap on sweeps per pressure solve */
+    int check_every;            /* sweeps between residual checks, >= 1 */
+    int bc[4];                  /* lbm2p_bc_kind per side (XMIN, XMAX, YMIN, YMAX); a
+                                   periodic side must be paired with its opposite */
+    int storage;                /* lbm2p_storage */
+    void *stream;               /* cudaStream_t the work is enqueued on */
+    void *(*alloc)(size_t bytes, void *ctx);            /* optional device allocator */
+    void (*release)(void *ptr, size_t bytes, void *ctx); /* its matching free */
+    void *alloc_ctx;
+} lbm2p_params;
+
+typedef struct {
+    const double *K;            /* [ny][nx] absolute permeability, required */
+    const double *S0;           /* [ny][nx] initial saturation, required */
+    const double *P0;           /* [ny][nx] initial pressure guess, or NULL (zero) */
+    const double *Fp, *Fs;      /* [ny][nx] dense sources at t = 0, or NULL (zero) */
+    const lbm2p_well *wells;    /* n_wells entries, or NULL */
+    int n_wells;                /* 0 .. LBM2P_MAX_WELLS */
+    /* Dirichlet wall traces for each side whose kind is DIRICHLET: the wall value at the
+       points k dx / 2, k = 0 .. 2n (n = ny for XMIN/XMAX, nx for YMIN/YMAX); a link of a
+       boundary node crosses the wall at one of these points.  NULL means zero. */
+    const double *P_b[4];
+    const double *S_b[4];
+    const int *init_replay;     /* NULL: iterate the t = 0 pressure to tol; else that
+                                   exact number of sweeps */
+} lbm2p_inputs;
+
+typedef struct {
+    int sub_iters;              /* pressure sweeps run in this step */
+    int status;                 /* lbm2p_status of this step */
+    double residual;            /* last evaluated r (NaN when no check ran) */
+    float sweep_ms;             /* device time of the pressure sweeps (timing on), else -1 */
+    float step_ms;              /* device time of the whole step (timing on), else -1 */
+} lbm2p_step_stats;
+
+/* ABI version of the loaded library (LBM2P_ABI_VERSION). */
+int lbm2p_abi_version(void);
+
+/* Fill params with defaults: phi = 0.2, beta = 0.4, quadratic mobility with mu_w = 1,
+   mu_n = 2, D_s = 0.01, REFERENCE mode with tau_p = 1, tol = 1e-8, check_every = 10,
+   max_sub_iters = 10^7, no-flux walls, FP32 storage, cudaMalloc, default stream. */
+void lbm2p_default_params(lbm2p_params *p);
+
+/* Create a solver and run the t = 0 initialisation of Sec. 4: f = f^eq(P0) (Eq. 3-3),
+ * tau_f from S0, the pressure solve, then g(0) = g^eq(S0) + eps g^(1) (Eqs. gini, gneq;
+ * grad S0 by second-order central differences, grad P by Eq. 3-10a) followed by the t = 0
+ * collision of g.  init_stats (may be NULL) receives the t = 0 solve's statistics.
+ * Returns EINVAL for inconsistent parameters (nothing allocated, *out = NULL). */
+lbm2p_status lbm2p_create(lbm2p **out, const lbm2p_params *p, const lbm2p_inputs *in,
+                          lbm2p_step_stats *init_stats);
+
+/* Replace the dense sources F_p, F_s (host [ny][nx] FP64, NULL = zero) used from the next
+   step on (Eq. 2-17 sources evaluated at the new time level). */
+lbm2p_status lbm2p_set_sources(lbm2p *h, const double *Fp, const double *Fs);
+
+/* Replace a Dirichlet side's wall traces (host FP64, 2n+1 values, NULL = zero). */
+lbm2p_status lbm2p_set_dirichlet(lbm2p *h, int side, const double *P_b, const double *S_b);
+
+/* Advance nsteps physical steps (Sec. 3 order, see the top of this file).
+ * Pressure stopping rule: every check_every-th sweep k >= 2 of a step computes
+ *     r_k = ||dP - mean(dP)||_2 / ||P^k - mean(P^k)||_2,   dP = P^k - P^{k-1},
+ * and the iteration stops when r_k <= tol, or at max_sub_iters (ENOTCONVERGED).
+ * replay: NULL, or nsteps sweep counts (>= 0) to run exactly instead.
+ * stats: NULL or nsteps entries.  Returns the worst status over the steps. */
+lbm2p_status lbm2p_step(lbm2p *h, int nsteps, const int *replay, lbm2p_step_stats *stats);
+
+/* Run exactly nsweeps pressure sweeps (Eq. 3-1) with the current tau_f and sources, no
+   stopping test; residual (may be NULL) receives r of the last sweep when nsweeps >= 2. */
+lbm2p_status lbm2p_pressure_sweeps(lbm2p *h, int nsweeps, double *residual);
+
+/* Darcy velocity u = -K lambda_t(S) grad P (Eq. 3-10b) of the current time level into
+   caller buffers of ny*nx floats (device pointers if on_device, else host). */
+lbm2p_status lbm2p_velocity(lbm2p *h, float *ux, float *uy, int on_device);
+
+/* Pressure (Eq. 3-9a; minus its mean when mean_free_P) and saturation S^n (Eq. 3-9b) of
+   the current time level into ny*nx float buffers (either may be NULL). */
+lbm2p_status lbm2p_fields(lbm2p *h, float *P, float *S, int mean_free_P, int on_device);
+
+/* Number of floats in a state image: 19 planes of ny*nx, in order f_1..f_8 (post-collision
+   pressure populations), g_0..g_8 (post-collision saturation populations), 1/tau_f, S. */
+size_t lbm2p_state_count(const lbm2p *h);
+
+/* Copy the state out / in (checkpoint and restart; count must equal lbm2p_state_count). */
+lbm2p_status lbm2p_get_state(lbm2p *h, float *buf, size_t count, int on_device);
+lbm2p_status lbm2p_set_state(lbm2p *h, const float *buf, size_t count, int on_device);
+
+/* Record CUDA events around each step and its sweeps (fills sweep_ms / step_ms). */
+lbm2p_status lbm2p_set_timing(lbm2p *h, int enable);
+
+/* Running totals since creation: kernels launched by the library, pressure sweeps run. */
+lbm2p_status lbm2p_counters(const lbm2p *h, long long *launches, long long *sweeps);
+
+/* One-line description of the last error of h (or of the last failed create if h NULL). */
+const char *lbm2p_last_error(const lbm2p *h);
+
+/* Free every resource of h (NULL is ignored).  Synchronises the stream first. */
+void lbm2p_destroy(lbm2p *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM2P_H */

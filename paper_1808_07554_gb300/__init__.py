@@ -1,0 +1,398 @@
+"""Python binding of the lbm2p C ABI (``include/lbm2p.h``).
+
+Argument marshalling only: every step of the solver runs in the CUDA kernels of
+``liblbm2p.so``.  The functions below carry the C names; ``Solver`` is a small convenience
+wrapper that owns a handle.  PyTorch, when used, only supplies device memory (its caching
+allocator, through the allocation callback) and the CUDA stream the work is queued on.
+
+The shared library is built in-tree by ``paper_1808_07554_gb300.build.build()`` (or the
+repository's ``__graft_entry__.build()``).  Importing this package never falls back to
+anything else: without the library every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "liblbm2p.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ENOTCONVERGED, ENONFINITE, ENOTIMPL = range(7)
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONVERGED",
+                5: "ENONFINITE", 6: "ENOTIMPL"}
+PERIODIC, NOFLUX, DIRICHLET = 0, 1, 2
+MOB_QUADRATIC, MOB_DECOUPLED, MOB_RATIONAL = 0, 1, 2
+TAU_REFERENCE, TAU_PHYSICAL_DT = 0, 1
+STORE_FP32, STORE_FP16_DEV = 0, 1
+MAX_WELLS = 16
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+RELEASE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
+
+
+class lbm2p_well(C.Structure):
+    _fields_ = [("i", C.c_int), ("j", C.c_int), ("q", C.c_double), ("is_producer", C.c_int)]
+
+
+class lbm2p_params(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("dx", C.c_double), ("dt", C.c_double),
+                ("phi", C.c_double), ("beta", C.c_double), ("mobility", C.c_int),
+                ("mu_w", C.c_double), ("mu_n", C.c_double), ("D_s", C.c_double),
+                ("tau_mode", C.c_int), ("tau_p", C.c_double), ("D_ref", C.c_double),
+                ("tol", C.c_double), ("max_sub_iters", C.c_int), ("check_every", C.c_int),
+                ("bc", C.c_int * 4), ("storage", C.c_int), ("stream", C.c_void_p),
+                ("alloc", ALLOC_FN), ("release", RELEASE_FN), ("alloc_ctx", C.c_void_p)]
+
+
+class lbm2p_inputs(C.Structure):
+    _fields_ = [("K", C.POINTER(C.c_double)), ("S0", C.POINTER(C.c_double)),
+                ("P0", C.POINTER(C.c_double)), ("Fp", C.POINTER(C.c_double)),
+                ("Fs", C.POINTER(C.c_double)), ("wells", C.POINTER(lbm2p_well)),
+                ("n_wells", C.c_int), ("P_b", C.POINTER(C.c_double) * 4),
+                ("S_b", C.POINTER(C.c_double) * 4), ("init_replay", C.POINTER(C.c_int))]
+
+
+class lbm2p_step_stats(C.Structure):
+    _fields_ = [("sub_iters", C.c_int), ("status", C.c_int), ("residual", C.c_double),
+                ("sweep_ms", C.c_float), ("step_ms", C.c_float)]
+
+
+class LBM2PError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load liblbm2p.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_1808_07554_gb300.build.build()")
+    try:                      # let torch bind its CUDA runtime first when it is present
+        import torch  # noqa: F401
+    except ImportError:
+        pass
+    lib = C.CDLL(path)
+    H = C.c_void_p
+    fp = C.POINTER(C.c_float)
+    sig = {
+        "lbm2p_abi_version": (C.c_int, []),
+        "lbm2p_default_params": (None, [C.POINTER(lbm2p_params)]),
+        "lbm2p_create": (C.c_int, [C.POINTER(H), C.POINTER(lbm2p_params),
+                                   C.POINTER(lbm2p_inputs), C.POINTER(lbm2p_step_stats)]),
+        "lbm2p_set_sources": (C.c_int, [H, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+        "lbm2p_set_dirichlet": (C.c_int, [H, C.c_int, C.POINTER(C.c_double),
+                                          C.POINTER(C.c_double)]),
+        "lbm2p_step": (C.c_int, [H, C.c_int, C.POINTER(C.c_int), C.POINTER(lbm2p_step_stats)]),
+        "lbm2p_pressure_sweeps": (C.c_int, [H, C.c_int, C.POINTER(C.c_double)]),
+        "lbm2p_velocity": (C.c_int, [H, fp, fp, C.c_int]),
+        "lbm2p_fields": (C.c_int, [H, fp, fp, C.c_int, C.c_int]),
+        "lbm2p_state_count": (C.c_size_t, [H]),
+        "lbm2p_get_state": (C.c_int, [H, fp, C.c_size_t, C.c_int]),
+        "lbm2p_set_state": (C.c_int, [H, fp, C.c_size_t, C.c_int]),
+        "lbm2p_set_timing": (C.c_int, [H, C.c_int]),
+        "lbm2p_counters": (C.c_int, [H, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
+        "lbm2p_last_error": (C.c_char_p, [H]),
+        "lbm2p_destroy": (None, [H]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _lib_or_raise():
+    return load_library()
+
+
+# ------------------------------------------------------------------------------------------
+# C-named thin wrappers
+# ------------------------------------------------------------------------------------------
+def lbm2p_abi_version() -> int:
+    return _lib_or_raise().lbm2p_abi_version()
+
+
+def lbm2p_default_params() -> lbm2p_params:
+    p = lbm2p_params()
+    _lib_or_raise().lbm2p_default_params(C.byref(p))
+    return p
+
+
+def lbm2p_last_error(h=None) -> str:
+    s = _lib_or_raise().lbm2p_last_error(h)
+    return s.decode() if s else ""
+
+
+def _check(st, h=None, allow=(OK,)):
+    if st not in allow:
+        raise LBM2PError(st, lbm2p_last_error(h))
+    return st
+
+
+def lbm2p_create(params: lbm2p_params, inputs: lbm2p_inputs, init_stats=None):
+    h = C.c_void_p()
+    st = _lib_or_raise().lbm2p_create(C.byref(h), C.byref(params), C.byref(inputs),
+                                      C.byref(init_stats) if init_stats is not None else None)
+    _check(st, None if not h.value else h, allow=(OK, ENOTCONVERGED))
+    return h, st
+
+
+def lbm2p_set_sources(h, Fp, Fs):
+    return _check(_lib_or_raise().lbm2p_set_sources(h, _dp(Fp), _dp(Fs)), h)
+
+
+def lbm2p_set_dirichlet(h, side, P_b, S_b):
+    return _check(_lib_or_raise().lbm2p_set_dirichlet(h, side, _dp(P_b), _dp(S_b)), h)
+
+
+def lbm2p_step(h, nsteps, replay=None, stats=None):
+    rp = None
+    if replay is not None:
+        rp = (C.c_int * nsteps)(*[int(v) for v in replay])
+    st = _lib_or_raise().lbm2p_step(h, nsteps, rp, stats)
+    return _check(st, h, allow=(OK, ENOTCONVERGED))
+
+
+def lbm2p_pressure_sweeps(h, nsweeps):
+    r = C.c_double(0.0)
+    _check(_lib_or_raise().lbm2p_pressure_sweeps(h, nsweeps, C.byref(r)), h)
+    return r.value
+
+
+def lbm2p_velocity(h, ux_ptr, uy_ptr, on_device):
+    return _check(_lib_or_raise().lbm2p_velocity(h, ux_ptr, uy_ptr, on_device), h)
+
+
+def lbm2p_fields(h, P_ptr, S_ptr, mean_free_P, on_device):
+    return _check(_lib_or_raise().lbm2p_fields(h, P_ptr, S_ptr, mean_free_P, on_device), h)
+
+
+def lbm2p_state_count(h) -> int:
+    return int(_lib_or_raise().lbm2p_state_count(h))
+
+
+def lbm2p_get_state(h, buf_ptr, count, on_device):
+    return _check(_lib_or_raise().lbm2p_get_state(h, buf_ptr, count, on_device), h)
+
+
+def lbm2p_set_state(h, buf_ptr, count, on_device):
+    return _check(_lib_or_raise().lbm2p_set_state(h, buf_ptr, count, on_device), h)
+
+
+def lbm2p_set_timing(h, enable):
+    return _check(_lib_or_raise().lbm2p_set_timing(h, int(bool(enable))), h)
+
+
+def lbm2p_counters(h):
+    a, b = C.c_longlong(0), C.c_longlong(0)
+    _check(_lib_or_raise().lbm2p_counters(h, C.byref(a), C.byref(b)), h)
+    return a.value, b.value
+
+
+def lbm2p_destroy(h):
+    if h:
+        _lib_or_raise().lbm2p_destroy(h)
+
+
+# ------------------------------------------------------------------------------------------
+# marshalling helpers
+# ------------------------------------------------------------------------------------------
+def _f64(a, n=None):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if n is not None and a.size != n:
+        raise ValueError(f"expected {n} values, got {a.size}")
+    return a
+
+
+def _dp(a):
+    if a is None:
+        return None
+    a = _f64(a)
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _fp(a):
+    return None if a is None else a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+class _TorchMemory:
+    """Device memory from torch's caching allocator on torch's current stream."""
+
+    def __init__(self, device=None):
+        import torch
+        self.torch = torch
+        self.device = torch.cuda.current_device() if device is None else device
+        self.stream = torch.cuda.current_stream(self.device)
+        self._live = {}
+
+        def _alloc(nbytes, ctx):
+            try:
+                ptr = torch.cuda.caching_allocator_alloc(int(nbytes), self.device, self.stream)
+            except Exception:       # out of memory: report NULL to the library
+                return None
+            self._live[int(ptr)] = int(nbytes)
+            return int(ptr)
+
+        def _release(ptr, nbytes, ctx):
+            if ptr and int(ptr) in self._live:
+                del self._live[int(ptr)]
+                torch.cuda.caching_allocator_delete(int(ptr))
+
+        self.alloc_fn = ALLOC_FN(_alloc)
+        self.release_fn = RELEASE_FN(_release)
+
+
+class Solver:
+    """Owns one lbm2p handle.  Arrays are numpy [ny, nx]; FP64 in, FP32 out."""
+
+    def __init__(self, *, nx, ny, dx, dt, phi, beta, mobility, mu_w, mu_n, D_s, tau_mode,
+                 tau_p, bc, K, S0, P0=None, Fp=None, Fs=None, wells=(), P_b=None, S_b=None,
+                 D_ref=0.0, tol=1e-8, max_sub_iters=10_000_000, check_every=10,
+                 init_replay=None, use_torch=True, stream=None):
+        lib = _lib_or_raise()
+        self.nx, self.ny = int(nx), int(ny)
+        n = self.nx * self.ny
+        p = lbm2p_params()
+        lib.lbm2p_default_params(C.byref(p))
+        p.nx, p.ny, p.dx, p.dt = self.nx, self.ny, float(dx), float(dt)
+        p.phi, p.beta, p.mobility = float(phi), float(beta), int(mobility)
+        p.mu_w, p.mu_n, p.D_s = float(mu_w), float(mu_n), float(D_s)
+        p.tau_mode, p.tau_p, p.D_ref = int(tau_mode), float(tau_p), float(D_ref)
+        p.tol, p.max_sub_iters, p.check_every = float(tol), int(max_sub_iters), int(check_every)
+        for s in range(4):
+            p.bc[s] = int(bc[s])
+        self._mem = None
+        if use_torch:
+            self._mem = _TorchMemory()
+            p.alloc = self._mem.alloc_fn
+            p.release = self._mem.release_fn
+            p.stream = self._mem.stream.cuda_stream if stream is None else stream
+        elif stream is not None:
+            p.stream = stream
+        self.params = p
+        keep = []
+        inp = lbm2p_inputs()
+
+        def put(a):
+            a = _f64(a, n)
+            keep.append(a)
+            return a.ctypes.data_as(C.POINTER(C.c_double))
+
+        inp.K = put(K)
+        inp.S0 = put(S0)
+        inp.P0 = put(P0) if P0 is not None else None
+        inp.Fp = put(Fp) if Fp is not None else None
+        inp.Fs = put(Fs) if Fs is not None else None
+        wl = list(wells)
+        if wl:
+            arr = (lbm2p_well * len(wl))(*[lbm2p_well(int(i), int(j), float(q), int(bool(pr)))
+                                           for (i, j, q, pr) in wl])
+            keep.append(arr)
+            inp.wells = C.cast(arr, C.POINTER(lbm2p_well))
+        inp.n_wells = len(wl)
+        for s in range(4):
+            if P_b is not None and P_b[s] is not None:
+                a = _f64(P_b[s])
+                keep.append(a)
+                inp.P_b[s] = a.ctypes.data_as(C.POINTER(C.c_double))
+            if S_b is not None and S_b[s] is not None:
+                a = _f64(S_b[s])
+                keep.append(a)
+                inp.S_b[s] = a.ctypes.data_as(C.POINTER(C.c_double))
+        if init_replay is not None:
+            ir = C.c_int(int(init_replay))
+            keep.append(ir)
+            inp.init_replay = C.pointer(ir)
+        self.init_stats = lbm2p_step_stats()
+        self.h, self.create_status = lbm2p_create(p, inp, self.init_stats)
+        del keep
+
+    @classmethod
+    def from_problem(cls, prob, **kw):
+        """Build from any object with the attributes of a problem description (nx, ny, dx,
+        dt, phi, beta, mobility, mu_w, mu_n, D_s, tau_mode, tau_p, bc, K, S0, P0, Fp, Fs,
+        wells, P_b, S_b, D_ref)."""
+        return cls(nx=prob.nx, ny=prob.ny, dx=prob.dx, dt=prob.dt, phi=prob.phi, beta=prob.beta,
+                   mobility=prob.mobility, mu_w=prob.mu_w, mu_n=prob.mu_n, D_s=prob.D_s,
+                   tau_mode=prob.tau_mode, tau_p=prob.tau_p, bc=prob.bc, K=prob.K, S0=prob.S0,
+                   P0=prob.P0, Fp=prob.Fp, Fs=prob.Fs, wells=prob.wells, P_b=prob.P_b,
+                   S_b=prob.S_b, D_ref=prob.D_ref, **kw)
+
+    # -- lifecycle ----------------------------------------------------------------------
+    def close(self):
+        if getattr(self, "h", None):
+            lbm2p_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- inputs ---------------------------------------------------------------------------
+    def set_sources(self, Fp=None, Fs=None):
+        n = self.nx * self.ny
+        lbm2p_set_sources(self.h, _f64(Fp, n), _f64(Fs, n))
+
+    def set_dirichlet(self, side, P_b=None, S_b=None):
+        lbm2p_set_dirichlet(self.h, side, P_b, S_b)
+
+    # -- stepping -------------------------------------------------------------------------
+    def step(self, nsteps=1, replay=None):
+        """Advance nsteps; returns (status, stats list)."""
+        stats = (lbm2p_step_stats * max(1, nsteps))()
+        st = lbm2p_step(self.h, nsteps, replay, stats)
+        return st, [stats[i] for i in range(nsteps)]
+
+    def pressure_sweeps(self, nsweeps):
+        return lbm2p_pressure_sweeps(self.h, nsweeps)
+
+    def set_timing(self, enable=True):
+        lbm2p_set_timing(self.h, enable)
+
+    def counters(self):
+        return lbm2p_counters(self.h)
+
+    # -- outputs --------------------------------------------------------------------------
+    def fields(self, mean_free_P=False):
+        P = np.empty((self.ny, self.nx), np.float32)
+        S = np.empty((self.ny, self.nx), np.float32)
+        lbm2p_fields(self.h, _fp(P), _fp(S), int(bool(mean_free_P)), 0)
+        return P, S
+
+    def velocity(self):
+        ux = np.empty((self.ny, self.nx), np.float32)
+        uy = np.empty((self.ny, self.nx), np.float32)
+        lbm2p_velocity(self.h, _fp(ux), _fp(uy), 0)
+        return ux, uy
+
+    def get_state(self):
+        n = lbm2p_state_count(self.h)
+        buf = np.empty(n, np.float32)
+        lbm2p_get_state(self.h, _fp(buf), n, 0)
+        return buf.reshape(19, self.ny, self.nx)
+
+    def set_state(self, state):
+        n = lbm2p_state_count(self.h)
+        buf = np.ascontiguousarray(state, dtype=np.float32).reshape(-1)
+        if buf.size != n:
+            raise ValueError(f"state must hold {n} floats")
+        lbm2p_set_state(self.h, _fp(buf), n, 0)

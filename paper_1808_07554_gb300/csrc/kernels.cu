@@ -1,0 +1,615 @@
+// CUDA kernels of the two-phase Darcy LB solver (sm_103a).
+//
+// Every lattice kernel is a grid-stride loop over row tiles of kBlock nodes (one node per
+// thread, consecutive threads on consecutive x): the grid is sized to the resident-block
+// capacity of the GPU, so each block sweeps many tiles and the FP64 residual partials stay
+// few.  Pull scheme: a node gathers f_i^+(x - c_i) from the previous sweep's buffer and
+// writes its own post-collision values into the other buffer (ping-pong), so one launch
+// is one fused stream + collide of Eq. 3-1 (or Eq. 3-2).  Wall rules of Sec. 4 are folded
+// into the gather: interior nodes take a branch-free path; only nodes on the lattice edge
+// evaluate the periodic / bounce-back / anti-bounce-back substitution.
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "lbm2p_device.cuh"
+
+namespace lbm2p_dev {
+
+// --------------------------------------------------------------------------------------
+// gather with the wall rules of Sec. 4
+// --------------------------------------------------------------------------------------
+// Value arriving at (x, y) along direction I from the post-collision plane src_i, for a
+// node on the lattice edge.  If x - c_I is outside the lattice the link crosses a wall:
+// periodic sides wrap; no-flux gives the node's own opposite population (bounce-back);
+// Dirichlet gives -opposite + 2 eq_opp * (wall value where the link crosses the wall)
+// (anti-bounce-back).  x-sides are tested first, so corner links follow the x-side rule.
+template <int I>
+__device__ __forceinline__ float pull_edge(const float *__restrict__ src_i,
+                                           const float *__restrict__ src_opp, const Geom &g,
+                                           const float *const *trace, float eq_opp, int x,
+                                           int y)
+{
+    constexpr int ex = cx(I), ey = cy(I);
+    int xs = x - ex, ys = y - ey, side = -1;
+    if (xs < 0 || xs >= g.nx) {
+        const int sd = xs < 0 ? 0 : 1;
+        if (g.bc[sd] == BC_PERIODIC)
+            xs += xs < 0 ? g.nx : -g.nx;
+        else
+            side = sd;
+    }
+    if (side < 0 && (ys < 0 || ys >= g.ny)) {
+        const int sd = ys < 0 ? 2 : 3;
+        if (g.bc[sd] == BC_PERIODIC)
+            ys += ys < 0 ? g.ny : -g.ny;
+        else
+            side = sd;
+    }
+    if (side < 0)
+        return src_i[ys * g.pitch + xs];
+    const float b = src_opp[y * g.pitch + x];
+    if (g.bc[side] == BC_NOFLUX)
+        return b;
+    const int k = side < 2 ? 2 * y + 1 - ey : 2 * x + 1 - ex;
+    return -b + 2.0f * eq_opp * trace[side][k];
+}
+
+__device__ __forceinline__ bool interior(const Geom &g, int x, int y)
+{
+    return x > 0 && x < g.nx - 1 && y > 0 && y < g.ny - 1;
+}
+
+// f_1 .. f_8 pulled into (x, y) (pressure distribution, planes 0..7)
+__device__ __forceinline__ void gather_f(const float *const *fin, const Geom &g,
+                                         const float *const *Pb, int x, int y, int o,
+                                         float (&f)[8])
+{
+    if (interior(g, x, y)) {
+        const int p = g.pitch;
+        f[0] = fin[0][o - 1];
+        f[1] = fin[1][o - p];
+        f[2] = fin[2][o + 1];
+        f[3] = fin[3][o + p];
+        f[4] = fin[4][o - p - 1];
+        f[5] = fin[5][o - p + 1];
+        f[6] = fin[6][o + p + 1];
+        f[7] = fin[7][o + p - 1];
+    } else {
+        f[0] = pull_edge<1>(fin[0], fin[opp(1) - 1], g, Pb, wgt(opp(1)), x, y);
+        f[1] = pull_edge<2>(fin[1], fin[opp(2) - 1], g, Pb, wgt(opp(2)), x, y);
+        f[2] = pull_edge<3>(fin[2], fin[opp(3) - 1], g, Pb, wgt(opp(3)), x, y);
+        f[3] = pull_edge<4>(fin[3], fin[opp(4) - 1], g, Pb, wgt(opp(4)), x, y);
+        f[4] = pull_edge<5>(fin[4], fin[opp(5) - 1], g, Pb, wgt(opp(5)), x, y);
+        f[5] = pull_edge<6>(fin[5], fin[opp(6) - 1], g, Pb, wgt(opp(6)), x, y);
+        f[6] = pull_edge<7>(fin[6], fin[opp(7) - 1], g, Pb, wgt(opp(7)), x, y);
+        f[7] = pull_edge<8>(fin[7], fin[opp(8) - 1], g, Pb, wgt(opp(8)), x, y);
+    }
+}
+
+// g_0 .. g_8 pulled into (x, y) (saturation distribution, planes 0..8)
+__device__ __forceinline__ void gather_g(const float *const *gin, const Geom &g, const Model &m,
+                                         const float *const *Sb, int x, int y, int o,
+                                         float (&q)[9])
+{
+    q[0] = gin[0][o];
+    if (interior(g, x, y)) {
+        const int p = g.pitch;
+        q[1] = gin[1][o - 1];
+        q[2] = gin[2][o - p];
+        q[3] = gin[3][o + 1];
+        q[4] = gin[4][o + p];
+        q[5] = gin[5][o - p - 1];
+        q[6] = gin[6][o - p + 1];
+        q[7] = gin[7][o + p + 1];
+        q[8] = gin[8][o + p - 1];
+    } else {
+        q[1] = pull_edge<1>(gin[1], gin[opp(1)], g, Sb, m.Gam[opp(1)], x, y);
+        q[2] = pull_edge<2>(gin[2], gin[opp(2)], g, Sb, m.Gam[opp(2)], x, y);
+        q[3] = pull_edge<3>(gin[3], gin[opp(3)], g, Sb, m.Gam[opp(3)], x, y);
+        q[4] = pull_edge<4>(gin[4], gin[opp(4)], g, Sb, m.Gam[opp(4)], x, y);
+        q[5] = pull_edge<5>(gin[5], gin[opp(5)], g, Sb, m.Gam[opp(5)], x, y);
+        q[6] = pull_edge<6>(gin[6], gin[opp(6)], g, Sb, m.Gam[opp(6)], x, y);
+        q[7] = pull_edge<7>(gin[7], gin[opp(7)], g, Sb, m.Gam[opp(7)], x, y);
+        q[8] = pull_edge<8>(gin[8], gin[opp(8)], g, Sb, m.Gam[opp(8)], x, y);
+    }
+}
+
+// Eq. 3-9a: P = sum_{i=1..8} f_i / (1 - w_0) = (9/5) sum
+__device__ __forceinline__ float pressure_of(const float (&f)[8])
+{
+    return (((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7]))) * 1.8f;
+}
+
+// sum_i c_i f_i (x and y components)
+__device__ __forceinline__ void first_moment(const float (&f)[8], float &mx, float &my)
+{
+    mx = (f[0] - f[2]) + ((f[4] - f[5]) - (f[6] - f[7]));
+    my = (f[1] - f[3]) + ((f[4] + f[5]) - (f[6] + f[7]));
+}
+
+__device__ __forceinline__ void mobility(const Model &m, float S, float &lw, float &lt)
+{
+    if (m.mobility == MOB_QUADRATIC) {
+        lw = S * S * m.inv_mu_w;
+        const float sn = 1.0f - S;
+        lt = lw + sn * sn * m.inv_mu_n;
+    } else if (m.mobility == MOB_DECOUPLED) {
+        lw = m.inv_mu_w;
+        lt = m.inv_mu_w;
+    } else {
+        lt = 1.0f / (0.5f - 0.2f * S);
+        lw = S * lt;
+    }
+}
+
+// dt F_s at node o: dense part plus wells; the producer uses S* = sum g / phi.
+__device__ __forceinline__ float saturation_source(const Model &m, const Wells &w,
+                                                   const float *Fs, int o, float Sstar)
+{
+    float F = Fs ? Fs[o] : 0.0f;
+    for (int k = 0; k < w.n; ++k) {
+        if (o == w.idx[k]) {
+            if (w.producer[k]) {
+                float lw, lt;
+                mobility(m, Sstar, lw, lt);
+                F -= w.qs[k] * (lt != 0.0f ? lw / lt : 0.0f);
+            } else {
+                F += w.qs[k];
+            }
+        }
+    }
+    return F;
+}
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1)
+        v += __shfl_xor_sync(0xffffffffu, v, s);
+    return v;
+}
+
+// --------------------------------------------------------------------------------------
+// a2/a3: fused pressure sweep (Eq. 3-1) with optional residual partials
+// --------------------------------------------------------------------------------------
+template <bool CHECK, bool WRITE_P>
+__global__ void __launch_bounds__(kBlock) k_pressure(const __grid_constant__ PressureArgs a)
+{
+    const Geom &g = a.g;
+    const int lane = threadIdx.x & 31;
+    double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
+    const float shift = CHECK ? *a.shift : 0.0f;
+    for (int t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
+        const int y = t / g.tiles_x;
+        const int x = (t - y * g.tiles_x) * kBlock + threadIdx.x;
+        float d = 0.0f, p = 0.0f;
+        if (x < g.nx) {
+            const int o = y * g.pitch + x;
+            float f[8];
+            gather_f(a.fin, g, a.Pb, x, y, o, f);
+            const float P = pressure_of(f);
+            const float it = a.inv_tau[o];
+            float F = a.Fp ? a.Fp[o] : 0.0f;
+            for (int k = 0; k < a.w.n; ++k)
+                if (o == a.w.idx[k])
+                    F += a.w.fp[k];
+            const float Fq = 0.125f * F;   // w_bar_i = 1/8 (Eq. 3-5a)
+            // Eq. 2-1b: f_i^+ = f_i - (f_i - w_i P)/tau_f + w_bar_i F~_p
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                a.fout[i][o] = fmaf(wgt(i + 1) * P - f[i], it, f[i]) + Fq;
+            if (CHECK) {
+                d = P - a.Pio[o];
+                p = P - shift;
+            }
+            if (WRITE_P)
+                a.Pio[o] = P;
+        }
+        if (CHECK) {
+            const float s0 = warp_sum(d), s1 = warp_sum(d * d);
+            const float s2 = warp_sum(p), s3 = warp_sum(p * p);
+            if (lane == 0) {
+                acc0 += s0;
+                acc1 += s1;
+                acc2 += s2;
+                acc3 += s3;
+            }
+        }
+    }
+    if (CHECK) {
+        __shared__ double red[kBlock / 32][4];
+        const int warp = threadIdx.x >> 5;
+        if (lane == 0) {
+            red[warp][0] = acc0;
+            red[warp][1] = acc1;
+            red[warp][2] = acc2;
+            red[warp][3] = acc3;
+        }
+        __syncthreads();
+        if (threadIdx.x < 4) {
+            double s = 0.0;
+#pragma unroll
+            for (int w = 0; w < kBlock / 32; ++w)
+                s += red[w][threadIdx.x];
+            a.partials[4 * blockIdx.x + threadIdx.x] = s;
+        }
+    }
+}
+
+// r = ||dP - mean dP|| / ||P - mean P|| from the block partials (FP64, fixed order)
+__global__ void __launch_bounds__(256) k_residual_finalize(const double *__restrict__ partials,
+                                                           int nparts, long long nnodes,
+                                                           float *shift, ResidualOut *out)
+{
+    __shared__ double red[256][4];
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int i = threadIdx.x; i < nparts; i += 256)
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            s[c] += partials[4 * i + c];
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+        red[threadIdx.x][c] = s[c];
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (threadIdx.x < h)
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                red[threadIdx.x][c] += red[threadIdx.x + h][c];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double N = (double)nnodes;
+        const double sd = red[0][0], sdd = red[0][1], sp = red[0][2], spp = red[0][3];
+        const double c = (double)*shift;
+        double r;
+        if (!isfinite(sd) || !isfinite(sdd) || !isfinite(sp) || !isfinite(spp)) {
+            r = nan("");
+        } else {
+            double num = sdd - sd * sd / N;
+            double den = spp - sp * sp / N;
+            num = num > 0.0 ? num : 0.0;
+            den = den > 0.0 ? den : 0.0;
+            r = den > 0.0 ? sqrt(num / den) : (num > 0.0 ? INFINITY : 0.0);
+            *shift = (float)(c + sp / N);
+        }
+        out->r = r;
+        out->mean_P = c + sp / N;
+        out->sums[0] = sd;
+        out->sums[1] = sdd;
+        out->sums[2] = sp;
+        out->sums[3] = spp;
+    }
+}
+
+// --------------------------------------------------------------------------------------
+// a1: stream g, S^n (Eq. 3-9b), 1/tau_f (Eq. 3-11a with D_p = K lambda_t(S))
+// --------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlock) k_refresh(const __grid_constant__ RefreshArgs a)
+{
+    const Geom &g = a.g;
+    for (int t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
+        const int y = t / g.tiles_x;
+        const int x = (t - y * g.tiles_x) * kBlock + threadIdx.x;
+        if (x >= g.nx)
+            continue;
+        const int o = y * g.pitch + x;
+        float q[9];
+        gather_g(a.gin, g, a.m, a.Sb, x, y, o, q);
+        const float sum = (q[0] + ((q[1] + q[2]) + (q[3] + q[4]))) + ((q[5] + q[6]) + (q[7] + q[8]));
+        const float Fs = saturation_source(a.m, a.w, a.Fs, o, sum * a.m.inv_phi);
+        const float S = (sum + 0.5f * Fs) * a.m.inv_phi;
+        float lw, lt;
+        mobility(a.m, S, lw, lt);
+        a.inv_tau[o] = 1.0f / (0.5f + a.m.s3 * a.K[o] * lt);
+    }
+}
+
+// --------------------------------------------------------------------------------------
+// a4 + a5: local grad P (Eq. 3-10a) and the fused saturation stream + collide (Eq. 3-2)
+// --------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlock) k_saturation(const __grid_constant__ SaturationArgs a)
+{
+    const Geom &g = a.g;
+    const Model &m = a.m;
+    for (int t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
+        const int y = t / g.tiles_x;
+        const int x = (t - y * g.tiles_x) * kBlock + threadIdx.x;
+        if (x >= g.nx)
+            continue;
+        const int o = y * g.pitch + x;
+        float f[8], q[9];
+        gather_f(a.fin, g, a.Pb, x, y, o, f);
+        gather_g(a.gin, g, m, a.Sb, x, y, o, q);
+        const float sum = (q[0] + ((q[1] + q[2]) + (q[3] + q[4]))) + ((q[5] + q[6]) + (q[7] + q[8]));
+        const float Fs = saturation_source(m, a.w, a.Fs, o, sum * m.inv_phi);
+        const float S = (sum + 0.5f * Fs) * m.inv_phi;
+        // grad_X P = -3 sum_i c_i f_i / tau_f  (lattice units, Eq. 3-10a)
+        float mx, my;
+        first_moment(f, mx, my);
+        const float it = a.inv_tau[o];
+        const float gx = -3.0f * mx * it, gy = -3.0f * my * it;
+        float lw, lt;
+        mobility(m, S, lw, lt);
+        // gamma~ = -3 lambda_w K dt / dx^2 (Eq. 3-8 in lattice units), pre-divided by tau_g
+        const float gam = -m.gam_c * lw * a.K[o] * m.inv_tau_g;
+        const float src = m.src_g * Fs;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const float wi = wgt(i);
+            const float cg = (float)cx(i) * gx + (float)cy(i) * gy;
+            const float eq = m.Gam[i] * S;
+            a.gout[i][o] = fmaf(eq - q[i], m.inv_tau_g, q[i]) + wi * src + gam * wi * cg;
+        }
+        a.S[o] = S;
+    }
+}
+
+// --------------------------------------------------------------------------------------
+// a6: initial g (Eqs. gini, gneq) followed by the t = 0 collision
+// --------------------------------------------------------------------------------------
+__device__ __forceinline__ float s_at(const float *S, const Geom &g, int x, int y)
+{
+    return S[y * g.pitch + x];
+}
+
+// central difference of S0 along one axis in lattice units; mirror at no-flux walls,
+// wrap if periodic, second-order one-sided at Dirichlet walls
+__device__ float fd_axis(const float *S, const Geom &g, int x, int y, int axis)
+{
+    const int n = axis == 0 ? g.nx : g.ny;
+    const int c = axis == 0 ? x : y;
+    const int lo_side = axis == 0 ? 0 : 2, hi_side = lo_side + 1;
+    auto at = [&](int cc) { return axis == 0 ? s_at(S, g, cc, y) : s_at(S, g, x, cc); };
+    if (c == 0 && g.bc[lo_side] == BC_DIRICHLET)
+        return (-3.0f * at(0) + 4.0f * at(1) - at(2)) * 0.5f;
+    if (c == n - 1 && g.bc[hi_side] == BC_DIRICHLET)
+        return (3.0f * at(n - 1) - 4.0f * at(n - 2) + at(n - 3)) * 0.5f;
+    const float lo = c - 1 >= 0 ? at(c - 1) : (g.bc[lo_side] == BC_PERIODIC ? at(n - 1) : at(c));
+    const float hi = c + 1 < n ? at(c + 1) : (g.bc[hi_side] == BC_PERIODIC ? at(0) : at(c));
+    return (hi - lo) * 0.5f;
+}
+
+__global__ void __launch_bounds__(kBlock) k_init_g(const __grid_constant__ InitGArgs a)
+{
+    const Geom &g = a.g;
+    const Model &m = a.m;
+    const float tg = 1.0f / m.inv_tau_g;
+    for (int t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
+        const int y = t / g.tiles_x;
+        const int x = (t - y * g.tiles_x) * kBlock + threadIdx.x;
+        if (x >= g.nx)
+            continue;
+        const int o = y * g.pitch + x;
+        const float S0 = a.S0[o];
+        const float sx = fd_axis(a.S0, g, x, y, 0), sy = fd_axis(a.S0, g, x, y, 1);
+        float f[8];
+        gather_f(a.fin, g, a.Pb, x, y, o, f);
+        float mx, my;
+        first_moment(f, mx, my);
+        const float it = a.inv_tau[o];
+        const float gx = -3.0f * mx * it, gy = -3.0f * my * it;
+        const float Fs = saturation_source(m, a.w, a.Fs, o, S0);   // S* = S0 at t = 0
+        float lw, lt;
+        mobility(m, S0, lw, lt);
+        const float gam0 = -m.gam_c * lw * a.K[o];
+        float q[9];
+        float sum = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const float wi = wgt(i);
+            const float cS = (float)cx(i) * sx + (float)cy(i) * sy;
+            const float cP = (float)cx(i) * gx + (float)cy(i) * gy;
+            const float neq = -tg * ((m.Gam[i] * m.inv_phi - wi * m.src_g) * Fs + m.Gam[i] * cS
+                                     - gam0 * wi * cP * m.inv_tau_g);
+            q[i] = m.Gam[i] * S0 + neq;
+            sum += q[i];
+        }
+        const float S = (sum + 0.5f * Fs) * m.inv_phi;
+        mobility(m, S, lw, lt);
+        const float gam = -m.gam_c * lw * a.K[o] * m.inv_tau_g;
+        const float src = m.src_g * Fs;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const float wi = wgt(i);
+            const float cg = (float)cx(i) * gx + (float)cy(i) * gy;
+            a.gout[i][o] = fmaf(m.Gam[i] * S - q[i], m.inv_tau_g, q[i]) + wi * src + gam * wi * cg;
+        }
+        a.S[o] = S;
+    }
+}
+
+// f_i^+ = w_i P0 (Eq. 3-3 for i >= 1); P0 may be null (zero)
+__global__ void __launch_bounds__(kBlock) k_fill_f_eq(float *f0, float *f1, float *f2, float *f3,
+                                                      float *f4, float *f5, float *f6, float *f7,
+                                                      const float *P0, Geom g)
+{
+    for (int t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
+        const int y = t / g.tiles_x;
+        const int x = (t - y * g.tiles_x) * kBlock + threadIdx.x;
+        if (x >= g.nx)
+            continue;
+        const int o = y * g.pitch + x;
+        const float P = P0 ? P0[o] : 0.0f;
+        f0[o] = wgt(1) * P;
+        f1[o] = wgt(2) * P;
+        f2[o] = wgt(3) * P;
+        f3[o] = wgt(4) * P;
+        f4[o] = wgt(5) * P;
+        f5[o] = wgt(6) * P;
+        f6[o] = wgt(7) * P;
+        f7[o] = wgt(8) * P;
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) k_tau_from_S(float *inv_tau, const float *S,
+                                                       const float *K, Geom g, Model m)
+{
+    for (int t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
+        const int y = t / g.tiles_x;
+        const int x = (t - y * g.tiles_x) * kBlock + threadIdx.x;
+        if (x >= g.nx)
+            continue;
+        const int o = y * g.pitch + x;
+        float lw, lt;
+        mobility(m, S[o], lw, lt);
+        inv_tau[o] = 1.0f / (0.5f + m.s3 * K[o] * lt);
+    }
+}
+
+// --------------------------------------------------------------------------------------
+// fields: P (Eq. 3-9a), S, u = -K lambda_t grad P (Eq. 3-10b) into compact [ny][nx]
+// --------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlock) k_fields(const __grid_constant__ FieldsArgs a)
+{
+    const Geom &g = a.g;
+    for (int t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
+        const int y = t / g.tiles_x;
+        const int x = (t - y * g.tiles_x) * kBlock + threadIdx.x;
+        if (x >= g.nx)
+            continue;
+        const int o = y * g.pitch + x;
+        const long long c = (long long)y * g.nx + x;
+        float f[8];
+        gather_f(a.fin, g, a.Pb, x, y, o, f);
+        const float S = a.S[o];
+        if (a.P_out)
+            a.P_out[c] = pressure_of(f);
+        if (a.S_out)
+            a.S_out[c] = S;
+        if (a.ux_out || a.uy_out) {
+            float mx, my;
+            first_moment(f, mx, my);
+            const float it = a.inv_tau[o];
+            const float gpx = -3.0f * mx * it * a.m.inv_dx, gpy = -3.0f * my * it * a.m.inv_dx;
+            float lw, lt;
+            mobility(a.m, S, lw, lt);
+            const float kl = a.K[o] * lt;
+            if (a.ux_out)
+                a.ux_out[c] = -kl * gpx;
+            if (a.uy_out)
+                a.uy_out[c] = -kl * gpy;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_sum_compact(const float *__restrict__ x, long long n,
+                                                     double *partials)
+{
+    __shared__ double red[256];
+    double s = 0.0;
+    for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += 256LL * gridDim.x)
+        s += (double)x[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (threadIdx.x < h)
+            red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        partials[blockIdx.x] = red[0];
+}
+
+__global__ void k_finalize_mean(const double *partials, int nparts, long long n, double *mean)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < nparts; ++i)
+            s += partials[i];
+        *mean = s / (double)n;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_subtract_mean(float *x, long long n, const double *mean)
+{
+    const float m = (float)*mean;
+    for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += 256LL * gridDim.x)
+        x[i] -= m;
+}
+
+}  // namespace lbm2p_dev
+
+// ======================================================================================
+// launchers
+// ======================================================================================
+namespace lbm2p_launch {
+
+static cudaStream_t S(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+int max_blocks_per_sm_pressure()
+{
+    int a = 0, b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pressure<false, false>, kBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pressure<true, true>, kBlock, 0);
+    int m = a < b ? a : b;
+    return m > 0 ? m : 1;
+}
+
+void pressure_sweep(const PressureArgs &a, bool check, bool write_p, int grid, void *stream)
+{
+    if (check && write_p)
+        k_pressure<true, true><<<grid, kBlock, 0, S(stream)>>>(a);
+    else if (check)
+        k_pressure<true, false><<<grid, kBlock, 0, S(stream)>>>(a);
+    else if (write_p)
+        k_pressure<false, true><<<grid, kBlock, 0, S(stream)>>>(a);
+    else
+        k_pressure<false, false><<<grid, kBlock, 0, S(stream)>>>(a);
+}
+
+void residual_finalize(const double *partials, int nparts, long long nnodes, float *shift,
+                       ResidualOut *out, void *stream)
+{
+    k_residual_finalize<<<1, 256, 0, S(stream)>>>(partials, nparts, nnodes, shift, out);
+}
+
+void refresh(const RefreshArgs &a, int grid, void *stream)
+{
+    k_refresh<<<grid, kBlock, 0, S(stream)>>>(a);
+}
+
+void saturation(const SaturationArgs &a, int grid, void *stream)
+{
+    k_saturation<<<grid, kBlock, 0, S(stream)>>>(a);
+}
+
+void init_g(const InitGArgs &a, int grid, void *stream)
+{
+    k_init_g<<<grid, kBlock, 0, S(stream)>>>(a);
+}
+
+void fill_f_eq(float *const fout[8], const float *P0, Geom g, int grid, void *stream)
+{
+    k_fill_f_eq<<<grid, kBlock, 0, S(stream)>>>(fout[0], fout[1], fout[2], fout[3], fout[4],
+                                                 fout[5], fout[6], fout[7], P0, g);
+}
+
+void tau_from_S(float *inv_tau, const float *Sp, const float *K, Geom g, Model m, int grid,
+                void *stream)
+{
+    k_tau_from_S<<<grid, kBlock, 0, S(stream)>>>(inv_tau, Sp, K, g, m);
+}
+
+void fields(const FieldsArgs &a, int grid, void *stream)
+{
+    k_fields<<<grid, kBlock, 0, S(stream)>>>(a);
+}
+
+void sum_compact(const float *x, long long n, double *partials, int grid, void *stream)
+{
+    k_sum_compact<<<grid, 256, 0, S(stream)>>>(x, n, partials);
+}
+
+void finalize_mean(const double *partials, int nparts, long long n, double *mean, void *stream)
+{
+    k_finalize_mean<<<1, 32, 0, S(stream)>>>(partials, nparts, n, mean);
+}
+
+void subtract_mean(float *x, long long n, const double *mean, int grid, void *stream)
+{
+    k_subtract_mean<<<grid, 256, 0, S(stream)>>>(x, n, mean);
+}
+
+}  // namespace lbm2p_launch

@@ -1,0 +1,168 @@
+// Device-side definitions shared by the solver's kernels and its runtime: the D2Q9
+// lattice, the mobility laws, and the argument blocks passed to each kernel by value.
+//
+// D2Q9 (Eqs. 3-5, 3-5a, 3-6): c_0 = (0,0); c_1..c_4 = (1,0), (0,1), (-1,0), (0,-1);
+// c_5..c_8 = (1,1), (-1,1), (-1,-1), (1,-1); weights 4/9, 1/9, 1/36; pressure source
+// weights 0, 1/8 (x8); c_s^2 = 1/3 in lattice units.
+//
+// Storage (structure of arrays, row pitch padded to 32 floats):
+//   f: 8 planes, f_1 .. f_8 (plane p holds direction p + 1).  f_0 is never stored: it
+//      enters neither P (Eq. 3-9a sums i = 1..8), nor grad P (c_0 = 0), nor any other f_i.
+//   g: 9 planes, g_0 .. g_8.
+#pragma once
+
+#include <cstdint>
+
+#include "lbm2p.h"
+
+namespace lbm2p_dev {
+
+constexpr int kBlock = 256;   // threads per block of every lattice kernel
+constexpr int kMaxWells = LBM2P_MAX_WELLS;
+
+enum : int { BC_PERIODIC = 0, BC_NOFLUX = 1, BC_DIRICHLET = 2 };
+enum : int { MOB_QUADRATIC = 0, MOB_DECOUPLED = 1, MOB_RATIONAL = 2 };
+
+__host__ __device__ constexpr int cx(int i)
+{
+    return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+}
+__host__ __device__ constexpr int cy(int i)
+{
+    return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+}
+__host__ __device__ constexpr int opp(int i)
+{
+    return i == 0 ? 0 : (i <= 4 ? ((i + 1) % 4) + 1 : ((i - 5 + 2) % 4) + 5);
+}
+__host__ __device__ constexpr float wgt(int i)
+{
+    return i == 0 ? 4.0f / 9.0f : (i <= 4 ? 1.0f / 9.0f : 1.0f / 36.0f);
+}
+
+static_assert(opp(1) == 3 && opp(2) == 4 && opp(3) == 1 && opp(4) == 2, "axis opposites");
+static_assert(opp(5) == 7 && opp(6) == 8 && opp(7) == 5 && opp(8) == 6, "diagonal opposites");
+static_assert(cx(5) == 1 && cy(5) == 1 && cx(7) == -1 && cy(7) == -1, "diagonals");
+
+// Geometry of one lattice.
+struct Geom {
+    int nx, ny, pitch;   // pitch in floats
+    int tiles_x;         // ceil(nx / kBlock)
+    int ntiles;          // tiles_x * ny
+    int bc[4];           // XMIN, XMAX, YMIN, YMAX
+};
+
+// Physical coefficients, already folded into lattice units by the host.
+struct Model {
+    int mobility;
+    float inv_mu_w, inv_mu_n;
+    float phi, inv_phi;
+    float s3;            // tau_f = 1/2 + s3 * D_p          (3 s)
+    float fs_scale;      // F~_s = fs_scale * F_s          (dt)
+    float inv_tau_g;     // 1 / tau_g
+    float src_g;         // 1 - 1/(2 tau_g)
+    float gam_c;         // gamma~ = -gam_c * lambda_w K   (3 dt / dx^2)
+    float inv_dx;
+    float Gam[9];        // g_i^eq / S (Eq. 3-4)
+};
+
+// Sparse point wells, rates already divided by dx^2.
+struct Wells {
+    int n;
+    int idx[kMaxWells];      // j * pitch + i
+    float fp[kMaxWells];     // pressure source in lattice units (+- s q)
+    float qs[kMaxWells];     // dt q / dx^2 (saturation source magnitude)
+    int producer[kMaxWells];
+};
+
+struct PressureArgs {
+    const float *fin[8];
+    float *fout[8];
+    const float *inv_tau;
+    const float *Fp;         // dense F~_p plane (lattice units) or nullptr
+    float *Pio;              // pressure plane written (WRITE_P) / read (CHECK)
+    double *partials;        // CHECK: 4 doubles per block
+    const float *shift;      // CHECK: constant subtracted from P before squaring
+    const float *Pb[4];      // Dirichlet traces (device FP32) or nullptr
+    Geom g;
+    Wells w;
+};
+
+struct RefreshArgs {        // stream g, S^n, 1/tau_f
+    const float *gin[9];
+    const float *K;
+    const float *Fs;         // dense F~_s plane or nullptr
+    float *inv_tau;
+    const float *Sb[4];
+    Geom g;
+    Model m;
+    Wells w;
+};
+
+struct SaturationArgs {     // stream f and g, grad P, collide g
+    const float *fin[8];
+    const float *gin[9];
+    float *gout[9];
+    const float *K;
+    const float *inv_tau;
+    const float *Fs;
+    float *S;                // S^n written here
+    const float *Pb[4];
+    const float *Sb[4];
+    Geom g;
+    Model m;
+    Wells w;
+};
+
+struct InitGArgs {          // Eqs. gini, gneq and the t = 0 collision
+    const float *fin[8];
+    float *gout[9];
+    const float *K;
+    const float *inv_tau;
+    const float *Fs;
+    const float *S0;         // initial saturation (read at the node and its neighbours)
+    float *S;                // out: S(t=0) from the initial g
+    const float *Pb[4];
+    const float *Sb[4];
+    Geom g;
+    Model m;
+    Wells w;
+};
+
+struct FieldsArgs {         // P, S, u into compact [ny][nx] outputs
+    const float *fin[8];
+    const float *inv_tau;
+    const float *K;
+    const float *S;
+    const float *Pb[4];
+    float *P_out, *S_out, *ux_out, *uy_out;   // any may be nullptr
+    Geom g;
+    Model m;
+};
+
+struct ResidualOut {        // written by the finalize kernel
+    double r;
+    double mean_P;
+    double sums[4];
+};
+
+}  // namespace lbm2p_dev
+
+// Launchers implemented in kernels.cu (all asynchronous on `stream`).
+namespace lbm2p_launch {
+using namespace lbm2p_dev;
+int max_blocks_per_sm_pressure();
+void pressure_sweep(const PressureArgs &a, bool check, bool write_p, int grid, void *stream);
+void residual_finalize(const double *partials, int nparts, long long nnodes, float *shift,
+                       ResidualOut *out, void *stream);
+void refresh(const RefreshArgs &a, int grid, void *stream);
+void saturation(const SaturationArgs &a, int grid, void *stream);
+void init_g(const InitGArgs &a, int grid, void *stream);
+void fill_f_eq(float *const fout[8], const float *P0, Geom g, int grid, void *stream);
+void tau_from_S(float *inv_tau, const float *S, const float *K, Geom g, Model m, int grid,
+                void *stream);
+void fields(const FieldsArgs &a, int grid, void *stream);
+void sum_compact(const float *x, long long n, double *partials, int grid, void *stream);
+void finalize_mean(const double *partials, int nparts, long long n, double *mean, void *stream);
+void subtract_mean(float *x, long long n, const double *mean, int grid, void *stream);
+}  // namespace lbm2p_launch

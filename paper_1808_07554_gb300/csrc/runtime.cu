@@ -1,0 +1,894 @@
+// Host runtime of the lbm2p C ABI: parameter checks, device memory, the physical-step
+// driver and the pressure sub-iteration control (Sec. 3).  Every lattice operation runs
+// in the kernels of kernels.cu; this file only validates, uploads, launches and reads back.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lbm2p.h"
+#include "lbm2p_device.cuh"
+
+using namespace lbm2p_dev;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct Alloc {
+    void *ptr;
+    size_t bytes;
+};
+
+}  // namespace
+
+struct lbm2p {
+    lbm2p_params p{};
+    int nx = 0, ny = 0, pitch = 0;
+    long long plane = 0;       // floats per plane
+    long long nnodes = 0;
+    Geom geom{};
+    Model model{};
+    Wells wells{};
+    double s = 0, tau_g = 0, D_ref = 0;
+    int grid = 0;              // blocks of every grid-stride lattice launch
+    void *stream = nullptr;
+    std::vector<Alloc> allocs;
+    float *fbuf[2][8] = {};
+    float *gbuf[2][9] = {};
+    float *inv_tau = nullptr, *K = nullptr, *S = nullptr, *Pio = nullptr, *tmp = nullptr;
+    float *Fp = nullptr, *Fs = nullptr;
+    float *Pb[4] = {}, *Sb[4] = {};
+    double *partials = nullptr, *mean = nullptr;
+    float *shift = nullptr;
+    ResidualOut *res = nullptr;
+    ResidualOut *res_host = nullptr;   // pinned
+    float *stage = nullptr;            // compact [ny][nx] device staging plane
+    int cur_f = 0, cur_g = 0;          // buffer holding the current post-collision state
+    long long launches = 0, sweeps = 0;
+    bool timing = false;
+    cudaEvent_t ev_step0 = nullptr, ev_step1 = nullptr, ev_sw0 = nullptr, ev_sw1 = nullptr;
+    std::string err;
+};
+
+namespace {
+
+lbm2p_status fail(lbm2p *h, lbm2p_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h)
+        h->err = buf;
+    else
+        g_create_error = buf;
+    return st;
+}
+
+#define CUDA_TRY(h, call)                                                                    \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail((h), LBM2P_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));   \
+    } while (0)
+
+lbm2p_status launched(lbm2p *h, const char *what)
+{
+    h->launches += 1;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return fail(h, LBM2P_ECUDA, "launch of %s failed: %s", what, cudaGetErrorString(e));
+    return LBM2P_OK;
+}
+
+#define LAUNCHED(h, what)                                                                    \
+    do {                                                                                     \
+        lbm2p_status st_ = launched((h), (what));                                            \
+        if (st_ != LBM2P_OK)                                                                 \
+            return st_;                                                                      \
+    } while (0)
+
+void *dev_alloc(lbm2p *h, size_t bytes)
+{
+    void *ptr = nullptr;
+    if (h->p.alloc) {
+        ptr = h->p.alloc(bytes, h->p.alloc_ctx);
+    } else if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        ptr = nullptr;
+    }
+    if (ptr)
+        h->allocs.push_back({ptr, bytes});
+    return ptr;
+}
+
+void free_all(lbm2p *h)
+{
+    for (auto &a : h->allocs) {
+        if (h->p.alloc && h->p.release)
+            h->p.release(a.ptr, a.bytes, h->p.alloc_ctx);
+        else if (!h->p.alloc)
+            cudaFree(a.ptr);
+    }
+    h->allocs.clear();
+    if (h->res_host)
+        cudaFreeHost(h->res_host);
+    h->res_host = nullptr;
+    for (cudaEvent_t *e : {&h->ev_step0, &h->ev_step1, &h->ev_sw0, &h->ev_sw1})
+        if (*e) {
+            cudaEventDestroy(*e);
+            *e = nullptr;
+        }
+}
+
+// lambda_t at S for the model (host, FP64; used for D_ref only)
+double lambda_t_host(const lbm2p_params &p, double S)
+{
+    if (p.mobility == LBM2P_MOB_QUADRATIC)
+        return S * S / p.mu_w + (1.0 - S) * (1.0 - S) / p.mu_n;
+    if (p.mobility == LBM2P_MOB_DECOUPLED)
+        return 1.0 / p.mu_w;
+    return 1.0 / (0.5 - 0.2 * S);
+}
+
+int trace_len(const lbm2p *h, int side) { return side < 2 ? 2 * h->ny + 1 : 2 * h->nx + 1; }
+
+// host FP64 [ny][nx] -> device pitched FP32 plane, with a scale factor
+lbm2p_status upload_plane(lbm2p *h, float *dst, const double *src, double scale)
+{
+    std::vector<float> tmp((size_t)h->nnodes);
+    for (long long a = 0; a < h->nnodes; ++a)
+        tmp[(size_t)a] = (float)(scale * src[a]);
+    CUDA_TRY(h, cudaMemcpy2DAsync(dst, (size_t)h->pitch * sizeof(float), tmp.data(),
+                                  (size_t)h->nx * sizeof(float), (size_t)h->nx * sizeof(float),
+                                  (size_t)h->ny, cudaMemcpyHostToDevice, (cudaStream_t)h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize((cudaStream_t)h->stream));
+    return LBM2P_OK;
+}
+
+lbm2p_status upload_trace(lbm2p *h, float *dst, const double *src, int n)
+{
+    std::vector<float> tmp((size_t)n, 0.0f);
+    if (src)
+        for (int k = 0; k < n; ++k)
+            tmp[(size_t)k] = (float)src[k];
+    CUDA_TRY(h, cudaMemcpyAsync(dst, tmp.data(), (size_t)n * sizeof(float), cudaMemcpyHostToDevice,
+                                (cudaStream_t)h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize((cudaStream_t)h->stream));
+    return LBM2P_OK;
+}
+
+// ---- kernel argument blocks for the current ping-pong state -----------------------------
+PressureArgs pressure_args(lbm2p *h, int src)
+{
+    PressureArgs a{};
+    for (int i = 0; i < 8; ++i) {
+        a.fin[i] = h->fbuf[src][i];
+        a.fout[i] = h->fbuf[1 - src][i];
+    }
+    a.inv_tau = h->inv_tau;
+    a.Fp = h->Fp;
+    a.Pio = h->Pio;
+    a.partials = h->partials;
+    a.shift = h->shift;
+    for (int s = 0; s < 4; ++s)
+        a.Pb[s] = h->Pb[s];
+    a.g = h->geom;
+    a.w = h->wells;
+    return a;
+}
+
+// ---- the pressure sub-iteration (Sec. 3) ------------------------------------------------
+// replay >= 0: exactly that many sweeps; replay < 0: until r <= tol at a check or the cap.
+lbm2p_status pressure_solve(lbm2p *h, int replay, int *k_out, double *r_out, float *ms_out)
+{
+    cudaStream_t st = (cudaStream_t)h->stream;
+    const int m = h->p.check_every;
+    const int cap = h->p.max_sub_iters;
+    double r = std::nan("");
+    float ms_total = 0.0f;
+    lbm2p_status status = LBM2P_OK;
+    int k = 0;
+    auto is_check = [&](int kk) {
+        if (replay >= 0)
+            return kk == replay;
+        return (kk % m == 0) || kk >= cap;
+    };
+    // run sweeps k+1 .. upto; the last one evaluates the residual when asked
+    auto run_batch = [&](int upto) -> lbm2p_status {
+        if (h->timing)
+            CUDA_TRY(h, cudaEventRecord(h->ev_sw0, st));
+        for (int kk = k + 1; kk <= upto; ++kk) {
+            const bool check = is_check(kk) && kk >= 2;
+            const bool write_p = is_check(kk + 1) && kk + 1 >= 2;
+            PressureArgs a = pressure_args(h, h->cur_f);
+            lbm2p_launch::pressure_sweep(a, check, write_p, h->grid, h->stream);
+            LAUNCHED(h, "pressure sweep");
+            h->cur_f = 1 - h->cur_f;
+            h->sweeps += 1;
+        }
+        if (h->timing)
+            CUDA_TRY(h, cudaEventRecord(h->ev_sw1, st));
+        k = upto;
+        return LBM2P_OK;
+    };
+    auto read_residual = [&]() -> lbm2p_status {
+        lbm2p_launch::residual_finalize(h->partials, h->grid, h->nnodes, h->shift, h->res,
+                                        h->stream);
+        LAUNCHED(h, "residual finalize");
+        CUDA_TRY(h, cudaMemcpyAsync(h->res_host, h->res, sizeof(ResidualOut),
+                                    cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(h, cudaStreamSynchronize(st));
+        r = h->res_host->r;
+        return LBM2P_OK;
+    };
+    auto add_time = [&]() -> lbm2p_status {
+        if (h->timing) {
+            float ms = 0.0f;
+            CUDA_TRY(h, cudaEventSynchronize(h->ev_sw1));
+            CUDA_TRY(h, cudaEventElapsedTime(&ms, h->ev_sw0, h->ev_sw1));
+            ms_total += ms;
+        }
+        return LBM2P_OK;
+    };
+    lbm2p_status e;
+    if (replay >= 0) {
+        if (replay > 0) {
+            if ((e = run_batch(replay)) != LBM2P_OK)
+                return e;
+            if ((e = add_time()) != LBM2P_OK)
+                return e;
+            if (replay >= 2) {
+                if ((e = read_residual()) != LBM2P_OK)
+                    return e;
+                if (std::isnan(r))
+                    status = LBM2P_ENONFINITE;
+            }
+        }
+    } else {
+        for (;;) {
+            int next = (k / m + 1) * m;
+            if (next > cap)
+                next = cap;
+            if (next < 1)
+                next = 1;
+            if ((e = run_batch(next)) != LBM2P_OK)
+                return e;
+            if ((e = add_time()) != LBM2P_OK)
+                return e;
+            if (k >= 2) {
+                if ((e = read_residual()) != LBM2P_OK)
+                    return e;
+                if (std::isnan(r)) {
+                    status = LBM2P_ENONFINITE;
+                    break;
+                }
+                if (r <= h->p.tol)
+                    break;
+            }
+            if (k >= cap) {
+                status = LBM2P_ENOTCONVERGED;
+                break;
+            }
+        }
+    }
+    if (k_out)
+        *k_out = k;
+    if (r_out)
+        *r_out = r;
+    if (ms_out)
+        *ms_out = h->timing ? ms_total : -1.0f;
+    if (status == LBM2P_ENONFINITE)
+        return fail(h, status, "pressure residual is not finite after %d sweeps", k);
+    if (status == LBM2P_ENOTCONVERGED)
+        return fail(h, status, "pressure residual %.3e above tol %.3e after %d sweeps", r,
+                    h->p.tol, k);
+    return LBM2P_OK;
+}
+
+RefreshArgs refresh_args(lbm2p *h)
+{
+    RefreshArgs a{};
+    for (int i = 0; i < 9; ++i)
+        a.gin[i] = h->gbuf[h->cur_g][i];
+    a.K = h->K;
+    a.Fs = h->Fs;
+    a.inv_tau = h->inv_tau;
+    for (int s = 0; s < 4; ++s)
+        a.Sb[s] = h->Sb[s];
+    a.g = h->geom;
+    a.m = h->model;
+    a.w = h->wells;
+    return a;
+}
+
+SaturationArgs saturation_args(lbm2p *h)
+{
+    SaturationArgs a{};
+    for (int i = 0; i < 8; ++i)
+        a.fin[i] = h->fbuf[h->cur_f][i];
+    for (int i = 0; i < 9; ++i) {
+        a.gin[i] = h->gbuf[h->cur_g][i];
+        a.gout[i] = h->gbuf[1 - h->cur_g][i];
+    }
+    a.K = h->K;
+    a.inv_tau = h->inv_tau;
+    a.Fs = h->Fs;
+    a.S = h->S;
+    for (int s = 0; s < 4; ++s) {
+        a.Pb[s] = h->Pb[s];
+        a.Sb[s] = h->Sb[s];
+    }
+    a.g = h->geom;
+    a.m = h->model;
+    a.w = h->wells;
+    return a;
+}
+
+lbm2p_status one_step(lbm2p *h, int replay, lbm2p_step_stats *stats)
+{
+    cudaStream_t st = (cudaStream_t)h->stream;
+    if (h->timing)
+        CUDA_TRY(h, cudaEventRecord(h->ev_step0, st));
+    // a1: stream g, S^n, tau_f
+    lbm2p_launch::refresh(refresh_args(h), h->grid, h->stream);
+    LAUNCHED(h, "refresh");
+    // a2/a3: pressure sub-iteration
+    int k = 0;
+    double r = std::nan("");
+    float sw_ms = -1.0f;
+    lbm2p_status ps = pressure_solve(h, replay, &k, &r, &sw_ms);
+    if (ps != LBM2P_OK && ps != LBM2P_ENOTCONVERGED) {
+        if (stats) {
+            stats->sub_iters = k;
+            stats->status = ps;
+            stats->residual = r;
+            stats->sweep_ms = sw_ms;
+            stats->step_ms = -1.0f;
+        }
+        return ps;
+    }
+    // a4/a5: grad P and the saturation update
+    lbm2p_launch::saturation(saturation_args(h), h->grid, h->stream);
+    LAUNCHED(h, "saturation");
+    h->cur_g = 1 - h->cur_g;
+    float step_ms = -1.0f;
+    if (h->timing) {
+        CUDA_TRY(h, cudaEventRecord(h->ev_step1, st));
+        CUDA_TRY(h, cudaEventSynchronize(h->ev_step1));
+        CUDA_TRY(h, cudaEventElapsedTime(&step_ms, h->ev_step0, h->ev_step1));
+    }
+    if (stats) {
+        stats->sub_iters = k;
+        stats->status = ps;
+        stats->residual = r;
+        stats->sweep_ms = sw_ms;
+        stats->step_ms = step_ms;
+    }
+    return ps;
+}
+
+lbm2p_status check_params(const lbm2p_params *p, const lbm2p_inputs *in)
+{
+    if (!p || !in)
+        return fail(nullptr, LBM2P_EINVAL, "params and inputs are required");
+    if (p->nx < 1 || p->ny < 1)
+        return fail(nullptr, LBM2P_EINVAL, "nx, ny must be >= 1 (got %d, %d)", p->nx, p->ny);
+    long long pitch = ((long long)p->nx + 31) / 32 * 32;
+    if (pitch * p->ny >= (1LL << 31) - 1024)
+        return fail(nullptr, LBM2P_EINVAL, "lattice %d x %d exceeds the 2^31 plane limit", p->nx, p->ny);
+    if (!(p->dx > 0) || !(p->dt > 0) || !std::isfinite(p->dx) || !std::isfinite(p->dt))
+        return fail(nullptr, LBM2P_EINVAL, "dx and dt must be positive");
+    if (!(p->phi > 0) || !(p->beta > 0))
+        return fail(nullptr, LBM2P_EINVAL, "phi and beta must be positive");
+    if (!(p->D_s > 0))
+        return fail(nullptr, LBM2P_EINVAL, "D_s must be positive (tau_g > 1/2)");
+    if (p->mobility == LBM2P_MOB_QUADRATIC) {
+        if (!(p->mu_w > 0) || !(p->mu_n > 0))
+            return fail(nullptr, LBM2P_EINVAL, "quadratic mobility needs mu_w, mu_n > 0");
+    } else if (p->mobility == LBM2P_MOB_DECOUPLED) {
+        if (!(p->mu_w > 0))
+            return fail(nullptr, LBM2P_EINVAL, "decoupled mobility needs mu_w > 0");
+    } else if (p->mobility != LBM2P_MOB_RATIONAL) {
+        return fail(nullptr, LBM2P_EINVAL, "unknown mobility law %d", p->mobility);
+    }
+    if (p->tau_mode == LBM2P_TAU_REFERENCE) {
+        if (!(p->tau_p > 0.5))
+            return fail(nullptr, LBM2P_EINVAL, "tau_p must exceed 1/2");
+    } else if (p->tau_mode != LBM2P_TAU_PHYSICAL_DT) {
+        return fail(nullptr, LBM2P_EINVAL, "unknown tau mode %d", p->tau_mode);
+    }
+    if (!(p->tol >= 0) || p->max_sub_iters < 1 || p->check_every < 1)
+        return fail(nullptr, LBM2P_EINVAL, "need tol >= 0, max_sub_iters >= 1, check_every >= 1");
+    for (int s = 0; s < 4; ++s)
+        if (p->bc[s] < 0 || p->bc[s] > 2)
+            return fail(nullptr, LBM2P_EINVAL, "unknown wall kind %d on side %d", p->bc[s], s);
+    if ((p->bc[0] == LBM2P_BC_PERIODIC) != (p->bc[1] == LBM2P_BC_PERIODIC) ||
+        (p->bc[2] == LBM2P_BC_PERIODIC) != (p->bc[3] == LBM2P_BC_PERIODIC))
+        return fail(nullptr, LBM2P_EINVAL, "a periodic side must be paired with its opposite");
+    if ((p->bc[0] == LBM2P_BC_DIRICHLET || p->bc[1] == LBM2P_BC_DIRICHLET) && p->nx < 3)
+        return fail(nullptr, LBM2P_EINVAL, "Dirichlet x-sides need nx >= 3");
+    if ((p->bc[2] == LBM2P_BC_DIRICHLET || p->bc[3] == LBM2P_BC_DIRICHLET) && p->ny < 3)
+        return fail(nullptr, LBM2P_EINVAL, "Dirichlet y-sides need ny >= 3");
+    if (p->storage == LBM2P_STORE_FP16_DEV)
+        return fail(nullptr, LBM2P_ENOTIMPL, "FP16 deviation storage is not available");
+    if (p->storage != LBM2P_STORE_FP32)
+        return fail(nullptr, LBM2P_EINVAL, "unknown storage %d", p->storage);
+    if (!in->K || !in->S0)
+        return fail(nullptr, LBM2P_EINVAL, "K and S0 are required");
+    if (in->n_wells < 0 || in->n_wells > LBM2P_MAX_WELLS || (in->n_wells > 0 && !in->wells))
+        return fail(nullptr, LBM2P_EINVAL, "0..%d wells supported", LBM2P_MAX_WELLS);
+    for (int m = 0; m < in->n_wells; ++m) {
+        const lbm2p_well &w = in->wells[m];
+        if (w.i < 0 || w.i >= p->nx || w.j < 0 || w.j >= p->ny || !(w.q >= 0) || !std::isfinite(w.q))
+            return fail(nullptr, LBM2P_EINVAL, "well %d out of range or negative rate", m);
+    }
+    const long long n = (long long)p->nx * p->ny;
+    for (long long a = 0; a < n; ++a) {
+        if (!(in->K[a] > 0) || !std::isfinite(in->K[a]))
+            return fail(nullptr, LBM2P_EINVAL, "K must be positive and finite (node %lld)", a);
+        if (!std::isfinite(in->S0[a]))
+            return fail(nullptr, LBM2P_EINVAL, "S0 must be finite (node %lld)", a);
+    }
+    if (in->init_replay && *in->init_replay < 0)
+        return fail(nullptr, LBM2P_EINVAL, "init_replay must be >= 0");
+    return LBM2P_OK;
+}
+
+lbm2p_status build(lbm2p *h, const lbm2p_inputs *in, lbm2p_step_stats *init_stats)
+{
+    const lbm2p_params &p = h->p;
+    h->nx = p.nx;
+    h->ny = p.ny;
+    h->pitch = (p.nx + 31) / 32 * 32;
+    h->plane = (long long)h->pitch * p.ny;
+    h->nnodes = (long long)p.nx * p.ny;
+    h->stream = p.stream;
+    Geom &g = h->geom;
+    g.nx = p.nx;
+    g.ny = p.ny;
+    g.pitch = h->pitch;
+    g.tiles_x = (p.nx + kBlock - 1) / kBlock;
+    g.ntiles = g.tiles_x * p.ny;
+    for (int s = 0; s < 4; ++s)
+        g.bc[s] = p.bc[s];
+
+    // pseudo-time scale s and the relaxation times (Eq. 3-11)
+    h->tau_g = 0.5 + 3.0 * p.D_s * p.dt / (p.beta * p.dx * p.dx);
+    if (p.tau_mode == LBM2P_TAU_REFERENCE) {
+        double D = p.D_ref;
+        if (!(D > 0)) {
+            double acc = 0.0;
+            for (long long a = 0; a < h->nnodes; ++a)
+                acc += std::log(in->K[a] * lambda_t_host(p, in->S0[a]));
+            D = std::exp(acc / (double)h->nnodes);
+        }
+        if (!(D > 0) || !std::isfinite(D))
+            return fail(h, LBM2P_EINVAL, "reference diffusivity is not positive");
+        h->D_ref = D;
+        h->s = (p.tau_p - 0.5) / (3.0 * D);
+    } else {
+        h->s = p.dt / (p.dx * p.dx);
+    }
+    Model &m = h->model;
+    m.mobility = p.mobility;
+    m.inv_mu_w = (float)(1.0 / p.mu_w);
+    m.inv_mu_n = p.mobility == LBM2P_MOB_QUADRATIC ? (float)(1.0 / p.mu_n) : 0.0f;
+    m.phi = (float)p.phi;
+    m.inv_phi = (float)(1.0 / p.phi);
+    m.s3 = (float)(3.0 * h->s);
+    m.fs_scale = (float)p.dt;
+    m.inv_tau_g = (float)(1.0 / h->tau_g);
+    m.src_g = (float)(1.0 - 0.5 / h->tau_g);
+    m.gam_c = (float)(3.0 * p.dt / (p.dx * p.dx));
+    m.inv_dx = (float)(1.0 / p.dx);
+    // Eq. 3-4: g_i^eq / S = w_i [phi + (beta - phi)(|c_i|^2 - 2 c_s^2) / (2 c_s^2)], c_s^2 = 1/3
+    for (int i = 0; i < 9; ++i) {
+        const double w = i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+        const double c2 = (double)(cx(i) * cx(i) + cy(i) * cy(i));
+        m.Gam[i] = (float)(w * (p.phi + (p.beta - p.phi) * (c2 - 2.0 / 3.0) / (2.0 / 3.0)));
+    }
+    Wells &w = h->wells;
+    w.n = in->n_wells;
+    for (int k = 0; k < in->n_wells; ++k) {
+        const lbm2p_well &wl = in->wells[k];
+        w.idx[k] = wl.j * h->pitch + wl.i;
+        w.producer[k] = wl.is_producer ? 1 : 0;
+        // F~_p = s dx^2 * (+-q / dx^2);  dt F_s magnitude = dt q / dx^2
+        w.fp[k] = (float)(wl.is_producer ? -h->s * wl.q : h->s * wl.q);
+        w.qs[k] = (float)(p.dt * wl.q / (p.dx * p.dx));
+    }
+
+    // device memory
+    int dev = 0, sms = 0;
+    CUDA_TRY(h, cudaGetDevice(&dev));
+    CUDA_TRY(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int per_sm = lbm2p_launch::max_blocks_per_sm_pressure();
+    long long grid = (long long)sms * per_sm;
+    if (grid > g.ntiles)
+        grid = g.ntiles;
+    h->grid = (int)(grid > 0 ? grid : 1);
+    const size_t pb = (size_t)h->plane * sizeof(float);
+    auto plane_alloc = [&](float **dst) -> bool {
+        *dst = (float *)dev_alloc(h, pb);
+        return *dst != nullptr;
+    };
+    bool ok = true;
+    for (int b = 0; b < 2; ++b) {
+        for (int i = 0; i < 8; ++i)
+            ok = ok && plane_alloc(&h->fbuf[b][i]);
+        for (int i = 0; i < 9; ++i)
+            ok = ok && plane_alloc(&h->gbuf[b][i]);
+    }
+    ok = ok && plane_alloc(&h->inv_tau) && plane_alloc(&h->K) && plane_alloc(&h->S) &&
+         plane_alloc(&h->Pio) && plane_alloc(&h->tmp);
+    if (in->Fp)
+        ok = ok && plane_alloc(&h->Fp);
+    if (in->Fs)
+        ok = ok && plane_alloc(&h->Fs);
+    for (int s = 0; s < 4; ++s) {
+        if (p.bc[s] == LBM2P_BC_DIRICHLET) {
+            h->Pb[s] = (float *)dev_alloc(h, (size_t)trace_len(h, s) * sizeof(float));
+            h->Sb[s] = (float *)dev_alloc(h, (size_t)trace_len(h, s) * sizeof(float));
+            ok = ok && h->Pb[s] && h->Sb[s];
+        }
+    }
+    h->partials = (double *)dev_alloc(h, (size_t)h->grid * 4 * sizeof(double));
+    h->mean = (double *)dev_alloc(h, 64);
+    h->shift = (float *)dev_alloc(h, 64);
+    h->res = (ResidualOut *)dev_alloc(h, sizeof(ResidualOut));
+    h->stage = (float *)dev_alloc(h, (size_t)h->nnodes * sizeof(float) * 4);
+    ok = ok && h->partials && h->mean && h->shift && h->res && h->stage;
+    if (!ok)
+        return fail(h, LBM2P_ENOMEM, "device allocation of %.1f MiB failed",
+                    (double)pb * 45 / (1 << 20));
+    CUDA_TRY(h, cudaMallocHost((void **)&h->res_host, sizeof(ResidualOut)));
+    for (cudaEvent_t *e : {&h->ev_step0, &h->ev_step1, &h->ev_sw0, &h->ev_sw1})
+        CUDA_TRY(h, cudaEventCreate(e));
+    cudaStream_t st = (cudaStream_t)h->stream;
+    for (auto &a : h->allocs)
+        CUDA_TRY(h, cudaMemsetAsync(a.ptr, 0, a.bytes, st));
+
+    // inputs
+    lbm2p_status e;
+    if ((e = upload_plane(h, h->K, in->K, 1.0)) != LBM2P_OK)
+        return e;
+    if (in->Fp && (e = upload_plane(h, h->Fp, in->Fp, h->s * p.dx * p.dx)) != LBM2P_OK)
+        return e;
+    if (in->Fs && (e = upload_plane(h, h->Fs, in->Fs, p.dt)) != LBM2P_OK)
+        return e;
+    for (int s = 0; s < 4; ++s) {
+        if (p.bc[s] == LBM2P_BC_DIRICHLET) {
+            if ((e = upload_trace(h, h->Pb[s], in->P_b[s], trace_len(h, s))) != LBM2P_OK)
+                return e;
+            if ((e = upload_trace(h, h->Sb[s], in->S_b[s], trace_len(h, s))) != LBM2P_OK)
+                return e;
+        }
+    }
+    // a6: f = f^eq(P0), tau_f from S0, the t = 0 pressure solve, then g(0) and its collision
+    if ((e = upload_plane(h, h->tmp, in->S0, 1.0)) != LBM2P_OK)   // tmp holds S0
+        return e;
+    const float *P0dev = nullptr;
+    if (in->P0) {
+        if ((e = upload_plane(h, h->Pio, in->P0, 1.0)) != LBM2P_OK)
+            return e;
+        P0dev = h->Pio;
+    }
+    h->cur_f = 0;
+    h->cur_g = 0;
+    lbm2p_launch::fill_f_eq(h->fbuf[0], P0dev, g, h->grid, h->stream);
+    LAUNCHED(h, "fill f_eq");
+    lbm2p_launch::tau_from_S(h->inv_tau, h->tmp, h->K, g, m, h->grid, h->stream);
+    LAUNCHED(h, "tau from S");
+    int k0 = 0;
+    double r0 = std::nan("");
+    float ms0 = -1.0f;
+    lbm2p_status ps = pressure_solve(h, in->init_replay ? *in->init_replay : -1, &k0, &r0, &ms0);
+    if (init_stats) {
+        init_stats->sub_iters = k0;
+        init_stats->status = ps;
+        init_stats->residual = r0;
+        init_stats->sweep_ms = ms0;
+        init_stats->step_ms = -1.0f;
+    }
+    if (ps != LBM2P_OK && ps != LBM2P_ENOTCONVERGED)
+        return ps;
+    InitGArgs a{};
+    for (int i = 0; i < 8; ++i)
+        a.fin[i] = h->fbuf[h->cur_f][i];
+    for (int i = 0; i < 9; ++i)
+        a.gout[i] = h->gbuf[0][i];
+    a.K = h->K;
+    a.inv_tau = h->inv_tau;
+    a.Fs = h->Fs;
+    a.S0 = h->tmp;
+    a.S = h->S;
+    for (int s = 0; s < 4; ++s) {
+        a.Pb[s] = h->Pb[s];
+        a.Sb[s] = h->Sb[s];
+    }
+    a.g = g;
+    a.m = m;
+    a.w = w;
+    lbm2p_launch::init_g(a, h->grid, h->stream);
+    LAUNCHED(h, "init g");
+    h->cur_g = 0;
+    CUDA_TRY(h, cudaStreamSynchronize(st));
+    return ps;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm2p_abi_version(void) { return LBM2P_ABI_VERSION; }
+
+void lbm2p_default_params(lbm2p_params *p)
+{
+    if (!p)
+        return;
+    std::memset(p, 0, sizeof *p);
+    p->nx = p->ny = 64;
+    p->dx = 1.0 / 64;
+    p->dt = 4.0 * p->dx * p->dx;
+    p->phi = 0.2;
+    p->beta = 0.4;
+    p->mobility = LBM2P_MOB_QUADRATIC;
+    p->mu_w = 1.0;
+    p->mu_n = 2.0;
+    p->D_s = 0.01;
+    p->tau_mode = LBM2P_TAU_REFERENCE;
+    p->tau_p = 1.0;
+    p->D_ref = 0.0;
+    p->tol = 1e-8;
+    p->max_sub_iters = 10000000;
+    p->check_every = 10;
+    for (int s = 0; s < 4; ++s)
+        p->bc[s] = LBM2P_BC_NOFLUX;
+    p->storage = LBM2P_STORE_FP32;
+}
+
+lbm2p_status lbm2p_create(lbm2p **out, const lbm2p_params *p, const lbm2p_inputs *in,
+                          lbm2p_step_stats *init_stats)
+{
+    if (!out)
+        return fail(nullptr, LBM2P_EINVAL, "out must not be NULL");
+    *out = nullptr;
+    lbm2p_status st = check_params(p, in);
+    if (st != LBM2P_OK)
+        return st;
+    lbm2p *h = new (std::nothrow) lbm2p();
+    if (!h)
+        return fail(nullptr, LBM2P_ENOMEM, "host allocation failed");
+    h->p = *p;
+    try {
+        st = build(h, in, init_stats);
+    } catch (const std::bad_alloc &) {
+        st = fail(h, LBM2P_ENOMEM, "host allocation failed");
+    }
+    if (st != LBM2P_OK && st != LBM2P_ENOTCONVERGED) {
+        g_create_error = h->err;
+        if (h->stream)
+            cudaStreamSynchronize((cudaStream_t)h->stream);
+        free_all(h);
+        delete h;
+        return st;
+    }
+    *out = h;
+    return st;
+}
+
+lbm2p_status lbm2p_set_sources(lbm2p *h, const double *Fp, const double *Fs)
+{
+    if (!h)
+        return fail(nullptr, LBM2P_EINVAL, "NULL handle");
+    if ((Fp && !h->Fp) || (Fs && !h->Fs))
+        return fail(h, LBM2P_EINVAL, "dense sources must be given at create to be replaced");
+    lbm2p_status e;
+    cudaStream_t st = (cudaStream_t)h->stream;
+    if (h->Fp) {
+        if (Fp) {
+            if ((e = upload_plane(h, h->Fp, Fp, h->s * h->p.dx * h->p.dx)) != LBM2P_OK)
+                return e;
+        } else {
+            CUDA_TRY(h, cudaMemsetAsync(h->Fp, 0, (size_t)h->plane * sizeof(float), st));
+        }
+    }
+    if (h->Fs) {
+        if (Fs) {
+            if ((e = upload_plane(h, h->Fs, Fs, h->p.dt)) != LBM2P_OK)
+                return e;
+        } else {
+            CUDA_TRY(h, cudaMemsetAsync(h->Fs, 0, (size_t)h->plane * sizeof(float), st));
+        }
+    }
+    return LBM2P_OK;
+}
+
+lbm2p_status lbm2p_set_dirichlet(lbm2p *h, int side, const double *P_b, const double *S_b)
+{
+    if (!h)
+        return fail(nullptr, LBM2P_EINVAL, "NULL handle");
+    if (side < 0 || side > 3 || h->p.bc[side] != LBM2P_BC_DIRICHLET)
+        return fail(h, LBM2P_EINVAL, "side %d is not a Dirichlet side", side);
+    lbm2p_status e;
+    if ((e = upload_trace(h, h->Pb[side], P_b, trace_len(h, side))) != LBM2P_OK)
+        return e;
+    return upload_trace(h, h->Sb[side], S_b, trace_len(h, side));
+}
+
+lbm2p_status lbm2p_step(lbm2p *h, int nsteps, const int *replay, lbm2p_step_stats *stats)
+{
+    if (!h)
+        return fail(nullptr, LBM2P_EINVAL, "NULL handle");
+    if (nsteps < 0)
+        return fail(h, LBM2P_EINVAL, "nsteps must be >= 0");
+    if (replay)
+        for (int s = 0; s < nsteps; ++s)
+            if (replay[s] < 0)
+                return fail(h, LBM2P_EINVAL, "replay counts must be >= 0");
+    lbm2p_status worst = LBM2P_OK;
+    for (int s = 0; s < nsteps; ++s) {
+        lbm2p_status st = one_step(h, replay ? replay[s] : -1, stats ? stats + s : nullptr);
+        if (st != LBM2P_OK && st != LBM2P_ENOTCONVERGED)
+            return st;
+        if (st != LBM2P_OK)
+            worst = st;
+    }
+    return worst;
+}
+
+lbm2p_status lbm2p_pressure_sweeps(lbm2p *h, int nsweeps, double *residual)
+{
+    if (!h)
+        return fail(nullptr, LBM2P_EINVAL, "NULL handle");
+    if (nsweeps < 0)
+        return fail(h, LBM2P_EINVAL, "nsweeps must be >= 0");
+    double r = std::nan("");
+    lbm2p_status st = pressure_solve(h, nsweeps, nullptr, &r, nullptr);
+    if (residual)
+        *residual = r;
+    return st;
+}
+
+static lbm2p_status run_fields(lbm2p *h, float *P, float *S, float *ux, float *uy, int on_device,
+                               int mean_free_P)
+{
+    if (!h)
+        return fail(nullptr, LBM2P_EINVAL, "NULL handle");
+    cudaStream_t st = (cudaStream_t)h->stream;
+    const long long n = h->nnodes;
+    float *outs[4] = {P, S, ux, uy};
+    float *dst[4] = {nullptr, nullptr, nullptr, nullptr};
+    for (int c = 0; c < 4; ++c)
+        if (outs[c])
+            dst[c] = on_device ? outs[c] : h->stage + (size_t)c * n;
+    FieldsArgs a{};
+    for (int i = 0; i < 8; ++i)
+        a.fin[i] = h->fbuf[h->cur_f][i];
+    a.inv_tau = h->inv_tau;
+    a.K = h->K;
+    a.S = h->S;
+    for (int s = 0; s < 4; ++s)
+        a.Pb[s] = h->Pb[s];
+    a.P_out = dst[0];
+    a.S_out = dst[1];
+    a.ux_out = dst[2];
+    a.uy_out = dst[3];
+    a.g = h->geom;
+    a.m = h->model;
+    lbm2p_launch::fields(a, h->grid, h->stream);
+    LAUNCHED(h, "fields");
+    if (P && mean_free_P) {
+        lbm2p_launch::sum_compact(dst[0], n, h->partials, h->grid, h->stream);
+        LAUNCHED(h, "sum");
+        lbm2p_launch::finalize_mean(h->partials, h->grid, n, h->mean, h->stream);
+        LAUNCHED(h, "mean");
+        lbm2p_launch::subtract_mean(dst[0], n, h->mean, h->grid, h->stream);
+        LAUNCHED(h, "subtract mean");
+    }
+    if (!on_device)
+        for (int c = 0; c < 4; ++c)
+            if (outs[c])
+                CUDA_TRY(h, cudaMemcpyAsync(outs[c], dst[c], (size_t)n * sizeof(float),
+                                            cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(h, cudaStreamSynchronize(st));
+    return LBM2P_OK;
+}
+
+lbm2p_status lbm2p_velocity(lbm2p *h, float *ux, float *uy, int on_device)
+{
+    return run_fields(h, nullptr, nullptr, ux, uy, on_device, 0);
+}
+
+lbm2p_status lbm2p_fields(lbm2p *h, float *P, float *S, int mean_free_P, int on_device)
+{
+    return run_fields(h, P, S, nullptr, nullptr, on_device, mean_free_P);
+}
+
+size_t lbm2p_state_count(const lbm2p *h)
+{
+    return h ? (size_t)19 * (size_t)h->nnodes : 0;
+}
+
+static lbm2p_status state_copy(lbm2p *h, float *buf, size_t count, int on_device, bool out)
+{
+    if (!h)
+        return fail(nullptr, LBM2P_EINVAL, "NULL handle");
+    if (!buf || count != lbm2p_state_count(h))
+        return fail(h, LBM2P_EINVAL, "state buffer must hold %zu floats", lbm2p_state_count(h));
+    cudaStream_t st = (cudaStream_t)h->stream;
+    float *planes[19];
+    for (int i = 0; i < 8; ++i)
+        planes[i] = h->fbuf[h->cur_f][i];
+    for (int i = 0; i < 9; ++i)
+        planes[8 + i] = h->gbuf[h->cur_g][i];
+    planes[17] = h->inv_tau;
+    planes[18] = h->S;
+    const size_t row = (size_t)h->nx * sizeof(float);
+    const size_t dpitch = (size_t)h->pitch * sizeof(float);
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice
+                                          : (out ? cudaMemcpyDeviceToHost : cudaMemcpyHostToDevice);
+    for (int c = 0; c < 19; ++c) {
+        float *hb = buf + (size_t)c * h->nnodes;
+        if (out)
+            CUDA_TRY(h, cudaMemcpy2DAsync(hb, row, planes[c], dpitch, row, (size_t)h->ny, kind, st));
+        else
+            CUDA_TRY(h, cudaMemcpy2DAsync(planes[c], dpitch, hb, row, row, (size_t)h->ny, kind, st));
+    }
+    CUDA_TRY(h, cudaStreamSynchronize(st));
+    return LBM2P_OK;
+}
+
+lbm2p_status lbm2p_get_state(lbm2p *h, float *buf, size_t count, int on_device)
+{
+    return state_copy(h, buf, count, on_device, true);
+}
+
+lbm2p_status lbm2p_set_state(lbm2p *h, const float *buf, size_t count, int on_device)
+{
+    return state_copy(h, const_cast<float *>(buf), count, on_device, false);
+}
+
+lbm2p_status lbm2p_set_timing(lbm2p *h, int enable)
+{
+    if (!h)
+        return fail(nullptr, LBM2P_EINVAL, "NULL handle");
+    h->timing = enable != 0;
+    return LBM2P_OK;
+}
+
+lbm2p_status lbm2p_counters(const lbm2p *h, long long *launches, long long *sweeps)
+{
+    if (!h)
+        return fail(nullptr, LBM2P_EINVAL, "NULL handle");
+    if (launches)
+        *launches = h->launches;
+    if (sweeps)
+        *sweeps = h->sweeps;
+    return LBM2P_OK;
+}
+
+const char *lbm2p_last_error(const lbm2p *h)
+{
+    return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+void lbm2p_destroy(lbm2p *h)
+{
+    if (!h)
+        return;
+    if (h->stream || true)
+        cudaStreamSynchronize((cudaStream_t)h->stream);
+    free_all(h);
+    delete h;
+}
+
+}  // extern "C"

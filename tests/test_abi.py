@@ -1,0 +1,102 @@
+"""The C ABI library: it builds for sm_103a, loads without a GPU, exports every function
+that include/lbm2p.h declares, and rejects bad parameters before touching the device."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1808_07554_gb300 import build
+    build.build()
+    import paper_1808_07554_gb300 as pkg
+    return pkg.load_library()
+
+
+def declared_functions():
+    names = []
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names += re.findall(r"\b(lbm2p_[a-z_0-9]+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_every_declared_function_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_abi_version_and_defaults(lib):
+    import paper_1808_07554_gb300 as pkg
+    assert pkg.lbm2p_abi_version() == 1
+    p = pkg.lbm2p_default_params()
+    assert (p.phi, p.beta, p.mu_w, p.mu_n, p.D_s, p.tau_p, p.tol) == (0.2, 0.4, 1.0, 2.0, 0.01, 1.0, 1e-8)
+    assert p.check_every == 10 and list(p.bc) == [1, 1, 1, 1]
+
+
+def _inputs(pkg, n, K=None, S0=None):
+    inp = pkg.lbm2p_inputs()
+    K = np.ones(n) if K is None else K
+    S0 = np.full(n, 0.2) if S0 is None else S0
+    inp.K = K.ctypes.data_as(C.POINTER(C.c_double))
+    inp.S0 = S0.ctypes.data_as(C.POINTER(C.c_double))
+    return inp, (K, S0)
+
+
+@pytest.mark.parametrize("field,value,status", [
+    ("nx", 0, 1), ("dx", -1.0, 1), ("phi", 0.0, 1), ("D_s", 0.0, 1), ("tau_p", 0.5, 1),
+    ("check_every", 0, 1), ("max_sub_iters", 0, 1), ("storage", 1, 6), ("mobility", 9, 1),
+    ("tol", -1.0, 1)])
+def test_bad_parameters_are_rejected_without_a_device(lib, field, value, status):
+    import paper_1808_07554_gb300 as pkg
+    p = pkg.lbm2p_default_params()
+    p.nx = p.ny = 8
+    setattr(p, field, value)
+    inp, keep = _inputs(pkg, 64)
+    h = C.c_void_p()
+    st = lib.lbm2p_create(C.byref(h), C.byref(p), C.byref(inp), None)
+    assert st == status and not h.value
+    assert len(pkg.lbm2p_last_error(None)) > 0
+
+
+def test_bad_walls_wells_and_fields_are_rejected(lib):
+    import paper_1808_07554_gb300 as pkg
+    p = pkg.lbm2p_default_params()
+    p.nx = p.ny = 8
+    p.bc[0] = pkg.PERIODIC                      # unpaired periodic side
+    inp, keep = _inputs(pkg, 64)
+    h = C.c_void_p()
+    assert lib.lbm2p_create(C.byref(h), C.byref(p), C.byref(inp), None) == pkg.EINVAL
+    p.bc[0] = pkg.NOFLUX
+    K = np.ones(64)
+    K[5] = -1.0                                 # non-positive permeability
+    inp, keep = _inputs(pkg, 64, K=K)
+    assert lib.lbm2p_create(C.byref(h), C.byref(p), C.byref(inp), None) == pkg.EINVAL
+    assert "K must be positive" in pkg.lbm2p_last_error(None)
+    inp, keep = _inputs(pkg, 64)
+    w = (pkg.lbm2p_well * 1)(pkg.lbm2p_well(8, 0, 1e-3, 0))    # outside the lattice
+    inp.wells = C.cast(w, C.POINTER(pkg.lbm2p_well))
+    inp.n_wells = 1
+    assert lib.lbm2p_create(C.byref(h), C.byref(p), C.byref(inp), None) == pkg.EINVAL
+    p.bc[0] = p.bc[1] = pkg.DIRICHLET
+    p.nx = 2
+    inp, keep = _inputs(pkg, 16)
+    assert lib.lbm2p_create(C.byref(h), C.byref(p), C.byref(inp), None) == pkg.EINVAL
+    assert not h.value
+
+
+def test_null_handle_calls_fail_cleanly(lib):
+    import paper_1808_07554_gb300 as pkg
+    assert lib.lbm2p_step(None, 1, None, None) == pkg.EINVAL
+    assert lib.lbm2p_fields(None, None, None, 0, 0) == pkg.EINVAL
+    assert lib.lbm2p_state_count(None) == 0
+    lib.lbm2p_destroy(None)

@@ -1,0 +1,319 @@
+"""GPU solver against the FP64 CPU oracle, through the C ABI.
+
+The oracle decides every sub-iteration count (its own stopping rule in FP64); the GPU
+replays those counts, so both run the same number of sweeps and their fields are compared
+element by element.  FP32 storage must match to relative L2 <= 1e-5 per field (P mean-free
+where the pressure has no Dirichlet side, S, u_x, u_y).
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from _problems import constant_diffusivity, uniform
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1808_07554_gb300 import build
+    build.build()
+    import paper_1808_07554_gb300 as pkg
+    pkg.load_library()
+    return pkg
+
+
+def _pkg():
+    import paper_1808_07554_gb300 as pkg
+    return pkg
+
+
+def run_pair(prob, nsteps, replay=None, init_replay=None, tol=1e-8, check_every=10):
+    """Run the oracle (free, or with the given counts) and replay its counts on the GPU."""
+    pkg = _pkg()
+    orc = O.Oracle(prob, tol=tol, check_every=check_every, init_replay=init_replay)
+    log = [orc.init_sub_iters]
+    gpu = pkg.Solver.from_problem(prob, tol=tol, check_every=check_every, init_replay=log[0])
+    assert gpu.init_stats.sub_iters == log[0]
+    for n in range(1, nsteps + 1):
+        t = n * prob.dt
+        if prob.sources_at is not None:
+            Fp, Fs = prob.sources_at(t)
+            orc.set_sources(Fp, Fs)
+            gpu.set_sources(Fp, Fs)
+        if prob.walls_at is not None:
+            Pb, Sb = prob.walls_at(t)
+            for s in range(4):
+                if prob.bc[s] == W.DIRICHLET:
+                    orc.set_dirichlet(s, Pb[s], Sb[s])
+                    gpu.set_dirichlet(s, Pb[s], Sb[s])
+        st, k, r = orc.step(1, None if replay is None else [replay[n - 1]])
+        assert st in (O.OK, O.ENOTCONVERGED)
+        log.append(int(k[0]))
+        gst, stats = gpu.step(1, replay=[log[-1]])
+        assert stats[0].sub_iters == log[-1]
+    return orc, gpu, log
+
+
+def compare(orc, gpu, gauge_free):
+    ref = orc.fields()
+    P, S = gpu.fields(mean_free_P=gauge_free)
+    ux, uy = gpu.velocity()
+    Pref = W.mean_free(ref["P"]) if gauge_free else ref["P"]
+    return {"P": W.rel_l2(P, Pref), "S": W.rel_l2(S, ref["S"]),
+            "ux": W.rel_l2(ux, ref["ux"]), "uy": W.rel_l2(uy, ref["uy"])}
+
+
+def assert_parity(err, tol=TOL):
+    bad = {k: v for k, v in err.items() if not v <= tol}
+    assert not bad, f"relative L2 above {tol}: {err}"
+
+
+# ------------------------------------------------------------------------------------------
+# the manufactured periodic workload, 64^2, 500 steps, sub-iterated to r <= 1e-8
+# ------------------------------------------------------------------------------------------
+def test_manufactured_64_full_run_parity():
+    prob = W.manufactured_periodic(64)
+    orc, gpu, log = run_pair(prob, prob.steps)
+    err = compare(orc, gpu, gauge_free=True)
+    launches, sweeps = gpu.counters()
+    assert sweeps == sum(log)
+    gpu.close()
+    assert_parity(err)
+
+
+def test_manufactured_short_run_free_counts_close_to_oracle():
+    pkg = _pkg()
+    prob = W.manufactured_periodic(32)
+    orc = O.Oracle(prob, tol=1e-6, check_every=10)
+    gpu = pkg.Solver.from_problem(prob, tol=1e-6, check_every=10)
+    assert abs(gpu.init_stats.sub_iters - orc.init_sub_iters) <= 20
+    for n in range(1, 4):
+        Fp, Fs = prob.sources_at(n * prob.dt)
+        orc.set_sources(Fp, Fs)
+        gpu.set_sources(Fp, Fs)
+        st, k, r = orc.step(1)
+        gst, stats = gpu.step(1)
+        assert gst == pkg.OK and stats[0].residual <= 1e-6
+        assert abs(stats[0].sub_iters - int(k[0])) <= 20
+    gpu.close()
+
+
+# ------------------------------------------------------------------------------------------
+# quarter five-spot on a GRF permeability (no-flux walls, wells), ragged sizes
+# ------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("nx,ny,seed", [(96, 70, 2), (300, 200, 5), (257, 33, 9)])
+def test_five_spot_parity(nx, ny, seed):
+    prob = W.quarter_five_spot(nx, ny, seed=seed, corr_len=8.0)
+    orc, gpu, log = run_pair(prob, 4, replay=[120, 60, 60, 40], init_replay=600)
+    err = compare(orc, gpu, gauge_free=True)
+    gpu.close()
+    assert_parity(err)
+
+
+def test_five_spot_converged_parity():
+    prob = W.quarter_five_spot(64, seed=2, corr_len=8.0)
+    orc, gpu, log = run_pair(prob, 5, tol=1e-8)
+    err = compare(orc, gpu, gauge_free=True)
+    gpu.close()
+    assert_parity(err)
+
+
+# ------------------------------------------------------------------------------------------
+# the paper's Dirichlet examples (time-dependent wall traces and sources on the GPU)
+# ------------------------------------------------------------------------------------------
+def test_example1_parity():
+    prob = W.example1(64)
+    orc, gpu, log = run_pair(prob, prob.steps, tol=1e-10)
+    err = compare(orc, gpu, gauge_free=False)
+    gpu.close()
+    assert_parity(err)
+
+
+def test_example2_parity():
+    prob = W.example2(64)
+    orc, gpu, log = run_pair(prob, 24, replay=[300] * 24, init_replay=900)
+    err = compare(orc, gpu, gauge_free=False)
+    gpu.close()
+    assert_parity(err)
+
+
+def test_linear_pressure_exact_on_gpu():
+    nx, ny = 40, 24
+    dx = 1.0 / nx
+    fun = lambda x, y: 0.3 + 0.7 * x - 0.4 * y
+    Pb = [fun(*W.wall_trace_points(s, nx, ny, dx)) for s in range(4)]
+    X, Y = W.node_coords(nx, ny, dx)
+    p = constant_diffusivity(nx, ny, 0.02, 1.3, bc=(2, 2, 2, 2), S0=0.0, P_b=Pb,
+                             S_b=[np.zeros_like(t) for t in Pb])
+    gpu = _pkg().Solver.from_problem(p, tol=1e-7, check_every=10)
+    P, _ = gpu.fields()
+    gpu.close()
+    assert np.max(np.abs(P - fun(X, Y))) < 2e-6
+
+
+# ------------------------------------------------------------------------------------------
+# full-size lattice (1024^2, the benchmark's launch configuration): one kernel at a time
+# from the same seeded state, element by element
+# ------------------------------------------------------------------------------------------
+def _random_state(prob, rng):
+    ny, nx = prob.ny, prob.nx
+    w = np.array([1 / 9] * 4 + [1 / 36] * 4)
+    P = rng.standard_normal((ny, nx))
+    f = (w[:, None, None] * P[None] + 0.01 * rng.standard_normal((8, ny, nx))).astype(np.float32)
+    S = (0.2 + 0.6 * rng.random((ny, nx))).astype(np.float32)
+    g = (0.02 * S[None] + 0.002 * rng.standard_normal((9, ny, nx))).astype(np.float32)
+    inv_tau = (1.0 / (0.6 + 2.0 * rng.random((ny, nx)))).astype(np.float32)
+    return f, g, inv_tau, S
+
+
+def test_full_size_single_kernels():
+    pkg = _pkg()
+    prob = W.quarter_five_spot(1024, seed=2)
+    rng = np.random.default_rng(1234)
+    f, g, inv_tau, S = _random_state(prob, rng)
+    gpu = pkg.Solver.from_problem(prob, init_replay=0)
+    gpu.set_state(np.concatenate([f, g, inv_tau[None], S[None]]))
+    orc = O.Oracle(prob, init_replay=0)
+    f9 = np.concatenate([np.zeros((1,) + f.shape[1:]), f.astype(np.float64)])
+    orc.set_state(f=f9, g=g.astype(np.float64), tau_f=1.0 / inv_tau.astype(np.float64),
+                  S=S.astype(np.float64))
+    # one pressure sweep (Eq. 3-1 with the wells), all eight planes
+    gpu.pressure_sweeps(1)
+    orc.pressure(1)
+    fg = gpu.get_state()[:8]
+    fo = orc.get_state()["f"][1:]
+    scale = np.max(np.abs(fo))
+    assert np.max(np.abs(fg - fo)) <= 2e-6 * scale
+    # a second sweep evaluates the residual of Sec. 3 in FP64
+    r_gpu = gpu.pressure_sweeps(2)
+    st, k, r_orc = orc.pressure(2)
+    assert r_gpu == pytest.approx(r_orc, rel=1e-3)
+    # one physical step with zero sweeps: S refresh + grad P + saturation collision
+    gst, stats = gpu.step(1, replay=[0])
+    orc.step(1, replay=[0])
+    state = gpu.get_state()
+    go = orc.get_state()
+    assert np.max(np.abs(state[8:17] - go["g"])) <= 2e-6 * np.max(np.abs(go["g"]))
+    tau_o = go["tau_f"]
+    assert np.max(np.abs(state[17] - 1.0 / tau_o) * tau_o) <= 2e-6
+    assert np.max(np.abs(state[18] - orc.fields()["S"])) <= 2e-6
+    gpu.close()
+    orc.close()
+
+
+# ------------------------------------------------------------------------------------------
+# edge cases: degenerate and ragged lattices, every wall kind
+# ------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("nx,ny,bc", [
+    (1, 5, (0, 0, 0, 0)), (2, 2, (1, 1, 1, 1)), (3, 3, (2, 2, 2, 2)), (5, 1, (1, 1, 0, 0)),
+    (257, 3, (1, 1, 1, 1)), (33, 65, (0, 0, 1, 1)), (31, 17, (2, 2, 0, 0)),
+    (12, 40, (1, 1, 2, 2))])
+def test_edge_lattices(nx, ny, bc):
+    rng = np.random.default_rng(nx * 1000 + ny)
+    Pb = [rng.random(2 * (ny if s < 2 else nx) + 1) for s in range(4)]
+    Sb = [0.2 + 0.5 * rng.random(2 * (ny if s < 2 else nx) + 1) for s in range(4)]
+    wells = [(0, 0, 2e-3, 0), (nx - 1, ny - 1, 2e-3, 1)] if nx * ny > 1 else []
+    prob = uniform(nx, ny, bc=bc, K=np.exp(rng.standard_normal((ny, nx))),
+                   S0=0.2 + 0.5 * rng.random((ny, nx)), Fs=0.1 * rng.standard_normal((ny, nx)),
+                   Fp=rng.standard_normal((ny, nx)), wells=wells, P_b=Pb, S_b=Sb)
+    orc, gpu, log = run_pair(prob, 3, replay=[15, 8, 11], init_replay=20)
+    gauge_free = W.DIRICHLET not in bc
+    ref = orc.fields()
+    P, S = gpu.fields(mean_free_P=gauge_free)
+    ux, uy = gpu.velocity()
+    Pref = W.mean_free(ref["P"]) if gauge_free else ref["P"]
+    for a, b in ((P, Pref), (S, ref["S"]), (ux, ref["ux"]), (uy, ref["uy"])):
+        assert np.max(np.abs(a - b)) <= 1e-5 * max(1.0, np.max(np.abs(b)))
+    gpu.close()
+
+
+# ------------------------------------------------------------------------------------------
+# invariants, checkpoints, errors, options
+# ------------------------------------------------------------------------------------------
+def test_zero_source_saturation_mass_on_gpu():
+    prob = W.quarter_five_spot(128, seed=3)
+    prob.wells = []
+    rng = np.random.default_rng(4)
+    prob.S0 = 0.3 + 0.2 * rng.random((128, 128))
+    prob.P0 = rng.standard_normal((128, 128))
+    gpu = _pkg().Solver.from_problem(prob, init_replay=50)
+    m0 = float(gpu.fields()[1].astype(np.float64).sum())
+    gpu.step(10, replay=[30] * 10)
+    m1 = float(gpu.fields()[1].astype(np.float64).sum())
+    gpu.close()
+    assert abs(m1 - m0) <= 1e-5 * abs(m0)
+
+
+def test_checkpoint_restart_is_bit_exact():
+    prob = W.quarter_five_spot(96, seed=2)
+    gpu = _pkg().Solver.from_problem(prob, init_replay=200)
+    gpu.step(2, replay=[40, 40])
+    saved = gpu.get_state().copy()
+    gpu.step(3, replay=[30, 20, 10])
+    a = gpu.get_state().copy()
+    gpu.set_state(saved)
+    gpu.step(3, replay=[30, 20, 10])
+    b = gpu.get_state()
+    gpu.close()
+    assert np.array_equal(a, b)
+
+
+def test_not_converged_and_nonfinite_status():
+    pkg = _pkg()
+    prob = W.quarter_five_spot(64, seed=2)
+    gpu = pkg.Solver.from_problem(prob, tol=0.0, max_sub_iters=25, check_every=10)
+    assert gpu.create_status == pkg.ENOTCONVERGED and gpu.init_stats.sub_iters == 25
+    st, stats = gpu.step(1)
+    assert st == pkg.ENOTCONVERGED and stats[0].sub_iters == 25
+    gpu.close()
+    prob.Fp = np.zeros((64, 64))
+    gpu = pkg.Solver.from_problem(prob, init_replay=10)
+    bad = np.zeros((64, 64))
+    bad[10, 10] = np.nan
+    gpu.set_sources(Fp=bad)
+    with pytest.raises(pkg.LBM2PError) as ei:
+        gpu.step(1)
+    assert ei.value.status == pkg.ENONFINITE
+    gpu.close()
+
+
+def test_timing_counters_and_device_outputs():
+    import torch
+    pkg = _pkg()
+    prob = W.quarter_five_spot(128, seed=2)
+    gpu = pkg.Solver.from_problem(prob, init_replay=100)
+    gpu.set_timing(True)
+    l0, s0 = gpu.counters()
+    st, stats = gpu.step(2, replay=[20, 20])
+    l1, s1 = gpu.counters()
+    assert s1 - s0 == 40 and l1 - l0 >= 44
+    assert all(s.sweep_ms > 0 and s.step_ms >= s.sweep_ms for s in stats)
+    P_h, S_h = gpu.fields(mean_free_P=True)
+    P_d = torch.empty((128, 128), dtype=torch.float32, device="cuda")
+    S_d = torch.empty_like(P_d)
+    fp = lambda t: C.cast(C.c_void_p(t.data_ptr()), C.POINTER(C.c_float))
+    pkg.lbm2p_fields(gpu.h, fp(P_d), fp(S_d), 1, 1)
+    torch.cuda.synchronize()
+    assert np.array_equal(P_d.cpu().numpy(), P_h) and np.array_equal(S_d.cpu().numpy(), S_h)
+    gpu.close()
+
+
+def test_cudamalloc_path_matches_torch_allocator():
+    pkg = _pkg()
+    prob = W.quarter_five_spot(80, seed=6)
+    a = pkg.Solver.from_problem(prob, init_replay=100, use_torch=True)
+    b = pkg.Solver.from_problem(prob, init_replay=100, use_torch=False)
+    a.step(2, replay=[10, 10])
+    b.step(2, replay=[10, 10])
+    assert np.array_equal(a.get_state(), b.get_state())
+    a.close()
+    b.close()
