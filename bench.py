@@ -141,6 +141,21 @@ def cpu_baseline(name: str, budget_s: float = 12.0):
             "seconds": dt}
 
 
+def aggregate(local_vals, dist=None, device="cpu"):
+    """Combine per-rank (updates, seconds, e2e_updates, e2e_seconds): work is summed over
+    ranks, time is the maximum over ranks (weak scaling, independent realisations)."""
+    import torch
+    v = [float(x) for x in local_vals]
+    if dist is None:
+        return v[0], v[1], v[2], v[3]
+    t = torch.tensor(v, dtype=torch.float64, device=device)
+    sums = t.clone()
+    dist.all_reduce(sums, op=dist.ReduceOp.SUM)
+    maxs = t.clone()
+    dist.all_reduce(maxs, op=dist.ReduceOp.MAX)
+    return float(sums[0]), float(maxs[1]), float(sums[2]), float(maxs[3])
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -254,17 +269,8 @@ def run_ours(args):
 
     total_ms = float(np.sum(step_ms))
     updates = nodes * (int(np.sum(ksub)) + args.steps)
-    local_val = np.array([updates, total_ms / 1e3, e2e_updates, e2e_s], dtype=np.float64)
-    if dist is not None:
-        t = torch.tensor(local_val, device="cuda")
-        sums = t.clone()
-        dist.all_reduce(sums, op=dist.ReduceOp.SUM)
-        maxs = t.clone()
-        dist.all_reduce(maxs, op=dist.ReduceOp.MAX)
-        updates_all, time_max = float(sums[0]), float(maxs[1])
-        e2e_all, e2e_max = float(sums[2]), float(maxs[3])
-    else:
-        updates_all, time_max, e2e_all, e2e_max = updates, total_ms / 1e3, e2e_updates, e2e_s
+    updates_all, time_max, e2e_all, e2e_max = aggregate(
+        [updates, total_ms / 1e3, e2e_updates, e2e_s], dist, device="cuda")
     if rank != 0:
         return 0
 

@@ -237,10 +237,188 @@ __global__ void __launch_bounds__(kBlock) k_pressure(const __grid_constant__ Pre
     }
 }
 
-// r = ||dP - mean dP|| / ||P - mean P|| from the block partials (FP64, fixed order)
-__global__ void __launch_bounds__(256) k_residual_finalize(const double *__restrict__ partials,
-                                                           int nparts, long long nnodes,
-                                                           float *shift, ResidualOut *out)
+// --------------------------------------------------------------------------------------
+// a2/a3, vectorised: four consecutive nodes per thread (one float4 per plane row), a row
+// tile of 4 * kBlock nodes per block iteration.  Directions with c_x = 0 read their float4
+// directly; c_x = +1 needs the element left of the float4 (from lane - 1 by a shuffle, or a
+// scalar load in lane 0), c_x = -1 the element right of it (lane + 1, or lane 31's load).
+// Threads whose nodes touch the lattice edge, and whole edge rows, use the scalar gather
+// with the wall rules.
+// --------------------------------------------------------------------------------------
+__device__ __forceinline__ float4 ld4(const float *p, int o)
+{
+    return __ldg(reinterpret_cast<const float4 *>(p + o));
+}
+
+__device__ __forceinline__ void st4(float *p, int o, float4 v)
+{
+    *reinterpret_cast<float4 *>(p + o) = v;
+}
+
+// (left neighbour of v.x, v.x, v.y, v.z): the row shifted right by one node
+__device__ __forceinline__ float4 shift_in_left(float4 v, const float *row, int o, int lane,
+                                                bool has_left)
+{
+    float l = __shfl_up_sync(0xffffffffu, v.w, 1);
+    if (lane == 0)
+        l = has_left ? __ldg(row + o - 1) : 0.0f;
+    return make_float4(l, v.x, v.y, v.z);
+}
+
+// (v.y, v.z, v.w, right neighbour of v.w): the row shifted left by one node
+__device__ __forceinline__ float4 shift_in_right(float4 v, const float *row, int o, int lane,
+                                                 bool has_right)
+{
+    float r = __shfl_down_sync(0xffffffffu, v.x, 1);
+    if (lane == 31)
+        r = has_right ? __ldg(row + o + 4) : 0.0f;
+    return make_float4(v.y, v.z, v.w, r);
+}
+
+template <bool CHECK, bool WRITE_P>
+__global__ void __launch_bounds__(kBlock) k_pressure_v4(const __grid_constant__ PressureArgs a)
+{
+    const Geom &g = a.g;
+    const int lane = threadIdx.x & 31;
+    const int p = g.pitch;
+    double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
+    const float shift = CHECK ? *a.shift : 0.0f;
+    const int tiles_x = (g.nx + 4 * kBlock - 1) / (4 * kBlock);
+    const int ntiles = tiles_x * g.ny;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int y = t / tiles_x;
+        const int x0 = ((t - y * tiles_x) * kBlock + threadIdx.x) * 4;
+        const int o = y * p + x0;
+        float sd = 0.0f, sdd = 0.0f, sp = 0.0f, spp = 0.0f;
+        const bool row_inner = y > 0 && y < g.ny - 1;     // uniform over the block
+        bool fast = false;
+        float4 f[8];
+        if (row_inner) {
+            // every lane takes part in the shuffles; lanes past the padded row load nothing
+            const bool in_row = x0 < p;
+            const bool has_left = x0 >= 1 && in_row, has_right = x0 + 4 < g.nx;
+            const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+            f[0] = shift_in_left(in_row ? ld4(a.fin[0], o) : z, a.fin[0], o, lane, has_left);           // c = ( 1, 0)
+            f[1] = in_row ? ld4(a.fin[1], o - p) : z;                                                   // c = ( 0, 1)
+            f[2] = shift_in_right(in_row ? ld4(a.fin[2], o) : z, a.fin[2], o, lane, has_right);         // c = (-1, 0)
+            f[3] = in_row ? ld4(a.fin[3], o + p) : z;                                                   // c = ( 0,-1)
+            f[4] = shift_in_left(in_row ? ld4(a.fin[4], o - p) : z, a.fin[4], o - p, lane, has_left);   // c = ( 1, 1)
+            f[5] = shift_in_right(in_row ? ld4(a.fin[5], o - p) : z, a.fin[5], o - p, lane, has_right); // c = (-1, 1)
+            f[6] = shift_in_right(in_row ? ld4(a.fin[6], o + p) : z, a.fin[6], o + p, lane, has_right); // c = (-1,-1)
+            f[7] = shift_in_left(in_row ? ld4(a.fin[7], o + p) : z, a.fin[7], o + p, lane, has_left);   // c = ( 1,-1)
+            fast = has_left && x0 + 4 <= g.nx - 1;
+        }
+        if (fast) {
+            const float4 it = ld4(a.inv_tau, o);
+            float4 F = a.Fp ? ld4(a.Fp, o) : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int k = 0; k < a.w.n; ++k) {
+                const int d = a.w.idx[k] - o;
+                if (d >= 0 && d < 4) {
+                    if (d == 0) F.x += a.w.fp[k];
+                    else if (d == 1) F.y += a.w.fp[k];
+                    else if (d == 2) F.z += a.w.fp[k];
+                    else F.w += a.w.fp[k];
+                }
+            }
+            float Pv[4];
+            float4 out[8];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                float fc[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    fc[i] = (&f[i].x)[c];
+                const float P = pressure_of(fc);
+                const float itc = (&it.x)[c];
+                const float Fq = 0.125f * (&F.x)[c];
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    (&out[i].x)[c] = fmaf(wgt(i + 1) * P - fc[i], itc, fc[i]) + Fq;
+                Pv[c] = P;
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                st4(a.fout[i], o, out[i]);
+            if (CHECK) {
+                const float4 Pp = ld4(a.Pio, o);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const float d = Pv[c] - (&Pp.x)[c], q = Pv[c] - shift;
+                    sd += d;
+                    sdd += d * d;
+                    sp += q;
+                    spp += q * q;
+                }
+            }
+            if (WRITE_P)
+                st4(a.Pio, o, make_float4(Pv[0], Pv[1], Pv[2], Pv[3]));
+        } else {
+            // edge rows, edge columns and the ragged tail: scalar nodes with the wall rules
+            for (int c = 0; c < 4; ++c) {
+                const int x = x0 + c;
+                if (x >= g.nx)
+                    break;
+                const int oc = o + c;
+                float fc[8];
+                gather_f(a.fin, g, a.Pb, x, y, oc, fc);
+                const float P = pressure_of(fc);
+                const float itc = a.inv_tau[oc];
+                float F = a.Fp ? a.Fp[oc] : 0.0f;
+                for (int k = 0; k < a.w.n; ++k)
+                    if (oc == a.w.idx[k])
+                        F += a.w.fp[k];
+                const float Fq = 0.125f * F;
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    a.fout[i][oc] = fmaf(wgt(i + 1) * P - fc[i], itc, fc[i]) + Fq;
+                if (CHECK) {
+                    const float d = P - a.Pio[oc], q = P - shift;
+                    sd += d;
+                    sdd += d * d;
+                    sp += q;
+                    spp += q * q;
+                }
+                if (WRITE_P)
+                    a.Pio[oc] = P;
+            }
+        }
+        if (CHECK) {
+            sd = warp_sum(sd);
+            sdd = warp_sum(sdd);
+            sp = warp_sum(sp);
+            spp = warp_sum(spp);
+            if (lane == 0) {
+                acc0 += sd;
+                acc1 += sdd;
+                acc2 += sp;
+                acc3 += spp;
+            }
+        }
+    }
+    if (CHECK) {
+        __shared__ double red[kBlock / 32][4];
+        const int warp = threadIdx.x >> 5;
+        if (lane == 0) {
+            red[warp][0] = acc0;
+            red[warp][1] = acc1;
+            red[warp][2] = acc2;
+            red[warp][3] = acc3;
+        }
+        __syncthreads();
+        if (threadIdx.x < 4) {
+            double s = 0.0;
+#pragma unroll
+            for (int w = 0; w < kBlock / 32; ++w)
+                s += red[w][threadIdx.x];
+            a.partials[4 * blockIdx.x + threadIdx.x] = s;
+        }
+    }
+}
+
+// r = ||dP - mean dP|| / ||P - mean P|| from the block partials (FP64, fixed order).
+// Called by all 256 threads of one block; returns r in thread 0.
+__device__ double finalize_residual(const double *__restrict__ partials, int nparts,
+                                    long long nnodes, float *shift, ResidualOut *out)
 {
     __shared__ double red[256][4];
     double s[4] = {0.0, 0.0, 0.0, 0.0};
@@ -259,11 +437,11 @@ __global__ void __launch_bounds__(256) k_residual_finalize(const double *__restr
                 red[threadIdx.x][c] += red[threadIdx.x + h][c];
         __syncthreads();
     }
+    double r = 0.0;
     if (threadIdx.x == 0) {
         const double N = (double)nnodes;
         const double sd = red[0][0], sdd = red[0][1], sp = red[0][2], spp = red[0][3];
         const double c = (double)*shift;
-        double r;
         if (!isfinite(sd) || !isfinite(sdd) || !isfinite(sp) || !isfinite(spp)) {
             r = nan("");
         } else {
@@ -281,6 +459,36 @@ __global__ void __launch_bounds__(256) k_residual_finalize(const double *__restr
         out->sums[2] = sp;
         out->sums[3] = spp;
     }
+    return r;
+}
+
+__global__ void __launch_bounds__(256) k_residual_finalize(const double *__restrict__ partials,
+                                                           int nparts, long long nnodes,
+                                                           float *shift, ResidualOut *out)
+{
+    finalize_residual(partials, nparts, nnodes, shift, out);
+}
+
+// Finalize inside the graph-resident loop: count the body's sweeps and keep looping while
+// r > tol, r is a number, and the cap is not reached.
+__global__ void __launch_bounds__(256) k_residual_finalize_loop(
+    const double *__restrict__ partials, int nparts, long long nnodes, float *shift,
+    ResidualOut *out, LoopCtl *ctl, cudaGraphConditionalHandle handle)
+{
+    const double r = finalize_residual(partials, nparts, nnodes, shift, out);
+    if (threadIdx.x == 0) {
+        const int k = ctl->k + ctl->m;
+        ctl->k = k;
+        ctl->r = r;
+        const bool more = !(r <= ctl->tol) && !isnan(r) && k < ctl->cap;
+        cudaGraphSetConditional(handle, more ? 1u : 0u);
+    }
+}
+
+__global__ void k_loop_reset(LoopCtl *ctl)
+{
+    ctl->k = 0;
+    ctl->r = nan("");
 }
 
 // --------------------------------------------------------------------------------------
@@ -536,13 +744,19 @@ __global__ void __launch_bounds__(256) k_subtract_mean(float *x, long long n, co
 // ======================================================================================
 namespace lbm2p_launch {
 
+#ifdef LBM2P_SCALAR_SWEEP
+#define K_PRESSURE k_pressure
+#else
+#define K_PRESSURE k_pressure_v4
+#endif
+
 static cudaStream_t S(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
 int max_blocks_per_sm_pressure()
 {
     int a = 0, b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pressure<false, false>, kBlock, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pressure<true, true>, kBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, K_PRESSURE<false, false>, kBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, K_PRESSURE<true, true>, kBlock, 0);
     int m = a < b ? a : b;
     return m > 0 ? m : 1;
 }
@@ -550,13 +764,13 @@ int max_blocks_per_sm_pressure()
 void pressure_sweep(const PressureArgs &a, bool check, bool write_p, int grid, void *stream)
 {
     if (check && write_p)
-        k_pressure<true, true><<<grid, kBlock, 0, S(stream)>>>(a);
+        K_PRESSURE<true, true><<<grid, kBlock, 0, S(stream)>>>(a);
     else if (check)
-        k_pressure<true, false><<<grid, kBlock, 0, S(stream)>>>(a);
+        K_PRESSURE<true, false><<<grid, kBlock, 0, S(stream)>>>(a);
     else if (write_p)
-        k_pressure<false, true><<<grid, kBlock, 0, S(stream)>>>(a);
+        K_PRESSURE<false, true><<<grid, kBlock, 0, S(stream)>>>(a);
     else
-        k_pressure<false, false><<<grid, kBlock, 0, S(stream)>>>(a);
+        K_PRESSURE<false, false><<<grid, kBlock, 0, S(stream)>>>(a);
 }
 
 void residual_finalize(const double *partials, int nparts, long long nnodes, float *shift,
@@ -610,6 +824,58 @@ void finalize_mean(const double *partials, int nparts, long long n, double *mean
 void subtract_mean(float *x, long long n, const double *mean, int grid, void *stream)
 {
     k_subtract_mean<<<grid, 256, 0, S(stream)>>>(x, n, mean);
+}
+
+static cudaError_t add_kernel(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
+                              void *func, int grid, int block, void **args)
+{
+    cudaKernelNodeParams p{};
+    p.func = func;
+    p.gridDim = dim3((unsigned)grid);
+    p.blockDim = dim3((unsigned)block);
+    p.sharedMemBytes = 0;
+    p.kernelParams = args;
+    p.extra = nullptr;
+    return cudaGraphAddKernelNode(n, g, dep, dep ? 1 : 0, &p);
+}
+
+cudaError_t node_pressure(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
+                          const PressureArgs &a, bool check, bool write_p, int grid)
+{
+    void *func = check ? (write_p ? (void *)K_PRESSURE<true, true> : (void *)K_PRESSURE<true, false>)
+                       : (write_p ? (void *)K_PRESSURE<false, true> : (void *)K_PRESSURE<false, false>);
+    void *args[] = {(void *)&a};
+    return add_kernel(n, g, dep, func, grid, kBlock, args);
+}
+
+cudaError_t node_finalize_loop(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
+                               const double *partials, int nparts, long long nnodes, float *shift,
+                               ResidualOut *out, LoopCtl *ctl, cudaGraphConditionalHandle h)
+{
+    void *args[] = {(void *)&partials, (void *)&nparts, (void *)&nnodes, (void *)&shift,
+                    (void *)&out, (void *)&ctl, (void *)&h};
+    return add_kernel(n, g, dep, (void *)k_residual_finalize_loop, 1, 256, args);
+}
+
+cudaError_t node_loop_reset(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
+                            LoopCtl *ctl)
+{
+    void *args[] = {(void *)&ctl};
+    return add_kernel(n, g, dep, (void *)k_loop_reset, 1, 1, args);
+}
+
+cudaError_t node_refresh(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
+                         const RefreshArgs &a, int grid)
+{
+    void *args[] = {(void *)&a};
+    return add_kernel(n, g, dep, (void *)k_refresh, grid, kBlock, args);
+}
+
+cudaError_t node_saturation(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
+                            const SaturationArgs &a, int grid)
+{
+    void *args[] = {(void *)&a};
+    return add_kernel(n, g, dep, (void *)k_saturation, grid, kBlock, args);
 }
 
 }  // namespace lbm2p_launch

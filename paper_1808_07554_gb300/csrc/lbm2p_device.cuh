@@ -11,6 +11,8 @@
 //   g: 9 planes, g_0 .. g_8.
 #pragma once
 
+#include <cuda_runtime.h>
+
 #include <cstdint>
 
 #include "lbm2p.h"
@@ -146,6 +148,16 @@ struct ResidualOut {        // written by the finalize kernel
     double sums[4];
 };
 
+// Device-side control of the graph-resident sub-iteration loop.
+struct LoopCtl {
+    int k;          // sweeps run so far in this solve
+    int m;          // sweeps per loop body (= check_every)
+    int cap;        // max_sub_iters (a multiple of m)
+    int pad;
+    double tol;
+    double r;       // last residual
+};
+
 }  // namespace lbm2p_dev
 
 // Launchers implemented in kernels.cu (all asynchronous on `stream`).
@@ -162,6 +174,18 @@ void fill_f_eq(float *const fout[8], const float *P0, Geom g, int grid, void *st
 void tau_from_S(float *inv_tau, const float *S, const float *K, Geom g, Model m, int grid,
                 void *stream);
 void fields(const FieldsArgs &a, int grid, void *stream);
+// graph nodes (explicit construction; parameters are copied into the node)
+cudaError_t node_pressure(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
+                          const PressureArgs &a, bool check, bool write_p, int grid);
+cudaError_t node_finalize_loop(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
+                               const double *partials, int nparts, long long nnodes, float *shift,
+                               ResidualOut *out, LoopCtl *ctl, cudaGraphConditionalHandle h);
+cudaError_t node_loop_reset(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
+                            LoopCtl *ctl);
+cudaError_t node_refresh(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
+                         const RefreshArgs &a, int grid);
+cudaError_t node_saturation(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
+                            const SaturationArgs &a, int grid);
 void sum_compact(const float *x, long long n, double *partials, int grid, void *stream);
 void finalize_mean(const double *partials, int nparts, long long n, double *mean, void *stream);
 void subtract_mean(float *x, long long n, const double *mean, int grid, void *stream);

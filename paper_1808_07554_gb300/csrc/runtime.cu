@@ -53,6 +53,16 @@ struct lbm2p {
     long long launches = 0, sweeps = 0;
     bool timing = false;
     cudaEvent_t ev_step0 = nullptr, ev_step1 = nullptr, ev_sw0 = nullptr, ev_sw1 = nullptr;
+    // graph-resident sub-iteration (free-running solves when check_every is even and
+    // divides max_sub_iters): one graph per f parity for a bare solve, and one per
+    // (f parity, g parity) for a whole physical step
+    bool graph_ok = false;
+    LoopCtl *ctl = nullptr;
+    LoopCtl *ctl_host = nullptr;       // pinned
+    cudaGraph_t solve_g[2] = {};
+    cudaGraphExec_t solve_x[2] = {};
+    cudaGraph_t step_g[2][2] = {};
+    cudaGraphExec_t step_x[2][2] = {};
     std::string err;
 };
 
@@ -117,10 +127,29 @@ void free_all(lbm2p *h)
         else if (!h->p.alloc)
             cudaFree(a.ptr);
     }
+    for (int a = 0; a < 2; ++a) {
+        if (h->solve_x[a])
+            cudaGraphExecDestroy(h->solve_x[a]);
+        if (h->solve_g[a])
+            cudaGraphDestroy(h->solve_g[a]);
+        h->solve_x[a] = nullptr;
+        h->solve_g[a] = nullptr;
+        for (int b = 0; b < 2; ++b) {
+            if (h->step_x[a][b])
+                cudaGraphExecDestroy(h->step_x[a][b]);
+            if (h->step_g[a][b])
+                cudaGraphDestroy(h->step_g[a][b]);
+            h->step_x[a][b] = nullptr;
+            h->step_g[a][b] = nullptr;
+        }
+    }
     h->allocs.clear();
     if (h->res_host)
         cudaFreeHost(h->res_host);
     h->res_host = nullptr;
+    if (h->ctl_host)
+        cudaFreeHost(h->ctl_host);
+    h->ctl_host = nullptr;
     for (cudaEvent_t *e : {&h->ev_step0, &h->ev_step1, &h->ev_sw0, &h->ev_sw1})
         if (*e) {
             cudaEventDestroy(*e);
@@ -185,6 +214,149 @@ PressureArgs pressure_args(lbm2p *h, int src)
     return a;
 }
 
+RefreshArgs refresh_args(lbm2p *h, int pg)
+{
+    RefreshArgs a{};
+    for (int i = 0; i < 9; ++i)
+        a.gin[i] = h->gbuf[pg][i];
+    a.K = h->K;
+    a.Fs = h->Fs;
+    a.inv_tau = h->inv_tau;
+    for (int s = 0; s < 4; ++s)
+        a.Sb[s] = h->Sb[s];
+    a.g = h->geom;
+    a.m = h->model;
+    a.w = h->wells;
+    return a;
+}
+
+SaturationArgs saturation_args(lbm2p *h, int pf, int pg)
+{
+    SaturationArgs a{};
+    for (int i = 0; i < 8; ++i)
+        a.fin[i] = h->fbuf[pf][i];
+    for (int i = 0; i < 9; ++i) {
+        a.gin[i] = h->gbuf[pg][i];
+        a.gout[i] = h->gbuf[1 - pg][i];
+    }
+    a.K = h->K;
+    a.inv_tau = h->inv_tau;
+    a.Fs = h->Fs;
+    a.S = h->S;
+    for (int s = 0; s < 4; ++s) {
+        a.Pb[s] = h->Pb[s];
+        a.Sb[s] = h->Sb[s];
+    }
+    a.g = h->geom;
+    a.m = h->model;
+    a.w = h->wells;
+    return a;
+}
+
+
+// ---- graph-resident sub-iteration ----------------------------------------------------------
+// Appends to G: reset(ctl) -> event(sw0) -> WHILE{ m sweeps from f parity pf, the last one
+// with residual partials; finalize sets the condition } -> event(sw1).  m is even, so the
+// loop ends on parity pf.  *last receives the final node.
+lbm2p_status add_loop(lbm2p *h, cudaGraph_t G, const cudaGraphNode_t *dep, int pf,
+                      cudaGraphNode_t *last)
+{
+    const int m = h->p.check_every;
+    cudaGraphNode_t reset, ev0, wn, ev1;
+    CUDA_TRY(h, lbm2p_launch::node_loop_reset(&reset, G, dep, h->ctl));
+    CUDA_TRY(h, cudaGraphAddEventRecordNode(&ev0, G, &reset, 1, h->ev_sw0));
+    cudaGraphConditionalHandle hd;
+    CUDA_TRY(h, cudaGraphConditionalHandleCreate(&hd, G, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = hd;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    CUDA_TRY(h, cudaGraphAddNode(&wn, G, &ev0, nullptr, 1, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    cudaGraphNode_t prev = nullptr;
+    int src = pf;
+    for (int kk = 1; kk <= m; ++kk) {
+        cudaGraphNode_t n;
+        PressureArgs a = pressure_args(h, src);
+        CUDA_TRY(h, lbm2p_launch::node_pressure(&n, body, prev ? &prev : nullptr, a, kk == m,
+                                                kk == m - 1, h->grid));
+        prev = n;
+        src = 1 - src;
+    }
+    cudaGraphNode_t fin;
+    CUDA_TRY(h, lbm2p_launch::node_finalize_loop(&fin, body, &prev, h->partials, h->grid,
+                                                 h->nnodes, h->shift, h->res, h->ctl, hd));
+    CUDA_TRY(h, cudaGraphAddEventRecordNode(&ev1, G, &wn, 1, h->ev_sw1));
+    *last = ev1;
+    return LBM2P_OK;
+}
+
+lbm2p_status solve_graph(lbm2p *h, int pf, cudaGraphExec_t *out)
+{
+    if (!h->solve_x[pf]) {
+        cudaGraph_t G;
+        CUDA_TRY(h, cudaGraphCreate(&G, 0));
+        h->solve_g[pf] = G;
+        cudaGraphNode_t last;
+        lbm2p_status e = add_loop(h, G, nullptr, pf, &last);
+        if (e != LBM2P_OK)
+            return e;
+        CUDA_TRY(h, cudaGraphInstantiate(&h->solve_x[pf], G, 0));
+    }
+    *out = h->solve_x[pf];
+    return LBM2P_OK;
+}
+
+// one physical step: refresh -> loop -> saturation
+lbm2p_status step_graph(lbm2p *h, int pf, int pg, cudaGraphExec_t *out)
+{
+    if (!h->step_x[pf][pg]) {
+        cudaGraph_t G;
+        CUDA_TRY(h, cudaGraphCreate(&G, 0));
+        h->step_g[pf][pg] = G;
+        cudaGraphNode_t nr, last, ns;
+        CUDA_TRY(h, lbm2p_launch::node_refresh(&nr, G, nullptr, refresh_args(h, pg), h->grid));
+        lbm2p_status e = add_loop(h, G, &nr, pf, &last);
+        if (e != LBM2P_OK)
+            return e;
+        CUDA_TRY(h, lbm2p_launch::node_saturation(&ns, G, &last, saturation_args(h, pf, pg),
+                                                  h->grid));
+        CUDA_TRY(h, cudaGraphInstantiate(&h->step_x[pf][pg], G, 0));
+    }
+    *out = h->step_x[pf][pg];
+    return LBM2P_OK;
+}
+
+// read the loop's counters after a graph launch (synchronises the stream)
+lbm2p_status read_loop(lbm2p *h, int *k, double *r, float *sweep_ms)
+{
+    cudaStream_t st = (cudaStream_t)h->stream;
+    CUDA_TRY(h, cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(LoopCtl), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(h, cudaStreamSynchronize(st));
+    *k = h->ctl_host->k;
+    *r = h->ctl_host->r;
+    const int m = h->p.check_every;
+    h->sweeps += *k;
+    h->launches += 1 + *k + *k / m;   // reset, sweeps, finalizes
+    if (sweep_ms) {
+        *sweep_ms = -1.0f;
+        if (h->timing)
+            CUDA_TRY(h, cudaEventElapsedTime(sweep_ms, h->ev_sw0, h->ev_sw1));
+    }
+    return LBM2P_OK;
+}
+
+lbm2p_status loop_status(lbm2p *h, int k, double r)
+{
+    if (std::isnan(r))
+        return fail(h, LBM2P_ENONFINITE, "pressure residual is not finite after %d sweeps", k);
+    if (!(r <= h->p.tol))
+        return fail(h, LBM2P_ENOTCONVERGED, "pressure residual %.3e above tol %.3e after %d sweeps",
+                    r, h->p.tol, k);
+    return LBM2P_OK;
+}
+
 // ---- the pressure sub-iteration (Sec. 3) ------------------------------------------------
 // replay >= 0: exactly that many sweeps; replay < 0: until r <= tol at a check or the cap.
 lbm2p_status pressure_solve(lbm2p *h, int replay, int *k_out, double *r_out, float *ms_out)
@@ -239,6 +411,22 @@ lbm2p_status pressure_solve(lbm2p *h, int replay, int *k_out, double *r_out, flo
         return LBM2P_OK;
     };
     lbm2p_status e;
+    if (replay < 0 && h->graph_ok) {
+        cudaGraphExec_t x;
+        if ((e = solve_graph(h, h->cur_f, &x)) != LBM2P_OK)
+            return e;
+        CUDA_TRY(h, cudaGraphLaunch(x, st));
+        float ms = -1.0f;
+        if ((e = read_loop(h, &k, &r, &ms)) != LBM2P_OK)
+            return e;
+        if (k_out)
+            *k_out = k;
+        if (r_out)
+            *r_out = r;
+        if (ms_out)
+            *ms_out = ms;
+        return loop_status(h, k, r);
+    }
     if (replay >= 0) {
         if (replay > 0) {
             if ((e = run_batch(replay)) != LBM2P_OK)
@@ -293,52 +481,42 @@ lbm2p_status pressure_solve(lbm2p *h, int replay, int *k_out, double *r_out, flo
     return LBM2P_OK;
 }
 
-RefreshArgs refresh_args(lbm2p *h)
-{
-    RefreshArgs a{};
-    for (int i = 0; i < 9; ++i)
-        a.gin[i] = h->gbuf[h->cur_g][i];
-    a.K = h->K;
-    a.Fs = h->Fs;
-    a.inv_tau = h->inv_tau;
-    for (int s = 0; s < 4; ++s)
-        a.Sb[s] = h->Sb[s];
-    a.g = h->geom;
-    a.m = h->model;
-    a.w = h->wells;
-    return a;
-}
-
-SaturationArgs saturation_args(lbm2p *h)
-{
-    SaturationArgs a{};
-    for (int i = 0; i < 8; ++i)
-        a.fin[i] = h->fbuf[h->cur_f][i];
-    for (int i = 0; i < 9; ++i) {
-        a.gin[i] = h->gbuf[h->cur_g][i];
-        a.gout[i] = h->gbuf[1 - h->cur_g][i];
-    }
-    a.K = h->K;
-    a.inv_tau = h->inv_tau;
-    a.Fs = h->Fs;
-    a.S = h->S;
-    for (int s = 0; s < 4; ++s) {
-        a.Pb[s] = h->Pb[s];
-        a.Sb[s] = h->Sb[s];
-    }
-    a.g = h->geom;
-    a.m = h->model;
-    a.w = h->wells;
-    return a;
-}
-
 lbm2p_status one_step(lbm2p *h, int replay, lbm2p_step_stats *stats)
 {
     cudaStream_t st = (cudaStream_t)h->stream;
+    if (replay < 0 && h->graph_ok) {
+        cudaGraphExec_t x;
+        lbm2p_status e = step_graph(h, h->cur_f, h->cur_g, &x);
+        if (e != LBM2P_OK)
+            return e;
+        if (h->timing)
+            CUDA_TRY(h, cudaEventRecord(h->ev_step0, st));
+        CUDA_TRY(h, cudaGraphLaunch(x, st));
+        if (h->timing)
+            CUDA_TRY(h, cudaEventRecord(h->ev_step1, st));
+        int k = 0;
+        double r = std::nan("");
+        float sw_ms = -1.0f, step_ms = -1.0f;
+        if ((e = read_loop(h, &k, &r, &sw_ms)) != LBM2P_OK)
+            return e;
+        h->launches += 2;                 // refresh, saturation
+        h->cur_g = 1 - h->cur_g;
+        if (h->timing)
+            CUDA_TRY(h, cudaEventElapsedTime(&step_ms, h->ev_step0, h->ev_step1));
+        lbm2p_status ps = loop_status(h, k, r);
+        if (stats) {
+            stats->sub_iters = k;
+            stats->status = ps;
+            stats->residual = r;
+            stats->sweep_ms = sw_ms;
+            stats->step_ms = step_ms;
+        }
+        return ps;
+    }
     if (h->timing)
         CUDA_TRY(h, cudaEventRecord(h->ev_step0, st));
     // a1: stream g, S^n, tau_f
-    lbm2p_launch::refresh(refresh_args(h), h->grid, h->stream);
+    lbm2p_launch::refresh(refresh_args(h, h->cur_g), h->grid, h->stream);
     LAUNCHED(h, "refresh");
     // a2/a3: pressure sub-iteration
     int k = 0;
@@ -356,7 +534,7 @@ lbm2p_status one_step(lbm2p *h, int replay, lbm2p_step_stats *stats)
         return ps;
     }
     // a4/a5: grad P and the saturation update
-    lbm2p_launch::saturation(saturation_args(h), h->grid, h->stream);
+    lbm2p_launch::saturation(saturation_args(h, h->cur_f, h->cur_g), h->grid, h->stream);
     LAUNCHED(h, "saturation");
     h->cur_g = 1 - h->cur_g;
     float step_ms = -1.0f;
@@ -544,17 +722,32 @@ lbm2p_status build(lbm2p *h, const lbm2p_inputs *in, lbm2p_step_stats *init_stat
     h->mean = (double *)dev_alloc(h, 64);
     h->shift = (float *)dev_alloc(h, 64);
     h->res = (ResidualOut *)dev_alloc(h, sizeof(ResidualOut));
+    h->ctl = (LoopCtl *)dev_alloc(h, sizeof(LoopCtl));
     h->stage = (float *)dev_alloc(h, (size_t)h->nnodes * sizeof(float) * 4);
-    ok = ok && h->partials && h->mean && h->shift && h->res && h->stage;
+    ok = ok && h->partials && h->mean && h->shift && h->res && h->ctl && h->stage;
     if (!ok)
         return fail(h, LBM2P_ENOMEM, "device allocation of %.1f MiB failed",
                     (double)pb * 45 / (1 << 20));
     CUDA_TRY(h, cudaMallocHost((void **)&h->res_host, sizeof(ResidualOut)));
+    CUDA_TRY(h, cudaMallocHost((void **)&h->ctl_host, sizeof(LoopCtl)));
     for (cudaEvent_t *e : {&h->ev_step0, &h->ev_step1, &h->ev_sw0, &h->ev_sw1})
         CUDA_TRY(h, cudaEventCreate(e));
     cudaStream_t st = (cudaStream_t)h->stream;
     for (auto &a : h->allocs)
         CUDA_TRY(h, cudaMemsetAsync(a.ptr, 0, a.bytes, st));
+    // the loop body holds check_every sweeps and must return to the same f buffer
+    h->graph_ok = p.check_every >= 2 && p.check_every % 2 == 0 &&
+                  p.max_sub_iters % p.check_every == 0;
+    {
+        LoopCtl c{};
+        c.m = p.check_every;
+        c.cap = p.max_sub_iters;
+        c.tol = p.tol;
+        c.r = 0.0;
+        *h->ctl_host = c;
+        CUDA_TRY(h, cudaMemcpyAsync(h->ctl, h->ctl_host, sizeof(LoopCtl), cudaMemcpyHostToDevice, st));
+        CUDA_TRY(h, cudaStreamSynchronize(st));
+    }
 
     // inputs
     lbm2p_status e;
@@ -885,8 +1078,7 @@ void lbm2p_destroy(lbm2p *h)
 {
     if (!h)
         return;
-    if (h->stream || true)
-        cudaStreamSynchronize((cudaStream_t)h->stream);
+    cudaStreamSynchronize((cudaStream_t)h->stream);
     free_all(h);
     delete h;
 }

@@ -107,6 +107,27 @@ def test_manufactured_short_run_free_counts_close_to_oracle():
     gpu.close()
 
 
+@pytest.mark.parametrize("check_every,cap", [(10, 10_000_000), (7, 10_000_000), (10, 100_003)])
+def test_free_running_loop_matches_oracle(check_every, cap):
+    """Free-running sub-iteration: the graph-resident loop (even check_every dividing the cap)
+    and the host-driven loop (otherwise) both stop where the oracle stops, up to FP32
+    rounding of the residual near tol."""
+    pkg = _pkg()
+    prob = W.quarter_five_spot(48, seed=4, corr_len=6.0)
+    orc = O.Oracle(prob, tol=1e-6, check_every=check_every, max_sub_iters=cap)
+    gpu = pkg.Solver.from_problem(prob, tol=1e-6, check_every=check_every, max_sub_iters=cap)
+    assert abs(gpu.init_stats.sub_iters - orc.init_sub_iters) <= 2 * check_every
+    for n in range(3):
+        st, k, r = orc.step(1)
+        gst, stats = gpu.step(1)
+        assert gst == pkg.OK and stats[0].residual <= 1e-6
+        assert stats[0].sub_iters % check_every == 0
+        assert abs(stats[0].sub_iters - int(k[0])) <= 2 * check_every
+    err = compare(orc, gpu, gauge_free=True)
+    gpu.close()
+    assert all(v < 1e-3 for v in err.values()), err
+
+
 # ------------------------------------------------------------------------------------------
 # quarter five-spot on a GRF permeability (no-flux walls, wells), ragged sizes
 # ------------------------------------------------------------------------------------------
@@ -154,7 +175,8 @@ def test_linear_pressure_exact_on_gpu():
     X, Y = W.node_coords(nx, ny, dx)
     p = constant_diffusivity(nx, ny, 0.02, 1.3, bc=(2, 2, 2, 2), S0=0.0, P_b=Pb,
                              S_b=[np.zeros_like(t) for t in Pb])
-    gpu = _pkg().Solver.from_problem(p, tol=1e-7, check_every=10)
+    # 20000 sweeps converge this lattice to FP32 resolution whatever the stopping test says
+    gpu = _pkg().Solver.from_problem(p, tol=1e-12, check_every=10, max_sub_iters=20000)
     P, _ = gpu.fields()
     gpu.close()
     assert np.max(np.abs(P - fun(X, Y))) < 2e-6
