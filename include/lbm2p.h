@@ -175,8 +175,13 @@ lbm2p_status lbm2p_velocity(lbm2p *h, float *ux, float *uy, int on_device);
    the current time level into ny*nx float buffers (either may be NULL). */
 lbm2p_status lbm2p_fields(lbm2p *h, float *P, float *S, int mean_free_P, int on_device);
 
-/* Number of floats in a state image: 19 planes of ny*nx, in order f_1..f_8 (post-collision
-   pressure populations), g_0..g_8 (post-collision saturation populations), 1/tau_f, S. */
+/* Number of floats in a state image: 20 planes of ny*nx, in order
+ *   n_1..n_8  pressure populations, stored as deviations n_i = f_i^+ - w_i R from the
+ *             reference pressure R below (f_i^+ the post-collision populations of Eq. 3-1),
+ *   g_0..g_8  post-collision saturation populations (Eq. 3-2),
+ *   1/tau_f, S, R.
+ * The library keeps f in this form on the device: R is the pressure of the last converged
+ * step, so the stored values are small and FP32 resolves them finely. */
 size_t lbm2p_state_count(const lbm2p *h);
 
 /* Copy the state out / in (checkpoint and restart; count must equal lbm2p_state_count). */

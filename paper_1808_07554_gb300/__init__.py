@@ -27,6 +27,7 @@ MOB_QUADRATIC, MOB_DECOUPLED, MOB_RATIONAL = 0, 1, 2
 TAU_REFERENCE, TAU_PHYSICAL_DT = 0, 1
 STORE_FP32, STORE_FP16_DEV = 0, 1
 MAX_WELLS = 16
+STATE_PLANES = 20   # n_1..n_8 (f^+ - w_i R), g_0..g_8, 1/tau_f, S, R
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 RELEASE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
@@ -388,7 +389,7 @@ class Solver:
         n = lbm2p_state_count(self.h)
         buf = np.empty(n, np.float32)
         lbm2p_get_state(self.h, _fp(buf), n, 0)
-        return buf.reshape(19, self.ny, self.nx)
+        return buf.reshape(STATE_PLANES, self.ny, self.nx)
 
     def set_state(self, state):
         n = lbm2p_state_count(self.h)

@@ -7,7 +7,9 @@
 // writes its own post-collision values into the other buffer (ping-pong), so one launch
 // is one fused stream + collide of Eq. 3-1 (or Eq. 3-2).  Wall rules of Sec. 4 are folded
 // into the gather: interior nodes take a branch-free path; only nodes on the lattice edge
-// evaluate the periodic / bounce-back / anti-bounce-back substitution.
+// evaluate the periodic / bounce-back / anti-bounce-back substitution.  The pressure
+// populations are stored as deviations from the step's reference pressure (see
+// lbm2p_device.cuh), and every pressure kernel works on those deviations.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -19,11 +21,76 @@ namespace lbm2p_dev {
 // --------------------------------------------------------------------------------------
 // gather with the wall rules of Sec. 4
 // --------------------------------------------------------------------------------------
-// Value arriving at (x, y) along direction I from the post-collision plane src_i, for a
-// node on the lattice edge.  If x - c_I is outside the lattice the link crosses a wall:
-// periodic sides wrap; no-flux gives the node's own opposite population (bounce-back);
-// Dirichlet gives -opposite + 2 eq_opp * (wall value where the link crosses the wall)
-// (anti-bounce-back).  x-sides are tested first, so corner links follow the x-side rule.
+__device__ __forceinline__ bool interior(const Geom &g, int x, int y)
+{
+    return x > 0 && x < g.nx - 1 && y > 0 && y < g.ny - 1;
+}
+
+// a_I = f_I(x) - w_I R(x) pulled into an edge node (x, y), with r0 = R(x).  Wall rules of
+// Sec. 4 in deviation form: a neighbour inside (or wrapped) gives n_I(src) + w_I (R(src) - r0);
+// bounce-back gives n_opp(x); anti-bounce-back gives -n_opp(x) + 2 w_I (P_b - r0).
+template <int I>
+__device__ __forceinline__ float pull_edge_dev(const float *__restrict__ n_i,
+                                               const float *__restrict__ n_opp,
+                                               const float *__restrict__ R, const Geom &g,
+                                               const float *const *Pb, int x, int y, float r0)
+{
+    constexpr int ex = cx(I), ey = cy(I);
+    int xs = x - ex, ys = y - ey, side = -1;
+    if (xs < 0 || xs >= g.nx) {
+        const int sd = xs < 0 ? 0 : 1;
+        if (g.bc[sd] == BC_PERIODIC)
+            xs += xs < 0 ? g.nx : -g.nx;
+        else
+            side = sd;
+    }
+    if (side < 0 && (ys < 0 || ys >= g.ny)) {
+        const int sd = ys < 0 ? 2 : 3;
+        if (g.bc[sd] == BC_PERIODIC)
+            ys += ys < 0 ? g.ny : -g.ny;
+        else
+            side = sd;
+    }
+    if (side < 0) {
+        const int src = ys * g.pitch + xs;
+        return n_i[src] + wgt(I) * (R[src] - r0);
+    }
+    const float b = n_opp[y * g.pitch + x];
+    if (g.bc[side] == BC_NOFLUX)
+        return b;
+    const int k = side < 2 ? 2 * y + 1 - ey : 2 * x + 1 - ex;
+    return -b + 2.0f * wgt(I) * (Pb[side][k] - r0);
+}
+
+// a_1 .. a_8 (pressure populations relative to R(x)) pulled into (x, y)
+__device__ __forceinline__ void gather_a(const float *const *fin, const float *__restrict__ R,
+                                         const Geom &g, const float *const *Pb, int x, int y,
+                                         int o, float (&a)[8])
+{
+    const float r0 = R[o];
+    if (interior(g, x, y)) {
+        const int p = g.pitch;
+        a[0] = fin[0][o - 1] + wgt(1) * (R[o - 1] - r0);
+        a[1] = fin[1][o - p] + wgt(2) * (R[o - p] - r0);
+        a[2] = fin[2][o + 1] + wgt(3) * (R[o + 1] - r0);
+        a[3] = fin[3][o + p] + wgt(4) * (R[o + p] - r0);
+        a[4] = fin[4][o - p - 1] + wgt(5) * (R[o - p - 1] - r0);
+        a[5] = fin[5][o - p + 1] + wgt(6) * (R[o - p + 1] - r0);
+        a[6] = fin[6][o + p + 1] + wgt(7) * (R[o + p + 1] - r0);
+        a[7] = fin[7][o + p - 1] + wgt(8) * (R[o + p - 1] - r0);
+    } else {
+        a[0] = pull_edge_dev<1>(fin[0], fin[opp(1) - 1], R, g, Pb, x, y, r0);
+        a[1] = pull_edge_dev<2>(fin[1], fin[opp(2) - 1], R, g, Pb, x, y, r0);
+        a[2] = pull_edge_dev<3>(fin[2], fin[opp(3) - 1], R, g, Pb, x, y, r0);
+        a[3] = pull_edge_dev<4>(fin[3], fin[opp(4) - 1], R, g, Pb, x, y, r0);
+        a[4] = pull_edge_dev<5>(fin[4], fin[opp(5) - 1], R, g, Pb, x, y, r0);
+        a[5] = pull_edge_dev<6>(fin[5], fin[opp(6) - 1], R, g, Pb, x, y, r0);
+        a[6] = pull_edge_dev<7>(fin[6], fin[opp(7) - 1], R, g, Pb, x, y, r0);
+        a[7] = pull_edge_dev<8>(fin[7], fin[opp(8) - 1], R, g, Pb, x, y, r0);
+    }
+}
+
+// generic pull for the saturation populations (plain values, planes 0..8)
 template <int I>
 __device__ __forceinline__ float pull_edge(const float *__restrict__ src_i,
                                            const float *__restrict__ src_opp, const Geom &g,
@@ -53,38 +120,6 @@ __device__ __forceinline__ float pull_edge(const float *__restrict__ src_i,
         return b;
     const int k = side < 2 ? 2 * y + 1 - ey : 2 * x + 1 - ex;
     return -b + 2.0f * eq_opp * trace[side][k];
-}
-
-__device__ __forceinline__ bool interior(const Geom &g, int x, int y)
-{
-    return x > 0 && x < g.nx - 1 && y > 0 && y < g.ny - 1;
-}
-
-// f_1 .. f_8 pulled into (x, y) (pressure distribution, planes 0..7)
-__device__ __forceinline__ void gather_f(const float *const *fin, const Geom &g,
-                                         const float *const *Pb, int x, int y, int o,
-                                         float (&f)[8])
-{
-    if (interior(g, x, y)) {
-        const int p = g.pitch;
-        f[0] = fin[0][o - 1];
-        f[1] = fin[1][o - p];
-        f[2] = fin[2][o + 1];
-        f[3] = fin[3][o + p];
-        f[4] = fin[4][o - p - 1];
-        f[5] = fin[5][o - p + 1];
-        f[6] = fin[6][o + p + 1];
-        f[7] = fin[7][o + p - 1];
-    } else {
-        f[0] = pull_edge<1>(fin[0], fin[opp(1) - 1], g, Pb, wgt(opp(1)), x, y);
-        f[1] = pull_edge<2>(fin[1], fin[opp(2) - 1], g, Pb, wgt(opp(2)), x, y);
-        f[2] = pull_edge<3>(fin[2], fin[opp(3) - 1], g, Pb, wgt(opp(3)), x, y);
-        f[3] = pull_edge<4>(fin[3], fin[opp(4) - 1], g, Pb, wgt(opp(4)), x, y);
-        f[4] = pull_edge<5>(fin[4], fin[opp(5) - 1], g, Pb, wgt(opp(5)), x, y);
-        f[5] = pull_edge<6>(fin[5], fin[opp(6) - 1], g, Pb, wgt(opp(6)), x, y);
-        f[6] = pull_edge<7>(fin[6], fin[opp(7) - 1], g, Pb, wgt(opp(7)), x, y);
-        f[7] = pull_edge<8>(fin[7], fin[opp(8) - 1], g, Pb, wgt(opp(8)), x, y);
-    }
 }
 
 // g_0 .. g_8 pulled into (x, y) (saturation distribution, planes 0..8)
@@ -171,79 +206,14 @@ __device__ __forceinline__ float warp_sum(float v)
 }
 
 // --------------------------------------------------------------------------------------
-// a2/a3: fused pressure sweep (Eq. 3-1) with optional residual partials
-// --------------------------------------------------------------------------------------
-template <bool CHECK, bool WRITE_P>
-__global__ void __launch_bounds__(kBlock) k_pressure(const __grid_constant__ PressureArgs a)
-{
-    const Geom &g = a.g;
-    const int lane = threadIdx.x & 31;
-    double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
-    const float shift = CHECK ? *a.shift : 0.0f;
-    for (int t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
-        const int y = t / g.tiles_x;
-        const int x = (t - y * g.tiles_x) * kBlock + threadIdx.x;
-        float d = 0.0f, p = 0.0f;
-        if (x < g.nx) {
-            const int o = y * g.pitch + x;
-            float f[8];
-            gather_f(a.fin, g, a.Pb, x, y, o, f);
-            const float P = pressure_of(f);
-            const float it = a.inv_tau[o];
-            float F = a.Fp ? a.Fp[o] : 0.0f;
-            for (int k = 0; k < a.w.n; ++k)
-                if (o == a.w.idx[k])
-                    F += a.w.fp[k];
-            const float Fq = 0.125f * F;   // w_bar_i = 1/8 (Eq. 3-5a)
-            // Eq. 2-1b: f_i^+ = f_i - (f_i - w_i P)/tau_f + w_bar_i F~_p
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-                a.fout[i][o] = fmaf(wgt(i + 1) * P - f[i], it, f[i]) + Fq;
-            if (CHECK) {
-                d = P - a.Pio[o];
-                p = P - shift;
-            }
-            if (WRITE_P)
-                a.Pio[o] = P;
-        }
-        if (CHECK) {
-            const float s0 = warp_sum(d), s1 = warp_sum(d * d);
-            const float s2 = warp_sum(p), s3 = warp_sum(p * p);
-            if (lane == 0) {
-                acc0 += s0;
-                acc1 += s1;
-                acc2 += s2;
-                acc3 += s3;
-            }
-        }
-    }
-    if (CHECK) {
-        __shared__ double red[kBlock / 32][4];
-        const int warp = threadIdx.x >> 5;
-        if (lane == 0) {
-            red[warp][0] = acc0;
-            red[warp][1] = acc1;
-            red[warp][2] = acc2;
-            red[warp][3] = acc3;
-        }
-        __syncthreads();
-        if (threadIdx.x < 4) {
-            double s = 0.0;
-#pragma unroll
-            for (int w = 0; w < kBlock / 32; ++w)
-                s += red[w][threadIdx.x];
-            a.partials[4 * blockIdx.x + threadIdx.x] = s;
-        }
-    }
-}
-
-// --------------------------------------------------------------------------------------
-// a2/a3, vectorised: four consecutive nodes per thread (one float4 per plane row), a row
-// tile of 4 * kBlock nodes per block iteration.  Directions with c_x = 0 read their float4
-// directly; c_x = +1 needs the element left of the float4 (from lane - 1 by a shuffle, or a
-// scalar load in lane 0), c_x = -1 the element right of it (lane + 1, or lane 31's load).
-// Threads whose nodes touch the lattice edge, and whole edge rows, use the scalar gather
-// with the wall rules.
+// a2/a3: fused pressure sweep (Eq. 3-1), four consecutive nodes per thread (one float4 per
+// plane row), a row tile of 4 * kBlock nodes per block iteration.  Directions with c_x = 0
+// read their float4 directly; c_x = +1 needs the element left of the float4 (from lane - 1
+// by a shuffle, or a scalar load in lane 0), c_x = -1 the element right of it (lane + 1, or
+// lane 31's load).  The reference pressure R is gathered the same way.  Threads whose nodes
+// touch the lattice edge, whole edge rows and the ragged tail use the scalar gather with the
+// wall rules.  CHECK adds the residual partials (dP - dP_prev and P - shift, FP32 per warp,
+// FP64 per block); WRITE_P stores dP for the next check.
 // --------------------------------------------------------------------------------------
 __device__ __forceinline__ float4 ld4(const float *p, int o)
 {
@@ -275,8 +245,15 @@ __device__ __forceinline__ float4 shift_in_right(float4 v, const float *row, int
     return make_float4(v.y, v.z, v.w, r);
 }
 
+// n + w (r - r0), elementwise
+__device__ __forceinline__ float4 dev4(float4 n, float w, float4 r, float4 r0)
+{
+    return make_float4(n.x + w * (r.x - r0.x), n.y + w * (r.y - r0.y), n.z + w * (r.z - r0.z),
+                       n.w + w * (r.w - r0.w));
+}
+
 template <bool CHECK, bool WRITE_P>
-__global__ void __launch_bounds__(kBlock) k_pressure_v4(const __grid_constant__ PressureArgs a)
+__global__ void __launch_bounds__(kBlock) k_pressure(const __grid_constant__ PressureArgs a)
 {
     const Geom &g = a.g;
     const int lane = threadIdx.x & 31;
@@ -292,21 +269,28 @@ __global__ void __launch_bounds__(kBlock) k_pressure_v4(const __grid_constant__ 
         float sd = 0.0f, sdd = 0.0f, sp = 0.0f, spp = 0.0f;
         const bool row_inner = y > 0 && y < g.ny - 1;     // uniform over the block
         bool fast = false;
-        float4 f[8];
+        float4 f[8], r0;
         if (row_inner) {
             // every lane takes part in the shuffles; lanes past the padded row load nothing
             const bool in_row = x0 < p;
-            const bool has_left = x0 >= 1 && in_row, has_right = x0 + 4 < g.nx;
+            const bool hl = x0 >= 1 && in_row, hr = x0 + 4 < g.nx;
             const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-            f[0] = shift_in_left(in_row ? ld4(a.fin[0], o) : z, a.fin[0], o, lane, has_left);           // c = ( 1, 0)
-            f[1] = in_row ? ld4(a.fin[1], o - p) : z;                                                   // c = ( 0, 1)
-            f[2] = shift_in_right(in_row ? ld4(a.fin[2], o) : z, a.fin[2], o, lane, has_right);         // c = (-1, 0)
-            f[3] = in_row ? ld4(a.fin[3], o + p) : z;                                                   // c = ( 0,-1)
-            f[4] = shift_in_left(in_row ? ld4(a.fin[4], o - p) : z, a.fin[4], o - p, lane, has_left);   // c = ( 1, 1)
-            f[5] = shift_in_right(in_row ? ld4(a.fin[5], o - p) : z, a.fin[5], o - p, lane, has_right); // c = (-1, 1)
-            f[6] = shift_in_right(in_row ? ld4(a.fin[6], o + p) : z, a.fin[6], o + p, lane, has_right); // c = (-1,-1)
-            f[7] = shift_in_left(in_row ? ld4(a.fin[7], o + p) : z, a.fin[7], o + p, lane, has_left);   // c = ( 1,-1)
-            fast = has_left && x0 + 4 <= g.nx - 1;
+            const float *R = a.R;
+            r0 = in_row ? ld4(R, o) : z;
+            const float4 rm = in_row ? ld4(R, o - p) : z, rp = in_row ? ld4(R, o + p) : z;
+            const float4 rl = shift_in_left(r0, R, o, lane, hl), rr = shift_in_right(r0, R, o, lane, hr);
+            const float4 rml = shift_in_left(rm, R, o - p, lane, hl), rmr = shift_in_right(rm, R, o - p, lane, hr);
+            const float4 rpl = shift_in_left(rp, R, o + p, lane, hl), rpr = shift_in_right(rp, R, o + p, lane, hr);
+            // a_i = n_i(x - c_i) + w_i (R(x - c_i) - R(x))
+            f[0] = dev4(shift_in_left(in_row ? ld4(a.fin[0], o) : z, a.fin[0], o, lane, hl), wgt(1), rl, r0);
+            f[1] = dev4(in_row ? ld4(a.fin[1], o - p) : z, wgt(2), rm, r0);
+            f[2] = dev4(shift_in_right(in_row ? ld4(a.fin[2], o) : z, a.fin[2], o, lane, hr), wgt(3), rr, r0);
+            f[3] = dev4(in_row ? ld4(a.fin[3], o + p) : z, wgt(4), rp, r0);
+            f[4] = dev4(shift_in_left(in_row ? ld4(a.fin[4], o - p) : z, a.fin[4], o - p, lane, hl), wgt(5), rml, r0);
+            f[5] = dev4(shift_in_right(in_row ? ld4(a.fin[5], o - p) : z, a.fin[5], o - p, lane, hr), wgt(6), rmr, r0);
+            f[6] = dev4(shift_in_right(in_row ? ld4(a.fin[6], o + p) : z, a.fin[6], o + p, lane, hr), wgt(7), rpr, r0);
+            f[7] = dev4(shift_in_left(in_row ? ld4(a.fin[7], o + p) : z, a.fin[7], o + p, lane, hl), wgt(8), rpl, r0);
+            fast = hl && x0 + 4 <= g.nx - 1;
         }
         if (fast) {
             const float4 it = ld4(a.inv_tau, o);
@@ -320,7 +304,7 @@ __global__ void __launch_bounds__(kBlock) k_pressure_v4(const __grid_constant__ 
                     else F.w += a.w.fp[k];
                 }
             }
-            float Pv[4];
+            float dPv[4];
             float4 out[8];
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
@@ -328,13 +312,14 @@ __global__ void __launch_bounds__(kBlock) k_pressure_v4(const __grid_constant__ 
 #pragma unroll
                 for (int i = 0; i < 8; ++i)
                     fc[i] = (&f[i].x)[c];
-                const float P = pressure_of(fc);
+                const float dP = pressure_of(fc);
                 const float itc = (&it.x)[c];
-                const float Fq = 0.125f * (&F.x)[c];
+                const float Fq = 0.125f * (&F.x)[c];   // w_bar_i = 1/8 (Eq. 3-5a)
+                // Eq. 2-1b relative to R: n_i^+ = a_i + (w_i dP - a_i)/tau_f + w_bar_i F~_p
 #pragma unroll
                 for (int i = 0; i < 8; ++i)
-                    (&out[i].x)[c] = fmaf(wgt(i + 1) * P - fc[i], itc, fc[i]) + Fq;
-                Pv[c] = P;
+                    (&out[i].x)[c] = fmaf(wgt(i + 1) * dP - fc[i], itc, fc[i]) + Fq;
+                dPv[c] = dP;
             }
 #pragma unroll
             for (int i = 0; i < 8; ++i)
@@ -343,7 +328,7 @@ __global__ void __launch_bounds__(kBlock) k_pressure_v4(const __grid_constant__ 
                 const float4 Pp = ld4(a.Pio, o);
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
-                    const float d = Pv[c] - (&Pp.x)[c], q = Pv[c] - shift;
+                    const float d = dPv[c] - (&Pp.x)[c], q = ((&r0.x)[c] - shift) + dPv[c];
                     sd += d;
                     sdd += d * d;
                     sp += q;
@@ -351,7 +336,7 @@ __global__ void __launch_bounds__(kBlock) k_pressure_v4(const __grid_constant__ 
                 }
             }
             if (WRITE_P)
-                st4(a.Pio, o, make_float4(Pv[0], Pv[1], Pv[2], Pv[3]));
+                st4(a.Pio, o, make_float4(dPv[0], dPv[1], dPv[2], dPv[3]));
         } else {
             // edge rows, edge columns and the ragged tail: scalar nodes with the wall rules
             for (int c = 0; c < 4; ++c) {
@@ -360,8 +345,8 @@ __global__ void __launch_bounds__(kBlock) k_pressure_v4(const __grid_constant__ 
                     break;
                 const int oc = o + c;
                 float fc[8];
-                gather_f(a.fin, g, a.Pb, x, y, oc, fc);
-                const float P = pressure_of(fc);
+                gather_a(a.fin, a.R, g, a.Pb, x, y, oc, fc);
+                const float dP = pressure_of(fc);
                 const float itc = a.inv_tau[oc];
                 float F = a.Fp ? a.Fp[oc] : 0.0f;
                 for (int k = 0; k < a.w.n; ++k)
@@ -370,16 +355,16 @@ __global__ void __launch_bounds__(kBlock) k_pressure_v4(const __grid_constant__ 
                 const float Fq = 0.125f * F;
 #pragma unroll
                 for (int i = 0; i < 8; ++i)
-                    a.fout[i][oc] = fmaf(wgt(i + 1) * P - fc[i], itc, fc[i]) + Fq;
+                    a.fout[i][oc] = fmaf(wgt(i + 1) * dP - fc[i], itc, fc[i]) + Fq;
                 if (CHECK) {
-                    const float d = P - a.Pio[oc], q = P - shift;
+                    const float d = dP - a.Pio[oc], q = (a.R[oc] - shift) + dP;
                     sd += d;
                     sdd += d * d;
                     sp += q;
                     spp += q * q;
                 }
                 if (WRITE_P)
-                    a.Pio[oc] = P;
+                    a.Pio[oc] = dP;
             }
         }
         if (CHECK) {
@@ -528,7 +513,8 @@ __global__ void __launch_bounds__(kBlock) k_saturation(const __grid_constant__ S
             continue;
         const int o = y * g.pitch + x;
         float f[8], q[9];
-        gather_f(a.fin, g, a.Pb, x, y, o, f);
+        gather_a(a.fin, a.R, g, a.Pb, x, y, o, f);
+        a.Pnew[o] = a.R[o] + pressure_of(f);
         gather_g(a.gin, g, m, a.Sb, x, y, o, q);
         const float sum = (q[0] + ((q[1] + q[2]) + (q[3] + q[4]))) + ((q[5] + q[6]) + (q[7] + q[8]));
         const float Fs = saturation_source(m, a.w, a.Fs, o, sum * m.inv_phi);
@@ -593,7 +579,8 @@ __global__ void __launch_bounds__(kBlock) k_init_g(const __grid_constant__ InitG
         const float S0 = a.S0[o];
         const float sx = fd_axis(a.S0, g, x, y, 0), sy = fd_axis(a.S0, g, x, y, 1);
         float f[8];
-        gather_f(a.fin, g, a.Pb, x, y, o, f);
+        gather_a(a.fin, a.R, g, a.Pb, x, y, o, f);
+        a.Pnew[o] = a.R[o] + pressure_of(f);
         float mx, my;
         first_moment(f, mx, my);
         const float it = a.inv_tau[o];
@@ -628,26 +615,22 @@ __global__ void __launch_bounds__(kBlock) k_init_g(const __grid_constant__ InitG
     }
 }
 
-// f_i^+ = w_i P0 (Eq. 3-3 for i >= 1); P0 may be null (zero)
-__global__ void __launch_bounds__(kBlock) k_fill_f_eq(float *f0, float *f1, float *f2, float *f3,
-                                                      float *f4, float *f5, float *f6, float *f7,
-                                                      const float *P0, Geom g)
+// move the reference pressure to Pnew: n_i += w_i (R - Pnew), R = Pnew (own node only)
+__global__ void __launch_bounds__(kBlock) k_rebase(const __grid_constant__ RebaseArgs a)
 {
+    const Geom &g = a.g;
     for (int t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
         const int y = t / g.tiles_x;
         const int x = (t - y * g.tiles_x) * kBlock + threadIdx.x;
         if (x >= g.nx)
             continue;
         const int o = y * g.pitch + x;
-        const float P = P0 ? P0[o] : 0.0f;
-        f0[o] = wgt(1) * P;
-        f1[o] = wgt(2) * P;
-        f2[o] = wgt(3) * P;
-        f3[o] = wgt(4) * P;
-        f4[o] = wgt(5) * P;
-        f5[o] = wgt(6) * P;
-        f6[o] = wgt(7) * P;
-        f7[o] = wgt(8) * P;
+        const float pn = a.Pnew[o];
+        const float d = a.R[o] - pn;
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            a.n[i][o] += wgt(i + 1) * d;
+        a.R[o] = pn;
     }
 }
 
@@ -680,10 +663,10 @@ __global__ void __launch_bounds__(kBlock) k_fields(const __grid_constant__ Field
         const int o = y * g.pitch + x;
         const long long c = (long long)y * g.nx + x;
         float f[8];
-        gather_f(a.fin, g, a.Pb, x, y, o, f);
+        gather_a(a.fin, a.R, g, a.Pb, x, y, o, f);
         const float S = a.S[o];
         if (a.P_out)
-            a.P_out[c] = pressure_of(f);
+            a.P_out[c] = a.R[o] + pressure_of(f);
         if (a.S_out)
             a.S_out[c] = S;
         if (a.ux_out || a.uy_out) {
@@ -744,33 +727,34 @@ __global__ void __launch_bounds__(256) k_subtract_mean(float *x, long long n, co
 // ======================================================================================
 namespace lbm2p_launch {
 
-#ifdef LBM2P_SCALAR_SWEEP
-#define K_PRESSURE k_pressure
-#else
-#define K_PRESSURE k_pressure_v4
-#endif
-
 static cudaStream_t S(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
-int max_blocks_per_sm_pressure()
+int max_blocks_per_sm_pressure(bool check)
 {
     int a = 0, b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, K_PRESSURE<false, false>, kBlock, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, K_PRESSURE<true, true>, kBlock, 0);
+    if (check) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pressure<true, true>, kBlock, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pressure<true, false>, kBlock, 0);
+    } else {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pressure<false, false>, kBlock, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pressure<false, true>, kBlock, 0);
+    }
     int m = a < b ? a : b;
     return m > 0 ? m : 1;
 }
 
 void pressure_sweep(const PressureArgs &a, bool check, bool write_p, int grid, void *stream)
 {
+    // grid: resident capacity of the plain sweep; check sweeps use the capacity of theirs
+    
     if (check && write_p)
-        K_PRESSURE<true, true><<<grid, kBlock, 0, S(stream)>>>(a);
+        k_pressure<true, true><<<grid, kBlock, 0, S(stream)>>>(a);
     else if (check)
-        K_PRESSURE<true, false><<<grid, kBlock, 0, S(stream)>>>(a);
+        k_pressure<true, false><<<grid, kBlock, 0, S(stream)>>>(a);
     else if (write_p)
-        K_PRESSURE<false, true><<<grid, kBlock, 0, S(stream)>>>(a);
+        k_pressure<false, true><<<grid, kBlock, 0, S(stream)>>>(a);
     else
-        K_PRESSURE<false, false><<<grid, kBlock, 0, S(stream)>>>(a);
+        k_pressure<false, false><<<grid, kBlock, 0, S(stream)>>>(a);
 }
 
 void residual_finalize(const double *partials, int nparts, long long nnodes, float *shift,
@@ -794,10 +778,9 @@ void init_g(const InitGArgs &a, int grid, void *stream)
     k_init_g<<<grid, kBlock, 0, S(stream)>>>(a);
 }
 
-void fill_f_eq(float *const fout[8], const float *P0, Geom g, int grid, void *stream)
+void rebase(const RebaseArgs &a, int grid, void *stream)
 {
-    k_fill_f_eq<<<grid, kBlock, 0, S(stream)>>>(fout[0], fout[1], fout[2], fout[3], fout[4],
-                                                 fout[5], fout[6], fout[7], P0, g);
+    k_rebase<<<grid, kBlock, 0, S(stream)>>>(a);
 }
 
 void tau_from_S(float *inv_tau, const float *Sp, const float *K, Geom g, Model m, int grid,
@@ -842,8 +825,8 @@ static cudaError_t add_kernel(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraph
 cudaError_t node_pressure(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
                           const PressureArgs &a, bool check, bool write_p, int grid)
 {
-    void *func = check ? (write_p ? (void *)K_PRESSURE<true, true> : (void *)K_PRESSURE<true, false>)
-                       : (write_p ? (void *)K_PRESSURE<false, true> : (void *)K_PRESSURE<false, false>);
+    void *func = check ? (write_p ? (void *)k_pressure<true, true> : (void *)k_pressure<true, false>)
+                       : (write_p ? (void *)k_pressure<false, true> : (void *)k_pressure<false, false>);
     void *args[] = {(void *)&a};
     return add_kernel(n, g, dep, func, grid, kBlock, args);
 }
@@ -876,6 +859,13 @@ cudaError_t node_saturation(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNo
 {
     void *args[] = {(void *)&a};
     return add_kernel(n, g, dep, (void *)k_saturation, grid, kBlock, args);
+}
+
+cudaError_t node_rebase(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
+                        const RebaseArgs &a, int grid)
+{
+    void *args[] = {(void *)&a};
+    return add_kernel(n, g, dep, (void *)k_rebase, grid, kBlock, args);
 }
 
 }  // namespace lbm2p_launch

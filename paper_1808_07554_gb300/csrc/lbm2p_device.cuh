@@ -6,9 +6,16 @@
 // weights 0, 1/8 (x8); c_s^2 = 1/3 in lattice units.
 //
 // Storage (structure of arrays, row pitch padded to 32 floats):
-//   f: 8 planes, f_1 .. f_8 (plane p holds direction p + 1).  f_0 is never stored: it
-//      enters neither P (Eq. 3-9a sums i = 1..8), nor grad P (c_0 = 0), nor any other f_i.
-//   g: 9 planes, g_0 .. g_8.
+//   f: 8 planes, direction p + 1 in plane p, stored as deviations from a reference
+//      pressure R(x):  n_i(x) = f_i^+(x) - w_i R(x).  R is fixed during the pressure
+//      sub-iteration of a step and moved to the step's pressure afterwards ("rebase"), so
+//      the stored values are the small non-equilibrium and increment parts of f and FP32
+//      resolves them finely.  Every sweep works on a_i = f_i(x) - w_i R(x) (pulled value
+//      relative to the node's own reference) and dP = P - R(x); because f^eq is linear in
+//      P, the collision keeps its form: n_i^+ = a_i + (w_i dP - a_i)/tau_f + F~_p/8.
+//      f_0 is never stored: it enters neither P (Eq. 3-9a sums i = 1..8), nor grad P
+//      (c_0 = 0), nor any other f_i.
+//   g: 9 planes, g_0 .. g_8, plain post-collision values.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -78,8 +85,9 @@ struct Wells {
 };
 
 struct PressureArgs {
-    const float *fin[8];
+    const float *fin[8];     // n_i of the previous sweep
     float *fout[8];
+    const float *R;          // reference pressure of this step
     const float *inv_tau;
     const float *Fp;         // dense F~_p plane (lattice units) or nullptr
     float *Pio;              // pressure plane written (WRITE_P) / read (CHECK)
@@ -103,6 +111,8 @@ struct RefreshArgs {        // stream g, S^n, 1/tau_f
 
 struct SaturationArgs {     // stream f and g, grad P, collide g
     const float *fin[8];
+    const float *R;
+    float *Pnew;             // P of the converged pressure state (for the rebase)
     const float *gin[9];
     float *gout[9];
     const float *K;
@@ -118,6 +128,8 @@ struct SaturationArgs {     // stream f and g, grad P, collide g
 
 struct InitGArgs {          // Eqs. gini, gneq and the t = 0 collision
     const float *fin[8];
+    const float *R;
+    float *Pnew;
     float *gout[9];
     const float *K;
     const float *inv_tau;
@@ -133,6 +145,7 @@ struct InitGArgs {          // Eqs. gini, gneq and the t = 0 collision
 
 struct FieldsArgs {         // P, S, u into compact [ny][nx] outputs
     const float *fin[8];
+    const float *R;
     const float *inv_tau;
     const float *K;
     const float *S;
@@ -140,6 +153,13 @@ struct FieldsArgs {         // P, S, u into compact [ny][nx] outputs
     float *P_out, *S_out, *ux_out, *uy_out;   // any may be nullptr
     Geom g;
     Model m;
+};
+
+struct RebaseArgs {         // n_i += w_i (R - Pnew); R = Pnew  (node-local)
+    float *n[8];
+    float *R;
+    const float *Pnew;
+    Geom g;
 };
 
 struct ResidualOut {        // written by the finalize kernel
@@ -163,14 +183,14 @@ struct LoopCtl {
 // Launchers implemented in kernels.cu (all asynchronous on `stream`).
 namespace lbm2p_launch {
 using namespace lbm2p_dev;
-int max_blocks_per_sm_pressure();
+int max_blocks_per_sm_pressure(bool check);
 void pressure_sweep(const PressureArgs &a, bool check, bool write_p, int grid, void *stream);
 void residual_finalize(const double *partials, int nparts, long long nnodes, float *shift,
                        ResidualOut *out, void *stream);
 void refresh(const RefreshArgs &a, int grid, void *stream);
 void saturation(const SaturationArgs &a, int grid, void *stream);
 void init_g(const InitGArgs &a, int grid, void *stream);
-void fill_f_eq(float *const fout[8], const float *P0, Geom g, int grid, void *stream);
+void rebase(const RebaseArgs &a, int grid, void *stream);
 void tau_from_S(float *inv_tau, const float *S, const float *K, Geom g, Model m, int grid,
                 void *stream);
 void fields(const FieldsArgs &a, int grid, void *stream);
@@ -186,6 +206,8 @@ cudaError_t node_refresh(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_
                          const RefreshArgs &a, int grid);
 cudaError_t node_saturation(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
                             const SaturationArgs &a, int grid);
+cudaError_t node_rebase(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
+                        const RebaseArgs &a, int grid);
 void sum_compact(const float *x, long long n, double *partials, int grid, void *stream);
 void finalize_mean(const double *partials, int nparts, long long n, double *mean, void *stream);
 void subtract_mean(float *x, long long n, const double *mean, int grid, void *stream);

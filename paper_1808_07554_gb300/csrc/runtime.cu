@@ -19,6 +19,7 @@ using namespace lbm2p_dev;
 namespace {
 
 thread_local std::string g_create_error;
+constexpr int kStatePlanes = 20;   // n_1..n_8, g_0..g_8, 1/tau_f, S, R
 
 struct Alloc {
     void *ptr;
@@ -37,11 +38,13 @@ struct lbm2p {
     Wells wells{};
     double s = 0, tau_g = 0, D_ref = 0;
     int grid = 0;              // blocks of every grid-stride lattice launch
+    int grid_check = 0;        // blocks of a pressure sweep that accumulates the residual
     void *stream = nullptr;
     std::vector<Alloc> allocs;
     float *fbuf[2][8] = {};
     float *gbuf[2][9] = {};
     float *inv_tau = nullptr, *K = nullptr, *S = nullptr, *Pio = nullptr, *tmp = nullptr;
+    float *R = nullptr;                // reference pressure of the pressure populations
     float *Fp = nullptr, *Fs = nullptr;
     float *Pb[4] = {}, *Sb[4] = {};
     double *partials = nullptr, *mean = nullptr;
@@ -202,6 +205,7 @@ PressureArgs pressure_args(lbm2p *h, int src)
         a.fin[i] = h->fbuf[src][i];
         a.fout[i] = h->fbuf[1 - src][i];
     }
+    a.R = h->R;
     a.inv_tau = h->inv_tau;
     a.Fp = h->Fp;
     a.Pio = h->Pio;
@@ -235,6 +239,8 @@ SaturationArgs saturation_args(lbm2p *h, int pf, int pg)
     SaturationArgs a{};
     for (int i = 0; i < 8; ++i)
         a.fin[i] = h->fbuf[pf][i];
+    a.R = h->R;
+    a.Pnew = h->Pio;
     for (int i = 0; i < 9; ++i) {
         a.gin[i] = h->gbuf[pg][i];
         a.gout[i] = h->gbuf[1 - pg][i];
@@ -253,6 +259,17 @@ SaturationArgs saturation_args(lbm2p *h, int pf, int pg)
     return a;
 }
 
+
+RebaseArgs rebase_args(lbm2p *h, int pf)
+{
+    RebaseArgs a{};
+    for (int i = 0; i < 8; ++i)
+        a.n[i] = h->fbuf[pf][i];
+    a.R = h->R;
+    a.Pnew = h->Pio;
+    a.g = h->geom;
+    return a;
+}
 
 // ---- graph-resident sub-iteration ----------------------------------------------------------
 // Appends to G: reset(ctl) -> event(sw0) -> WHILE{ m sweeps from f parity pf, the last one
@@ -280,12 +297,12 @@ lbm2p_status add_loop(lbm2p *h, cudaGraph_t G, const cudaGraphNode_t *dep, int p
         cudaGraphNode_t n;
         PressureArgs a = pressure_args(h, src);
         CUDA_TRY(h, lbm2p_launch::node_pressure(&n, body, prev ? &prev : nullptr, a, kk == m,
-                                                kk == m - 1, h->grid));
+                                                kk == m - 1, kk == m ? h->grid_check : h->grid));
         prev = n;
         src = 1 - src;
     }
     cudaGraphNode_t fin;
-    CUDA_TRY(h, lbm2p_launch::node_finalize_loop(&fin, body, &prev, h->partials, h->grid,
+    CUDA_TRY(h, lbm2p_launch::node_finalize_loop(&fin, body, &prev, h->partials, h->grid_check,
                                                  h->nnodes, h->shift, h->res, h->ctl, hd));
     CUDA_TRY(h, cudaGraphAddEventRecordNode(&ev1, G, &wn, 1, h->ev_sw1));
     *last = ev1;
@@ -322,6 +339,8 @@ lbm2p_status step_graph(lbm2p *h, int pf, int pg, cudaGraphExec_t *out)
             return e;
         CUDA_TRY(h, lbm2p_launch::node_saturation(&ns, G, &last, saturation_args(h, pf, pg),
                                                   h->grid));
+        cudaGraphNode_t nb;
+        CUDA_TRY(h, lbm2p_launch::node_rebase(&nb, G, &ns, rebase_args(h, pf), h->grid));
         CUDA_TRY(h, cudaGraphInstantiate(&h->step_x[pf][pg], G, 0));
     }
     *out = h->step_x[pf][pg];
@@ -381,7 +400,8 @@ lbm2p_status pressure_solve(lbm2p *h, int replay, int *k_out, double *r_out, flo
             const bool check = is_check(kk) && kk >= 2;
             const bool write_p = is_check(kk + 1) && kk + 1 >= 2;
             PressureArgs a = pressure_args(h, h->cur_f);
-            lbm2p_launch::pressure_sweep(a, check, write_p, h->grid, h->stream);
+            lbm2p_launch::pressure_sweep(a, check, write_p, check ? h->grid_check : h->grid,
+                                         h->stream);
             LAUNCHED(h, "pressure sweep");
             h->cur_f = 1 - h->cur_f;
             h->sweeps += 1;
@@ -392,7 +412,7 @@ lbm2p_status pressure_solve(lbm2p *h, int replay, int *k_out, double *r_out, flo
         return LBM2P_OK;
     };
     auto read_residual = [&]() -> lbm2p_status {
-        lbm2p_launch::residual_finalize(h->partials, h->grid, h->nnodes, h->shift, h->res,
+        lbm2p_launch::residual_finalize(h->partials, h->grid_check, h->nnodes, h->shift, h->res,
                                         h->stream);
         LAUNCHED(h, "residual finalize");
         CUDA_TRY(h, cudaMemcpyAsync(h->res_host, h->res, sizeof(ResidualOut),
@@ -499,7 +519,7 @@ lbm2p_status one_step(lbm2p *h, int replay, lbm2p_step_stats *stats)
         float sw_ms = -1.0f, step_ms = -1.0f;
         if ((e = read_loop(h, &k, &r, &sw_ms)) != LBM2P_OK)
             return e;
-        h->launches += 2;                 // refresh, saturation
+        h->launches += 3;                 // refresh, saturation, rebase
         h->cur_g = 1 - h->cur_g;
         if (h->timing)
             CUDA_TRY(h, cudaEventElapsedTime(&step_ms, h->ev_step0, h->ev_step1));
@@ -536,6 +556,8 @@ lbm2p_status one_step(lbm2p *h, int replay, lbm2p_step_stats *stats)
     // a4/a5: grad P and the saturation update
     lbm2p_launch::saturation(saturation_args(h, h->cur_f, h->cur_g), h->grid, h->stream);
     LAUNCHED(h, "saturation");
+    lbm2p_launch::rebase(rebase_args(h, h->cur_f), h->grid, h->stream);
+    LAUNCHED(h, "rebase");
     h->cur_g = 1 - h->cur_g;
     float step_ms = -1.0f;
     if (h->timing) {
@@ -688,11 +710,16 @@ lbm2p_status build(lbm2p *h, const lbm2p_inputs *in, lbm2p_step_stats *init_stat
     int dev = 0, sms = 0;
     CUDA_TRY(h, cudaGetDevice(&dev));
     CUDA_TRY(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int per_sm = lbm2p_launch::max_blocks_per_sm_pressure();
-    long long grid = (long long)sms * per_sm;
-    if (grid > g.ntiles)
-        grid = g.ntiles;
-    h->grid = (int)(grid > 0 ? grid : 1);
+    // grids: the resident-block capacity of the GPU (multiples of the SM count), capped by
+    // the number of row tiles of the widest kernel work item
+    auto cap_grid = [&](long long blocks) {
+        const long long tiles = (long long)g.ntiles;
+        if (blocks > tiles)
+            blocks = tiles;
+        return (int)(blocks > 0 ? blocks : 1);
+    };
+    h->grid = cap_grid((long long)sms * lbm2p_launch::max_blocks_per_sm_pressure(false));
+    h->grid_check = cap_grid((long long)sms * lbm2p_launch::max_blocks_per_sm_pressure(true));
     const size_t pb = (size_t)h->plane * sizeof(float);
     auto plane_alloc = [&](float **dst) -> bool {
         *dst = (float *)dev_alloc(h, pb);
@@ -706,7 +733,7 @@ lbm2p_status build(lbm2p *h, const lbm2p_inputs *in, lbm2p_step_stats *init_stat
             ok = ok && plane_alloc(&h->gbuf[b][i]);
     }
     ok = ok && plane_alloc(&h->inv_tau) && plane_alloc(&h->K) && plane_alloc(&h->S) &&
-         plane_alloc(&h->Pio) && plane_alloc(&h->tmp);
+         plane_alloc(&h->Pio) && plane_alloc(&h->tmp) && plane_alloc(&h->R);
     if (in->Fp)
         ok = ok && plane_alloc(&h->Fp);
     if (in->Fs)
@@ -718,7 +745,7 @@ lbm2p_status build(lbm2p *h, const lbm2p_inputs *in, lbm2p_step_stats *init_stat
             ok = ok && h->Pb[s] && h->Sb[s];
         }
     }
-    h->partials = (double *)dev_alloc(h, (size_t)h->grid * 4 * sizeof(double));
+    h->partials = (double *)dev_alloc(h, (size_t)(h->grid > h->grid_check ? h->grid : h->grid_check) * 4 * sizeof(double));
     h->mean = (double *)dev_alloc(h, 64);
     h->shift = (float *)dev_alloc(h, 64);
     h->res = (ResidualOut *)dev_alloc(h, sizeof(ResidualOut));
@@ -768,16 +795,11 @@ lbm2p_status build(lbm2p *h, const lbm2p_inputs *in, lbm2p_step_stats *init_stat
     // a6: f = f^eq(P0), tau_f from S0, the t = 0 pressure solve, then g(0) and its collision
     if ((e = upload_plane(h, h->tmp, in->S0, 1.0)) != LBM2P_OK)   // tmp holds S0
         return e;
-    const float *P0dev = nullptr;
-    if (in->P0) {
-        if ((e = upload_plane(h, h->Pio, in->P0, 1.0)) != LBM2P_OK)
-            return e;
-        P0dev = h->Pio;
-    }
+    // f^+ = f^eq(P0): reference R = P0 and zero deviations (the planes are zeroed above)
+    if (in->P0 && (e = upload_plane(h, h->R, in->P0, 1.0)) != LBM2P_OK)
+        return e;
     h->cur_f = 0;
     h->cur_g = 0;
-    lbm2p_launch::fill_f_eq(h->fbuf[0], P0dev, g, h->grid, h->stream);
-    LAUNCHED(h, "fill f_eq");
     lbm2p_launch::tau_from_S(h->inv_tau, h->tmp, h->K, g, m, h->grid, h->stream);
     LAUNCHED(h, "tau from S");
     int k0 = 0;
@@ -796,6 +818,8 @@ lbm2p_status build(lbm2p *h, const lbm2p_inputs *in, lbm2p_step_stats *init_stat
     InitGArgs a{};
     for (int i = 0; i < 8; ++i)
         a.fin[i] = h->fbuf[h->cur_f][i];
+    a.R = h->R;
+    a.Pnew = h->Pio;
     for (int i = 0; i < 9; ++i)
         a.gout[i] = h->gbuf[0][i];
     a.K = h->K;
@@ -812,6 +836,8 @@ lbm2p_status build(lbm2p *h, const lbm2p_inputs *in, lbm2p_step_stats *init_stat
     a.w = w;
     lbm2p_launch::init_g(a, h->grid, h->stream);
     LAUNCHED(h, "init g");
+    lbm2p_launch::rebase(rebase_args(h, h->cur_f), h->grid, h->stream);
+    LAUNCHED(h, "rebase");
     h->cur_g = 0;
     CUDA_TRY(h, cudaStreamSynchronize(st));
     return ps;
@@ -966,6 +992,7 @@ static lbm2p_status run_fields(lbm2p *h, float *P, float *S, float *ux, float *u
     FieldsArgs a{};
     for (int i = 0; i < 8; ++i)
         a.fin[i] = h->fbuf[h->cur_f][i];
+    a.R = h->R;
     a.inv_tau = h->inv_tau;
     a.K = h->K;
     a.S = h->S;
@@ -1008,7 +1035,7 @@ lbm2p_status lbm2p_fields(lbm2p *h, float *P, float *S, int mean_free_P, int on_
 
 size_t lbm2p_state_count(const lbm2p *h)
 {
-    return h ? (size_t)19 * (size_t)h->nnodes : 0;
+    return h ? (size_t)kStatePlanes * (size_t)h->nnodes : 0;
 }
 
 static lbm2p_status state_copy(lbm2p *h, float *buf, size_t count, int on_device, bool out)
@@ -1018,18 +1045,19 @@ static lbm2p_status state_copy(lbm2p *h, float *buf, size_t count, int on_device
     if (!buf || count != lbm2p_state_count(h))
         return fail(h, LBM2P_EINVAL, "state buffer must hold %zu floats", lbm2p_state_count(h));
     cudaStream_t st = (cudaStream_t)h->stream;
-    float *planes[19];
+    float *planes[kStatePlanes];
     for (int i = 0; i < 8; ++i)
         planes[i] = h->fbuf[h->cur_f][i];
     for (int i = 0; i < 9; ++i)
         planes[8 + i] = h->gbuf[h->cur_g][i];
     planes[17] = h->inv_tau;
     planes[18] = h->S;
+    planes[19] = h->R;
     const size_t row = (size_t)h->nx * sizeof(float);
     const size_t dpitch = (size_t)h->pitch * sizeof(float);
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice
                                           : (out ? cudaMemcpyDeviceToHost : cudaMemcpyHostToDevice);
-    for (int c = 0; c < 19; ++c) {
+    for (int c = 0; c < kStatePlanes; ++c) {
         float *hb = buf + (size_t)c * h->nnodes;
         if (out)
             CUDA_TRY(h, cudaMemcpy2DAsync(hb, row, planes[c], dpitch, row, (size_t)h->ny, kind, st));
