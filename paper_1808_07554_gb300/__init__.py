@@ -100,6 +100,10 @@ def load_library(path: str = LIB_PATH):
         "lbm2p_set_state": (C.c_int, [H, fp, C.c_size_t, C.c_int]),
         "lbm2p_set_timing": (C.c_int, [H, C.c_int]),
         "lbm2p_counters": (C.c_int, [H, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
+        "lbm2p_pressure_sweep_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int),
+                                                   C.POINTER(fp), C.POINTER(fp), fp, fp, fp,
+                                                   C.POINTER(fp), fp, C.POINTER(C.c_double),
+                                                   C.c_void_p]),
         "lbm2p_last_error": (C.c_char_p, [H]),
         "lbm2p_destroy": (None, [H]),
     }
@@ -197,6 +201,23 @@ def lbm2p_counters(h):
     a, b = C.c_longlong(0), C.c_longlong(0)
     _check(_lib_or_raise().lbm2p_counters(h, C.byref(a), C.byref(b)), h)
     return a.value, b.value
+
+
+def lbm2p_pressure_sweep_noalloc(nx, ny, pitch, bc, n_in, n_out, R, inv_tau, Fp, P_b, dP,
+                                 stream=None):
+    """Device pointers (ints) in, residual out; allocates nothing (see include/lbm2p.h)."""
+    fp = C.POINTER(C.c_float)
+    cast = lambda p: C.cast(C.c_void_p(p), fp) if p else None
+    bcs = (C.c_int * 4)(*[int(b) for b in bc])
+    nin = (fp * 8)(*[cast(p) for p in n_in])
+    nout = (fp * 8)(*[cast(p) for p in n_out])
+    pb = (fp * 4)(*[cast(p) for p in (P_b if P_b is not None else [0, 0, 0, 0])])
+    r = C.c_double(0.0)
+    st = _lib_or_raise().lbm2p_pressure_sweep_noalloc(
+        int(nx), int(ny), int(pitch), bcs, nin, nout, cast(R), cast(inv_tau), cast(Fp), pb,
+        cast(dP), C.byref(r), C.c_void_p(stream) if stream else None)
+    _check(st, None)
+    return r.value
 
 
 def lbm2p_destroy(h):

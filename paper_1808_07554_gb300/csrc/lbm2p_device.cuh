@@ -180,6 +180,11 @@ struct LoopCtl {
 
 }  // namespace lbm2p_dev
 
+// Error text for calls made without a handle (read back by lbm2p_last_error(NULL)).
+namespace lbm2p_internal {
+lbm2p_status set_global_error(lbm2p_status st, const char *fmt, ...);
+}
+
 // Launchers implemented in kernels.cu (all asynchronous on `stream`).
 namespace lbm2p_launch {
 using namespace lbm2p_dev;

@@ -845,6 +845,19 @@ lbm2p_status build(lbm2p *h, const lbm2p_inputs *in, lbm2p_step_stats *init_stat
 
 }  // namespace
 
+namespace lbm2p_internal {
+lbm2p_status set_global_error(lbm2p_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_create_error = buf;
+    return st;
+}
+}  // namespace lbm2p_internal
+
 extern "C" {
 
 int lbm2p_abi_version(void) { return LBM2P_ABI_VERSION; }
