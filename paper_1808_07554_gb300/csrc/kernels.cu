@@ -400,6 +400,73 @@ __global__ void __launch_bounds__(kBlock) k_pressure(const __grid_constant__ Pre
     }
 }
 
+#ifdef LBM2P_SWEEP_SCALAR
+// One node per thread (row tiles of kBlock nodes): the same sweep with scalar loads.
+template <bool CHECK, bool WRITE_P>
+__global__ void __launch_bounds__(kBlock) k_pressure_scalar(const __grid_constant__ PressureArgs a)
+{
+    const Geom &g = a.g;
+    const int lane = threadIdx.x & 31;
+    double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
+    const float shift = CHECK ? *a.shift : 0.0f;
+    for (int t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
+        const int y = t / g.tiles_x;
+        const int x = (t - y * g.tiles_x) * kBlock + threadIdx.x;
+        float d = 0.0f, q = 0.0f;
+        if (x < g.nx) {
+            const int o = y * g.pitch + x;
+            float f[8];
+            gather_a(a.fin, a.R, g, a.Pb, x, y, o, f);
+            const float dP = pressure_of(f);
+            const float it = a.inv_tau[o];
+            float F = a.Fp ? a.Fp[o] : 0.0f;
+            for (int k = 0; k < a.w.n; ++k)
+                if (o == a.w.idx[k])
+                    F += a.w.fp[k];
+            const float Fq = 0.125f * F;
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                a.fout[i][o] = fmaf(wgt(i + 1) * dP - f[i], it, f[i]) + Fq;
+            if (CHECK) {
+                d = dP - a.Pio[o];
+                q = (a.R[o] - shift) + dP;
+            }
+            if (WRITE_P)
+                a.Pio[o] = dP;
+        }
+        if (CHECK) {
+            const float s0 = warp_sum(d), s1 = warp_sum(d * d), s2 = warp_sum(q), s3 = warp_sum(q * q);
+            if (lane == 0) {
+                acc0 += s0;
+                acc1 += s1;
+                acc2 += s2;
+                acc3 += s3;
+            }
+        }
+    }
+    if (CHECK) {
+        __shared__ double red[kBlock / 32][4];
+        const int warp = threadIdx.x >> 5;
+        if (lane == 0) {
+            red[warp][0] = acc0;
+            red[warp][1] = acc1;
+            red[warp][2] = acc2;
+            red[warp][3] = acc3;
+        }
+        __syncthreads();
+        if (threadIdx.x < 4) {
+            double s = 0.0;
+            for (int w = 0; w < kBlock / 32; ++w)
+                s += red[w][threadIdx.x];
+            a.partials[4 * blockIdx.x + threadIdx.x] = s;
+        }
+    }
+}
+#define K_SWEEP k_pressure_scalar
+#else
+#define K_SWEEP k_pressure
+#endif
+
 // r = ||dP - mean dP|| / ||P - mean P|| from the block partials (FP64, fixed order).
 // Called by all 256 threads of one block; returns r in thread 0.
 __device__ double finalize_residual(const double *__restrict__ partials, int nparts,
@@ -733,11 +800,11 @@ int max_blocks_per_sm_pressure(bool check)
 {
     int a = 0, b = 0;
     if (check) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pressure<true, true>, kBlock, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pressure<true, false>, kBlock, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, K_SWEEP<true, true>, kBlock, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, K_SWEEP<true, false>, kBlock, 0);
     } else {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pressure<false, false>, kBlock, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pressure<false, true>, kBlock, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, K_SWEEP<false, false>, kBlock, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, K_SWEEP<false, true>, kBlock, 0);
     }
     int m = a < b ? a : b;
     return m > 0 ? m : 1;
@@ -748,13 +815,13 @@ void pressure_sweep(const PressureArgs &a, bool check, bool write_p, int grid, v
     // grid: resident capacity of the plain sweep; check sweeps use the capacity of theirs
     
     if (check && write_p)
-        k_pressure<true, true><<<grid, kBlock, 0, S(stream)>>>(a);
+        K_SWEEP<true, true><<<grid, kBlock, 0, S(stream)>>>(a);
     else if (check)
-        k_pressure<true, false><<<grid, kBlock, 0, S(stream)>>>(a);
+        K_SWEEP<true, false><<<grid, kBlock, 0, S(stream)>>>(a);
     else if (write_p)
-        k_pressure<false, true><<<grid, kBlock, 0, S(stream)>>>(a);
+        K_SWEEP<false, true><<<grid, kBlock, 0, S(stream)>>>(a);
     else
-        k_pressure<false, false><<<grid, kBlock, 0, S(stream)>>>(a);
+        K_SWEEP<false, false><<<grid, kBlock, 0, S(stream)>>>(a);
 }
 
 void residual_finalize(const double *partials, int nparts, long long nnodes, float *shift,
@@ -825,8 +892,8 @@ static cudaError_t add_kernel(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraph
 cudaError_t node_pressure(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
                           const PressureArgs &a, bool check, bool write_p, int grid)
 {
-    void *func = check ? (write_p ? (void *)k_pressure<true, true> : (void *)k_pressure<true, false>)
-                       : (write_p ? (void *)k_pressure<false, true> : (void *)k_pressure<false, false>);
+    void *func = check ? (write_p ? (void *)K_SWEEP<true, true> : (void *)K_SWEEP<true, false>)
+                       : (write_p ? (void *)K_SWEEP<false, true> : (void *)K_SWEEP<false, false>);
     void *args[] = {(void *)&a};
     return add_kernel(n, g, dep, func, grid, kBlock, args);
 }
