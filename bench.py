@@ -345,7 +345,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="five_spot_1024")
-    ap.add_argument("--check-every", type=int, default=10)
+    ap.add_argument("--check-every", type=int, default=8)
     ap.add_argument("--max-sub-iters", type=int, default=10_000_000)
     ap.add_argument("--cold-start", action="store_true",
                     help="start the t = 0 pressure solve from P0 = 0 instead of a coarse solve")

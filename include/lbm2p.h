@@ -42,7 +42,7 @@
 extern "C" {
 #endif
 
-#define LBM2P_ABI_VERSION 1
+#define LBM2P_ABI_VERSION 2
 /* Sparse wells passed to the sweep kernels as launch arguments (more wells: error). */
 #define LBM2P_MAX_WELLS 16
 
@@ -102,6 +102,10 @@ typedef struct {
     int bc[4];                  /* lbm2p_bc_kind per side (XMIN, XMAX, YMIN, YMAX); a
                                    periodic side must be paired with its opposite */
     int storage;                /* lbm2p_storage */
+    int fuse_sweeps;            /* pressure sweeps fused per kernel launch: 0 = automatic,
+                                   1 = one sweep per launch, 2 or 4 = that many (results are
+                                   identical bit for bit; fusion reads and writes the
+                                   populations once per fused group of sweeps) */
     void *stream;               /* cudaStream_t the work is enqueued on */
     void *(*alloc)(size_t bytes, void *ctx);            /* optional device allocator */
     void (*release)(void *ptr, size_t bytes, void *ctx); /* its matching free */
@@ -136,7 +140,7 @@ typedef struct {
 int lbm2p_abi_version(void);
 
 /* Fill params with defaults: phi = 0.2, beta = 0.4, quadratic mobility with mu_w = 1,
-   mu_n = 2, D_s = 0.01, REFERENCE mode with tau_p = 1, tol = 1e-8, check_every = 10,
+   mu_n = 2, D_s = 0.01, REFERENCE mode with tau_p = 1, tol = 1e-8, check_every = 8,
    max_sub_iters = 10^7, no-flux walls, FP32 storage, cudaMalloc, default stream. */
 void lbm2p_default_params(lbm2p_params *p);
 

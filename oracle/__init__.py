@@ -92,7 +92,7 @@ class OracleError(RuntimeError):
 class Oracle:
     """FP64 reference solver.  Arrays are [ny, nx] float64, row-major."""
 
-    def __init__(self, prob, tol=1e-8, max_sub_iters=10_000_000, check_every=10,
+    def __init__(self, prob, tol=1e-8, max_sub_iters=10_000_000, check_every=8,
                  init_replay=None):
         lib = _load()
         self.lib = lib
@@ -247,7 +247,7 @@ class Oracle:
         return out
 
 
-def run_problem(prob, nsteps=None, tol=1e-8, check_every=10, max_sub_iters=10_000_000,
+def run_problem(prob, nsteps=None, tol=1e-8, check_every=8, max_sub_iters=10_000_000,
                 replay=None, init_replay=None):
     """Run a workloads.Problem through the oracle, updating time-dependent sources and
     wall values before each step.  Returns (oracle, sub_iters log [init, step1, ...])."""

@@ -43,7 +43,8 @@ class lbm2p_params(C.Structure):
                 ("mu_w", C.c_double), ("mu_n", C.c_double), ("D_s", C.c_double),
                 ("tau_mode", C.c_int), ("tau_p", C.c_double), ("D_ref", C.c_double),
                 ("tol", C.c_double), ("max_sub_iters", C.c_int), ("check_every", C.c_int),
-                ("bc", C.c_int * 4), ("storage", C.c_int), ("stream", C.c_void_p),
+                ("bc", C.c_int * 4), ("storage", C.c_int), ("fuse_sweeps", C.c_int),
+                ("stream", C.c_void_p),
                 ("alloc", ALLOC_FN), ("release", RELEASE_FN), ("alloc_ctx", C.c_void_p)]
 
 
@@ -280,8 +281,8 @@ class Solver:
 
     def __init__(self, *, nx, ny, dx, dt, phi, beta, mobility, mu_w, mu_n, D_s, tau_mode,
                  tau_p, bc, K, S0, P0=None, Fp=None, Fs=None, wells=(), P_b=None, S_b=None,
-                 D_ref=0.0, tol=1e-8, max_sub_iters=10_000_000, check_every=10,
-                 init_replay=None, use_torch=True, stream=None):
+                 D_ref=0.0, tol=1e-8, max_sub_iters=10_000_000, check_every=8,
+                 init_replay=None, use_torch=True, stream=None, fuse_sweeps=0):
         lib = _lib_or_raise()
         self.nx, self.ny = int(nx), int(ny)
         n = self.nx * self.ny
@@ -292,6 +293,7 @@ class Solver:
         p.mu_w, p.mu_n, p.D_s = float(mu_w), float(mu_n), float(D_s)
         p.tau_mode, p.tau_p, p.D_ref = int(tau_mode), float(tau_p), float(D_ref)
         p.tol, p.max_sub_iters, p.check_every = float(tol), int(max_sub_iters), int(check_every)
+        p.fuse_sweeps = int(fuse_sweeps)
         for s in range(4):
             p.bc[s] = int(bc[s])
         self._mem = None

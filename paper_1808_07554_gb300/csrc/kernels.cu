@@ -21,6 +21,21 @@ namespace lbm2p_dev {
 // --------------------------------------------------------------------------------------
 // gather with the wall rules of Sec. 4
 // --------------------------------------------------------------------------------------
+// The per-node arithmetic of a pressure sweep, written with explicit fused multiply-adds so
+// that every kernel that performs a sweep (one per launch, or several fused in one launch)
+// produces bit-identical populations.
+// a_i = n_i(src) + w_i (R(src) - R(x))
+__device__ __forceinline__ float dev1(float n, float w, float r, float r0)
+{
+    return fmaf(w, r - r0, n);
+}
+
+// n_i^+ = a_i + (w_i dP - a_i) / tau_f + F~_p / 8   (Eq. 2-1b relative to R)
+__device__ __forceinline__ float collide1(float a, float w, float dP, float it, float Fq)
+{
+    return fmaf(fmaf(w, dP, -a), it, a) + Fq;
+}
+
 __device__ __forceinline__ bool interior(const Geom &g, int x, int y)
 {
     return x > 0 && x < g.nx - 1 && y > 0 && y < g.ny - 1;
@@ -53,7 +68,7 @@ __device__ __forceinline__ float pull_edge_dev(const float *__restrict__ n_i,
     }
     if (side < 0) {
         const int src = ys * g.pitch + xs;
-        return n_i[src] + wgt(I) * (R[src] - r0);
+        return dev1(n_i[src], wgt(I), R[src], r0);
     }
     const float b = n_opp[y * g.pitch + x];
     if (g.bc[side] == BC_NOFLUX)
@@ -70,14 +85,14 @@ __device__ __forceinline__ void gather_a(const float *const *fin, const float *_
     const float r0 = R[o];
     if (interior(g, x, y)) {
         const int p = g.pitch;
-        a[0] = fin[0][o - 1] + wgt(1) * (R[o - 1] - r0);
-        a[1] = fin[1][o - p] + wgt(2) * (R[o - p] - r0);
-        a[2] = fin[2][o + 1] + wgt(3) * (R[o + 1] - r0);
-        a[3] = fin[3][o + p] + wgt(4) * (R[o + p] - r0);
-        a[4] = fin[4][o - p - 1] + wgt(5) * (R[o - p - 1] - r0);
-        a[5] = fin[5][o - p + 1] + wgt(6) * (R[o - p + 1] - r0);
-        a[6] = fin[6][o + p + 1] + wgt(7) * (R[o + p + 1] - r0);
-        a[7] = fin[7][o + p - 1] + wgt(8) * (R[o + p - 1] - r0);
+        a[0] = dev1(fin[0][o - 1], wgt(1), R[o - 1], r0);
+        a[1] = dev1(fin[1][o - p], wgt(2), R[o - p], r0);
+        a[2] = dev1(fin[2][o + 1], wgt(3), R[o + 1], r0);
+        a[3] = dev1(fin[3][o + p], wgt(4), R[o + p], r0);
+        a[4] = dev1(fin[4][o - p - 1], wgt(5), R[o - p - 1], r0);
+        a[5] = dev1(fin[5][o - p + 1], wgt(6), R[o - p + 1], r0);
+        a[6] = dev1(fin[6][o + p + 1], wgt(7), R[o + p + 1], r0);
+        a[7] = dev1(fin[7][o + p - 1], wgt(8), R[o + p - 1], r0);
     } else {
         a[0] = pull_edge_dev<1>(fin[0], fin[opp(1) - 1], R, g, Pb, x, y, r0);
         a[1] = pull_edge_dev<2>(fin[1], fin[opp(2) - 1], R, g, Pb, x, y, r0);
@@ -248,8 +263,8 @@ __device__ __forceinline__ float4 shift_in_right(float4 v, const float *row, int
 // n + w (r - r0), elementwise
 __device__ __forceinline__ float4 dev4(float4 n, float w, float4 r, float4 r0)
 {
-    return make_float4(n.x + w * (r.x - r0.x), n.y + w * (r.y - r0.y), n.z + w * (r.z - r0.z),
-                       n.w + w * (r.w - r0.w));
+    return make_float4(dev1(n.x, w, r.x, r0.x), dev1(n.y, w, r.y, r0.y), dev1(n.z, w, r.z, r0.z),
+                       dev1(n.w, w, r.w, r0.w));
 }
 
 template <bool CHECK, bool WRITE_P>
@@ -318,7 +333,7 @@ __global__ void __launch_bounds__(kBlock) k_pressure(const __grid_constant__ Pre
                 // Eq. 2-1b relative to R: n_i^+ = a_i + (w_i dP - a_i)/tau_f + w_bar_i F~_p
 #pragma unroll
                 for (int i = 0; i < 8; ++i)
-                    (&out[i].x)[c] = fmaf(wgt(i + 1) * dP - fc[i], itc, fc[i]) + Fq;
+                    (&out[i].x)[c] = collide1(fc[i], wgt(i + 1), dP, itc, Fq);
                 dPv[c] = dP;
             }
 #pragma unroll
@@ -355,7 +370,7 @@ __global__ void __launch_bounds__(kBlock) k_pressure(const __grid_constant__ Pre
                 const float Fq = 0.125f * F;
 #pragma unroll
                 for (int i = 0; i < 8; ++i)
-                    a.fout[i][oc] = fmaf(wgt(i + 1) * dP - fc[i], itc, fc[i]) + Fq;
+                    a.fout[i][oc] = collide1(fc[i], wgt(i + 1), dP, itc, Fq);
                 if (CHECK) {
                     const float d = dP - a.Pio[oc], q = (a.R[oc] - shift) + dP;
                     sd += d;
@@ -400,6 +415,211 @@ __global__ void __launch_bounds__(kBlock) k_pressure(const __grid_constant__ Pre
     }
 }
 
+// --------------------------------------------------------------------------------------
+// a2/a3 fused in time: T pressure sweeps per launch.
+//
+// Block b owns a strip of W = blockDim.x columns and H rows.  It marches down its rows;
+// at iteration j it loads input row j+1 (stage 0: the populations of the previous launch)
+// into shared memory and computes stage s (the s-th sweep) at row j - s + 1, s = 1..T,
+// each stage from the three rows of the stage before it.  Stage s is computed on the
+// columns [x0 - (T - s), x0 + W + (T - s)): the halo a stage needs shrinks by one node per
+// stage, so stage T covers exactly the owned strip.  Shared memory holds, per stage
+// s < T, a ring of its last three rows (8 planes each), the reference pressure R of the
+// last T + 2 input rows, and (CHECK) the stage T-1 pressure increments.  Periodic sides
+// need no special case: halo loads wrap, so the shared rows hold the periodic images.
+// Nodes beyond a wall are skipped, and nodes on a wall apply the wall rules of Sec. 4 to
+// their own stage values.  Every node of every stage is computed with the same arithmetic
+// as one sweep of k_pressure, so T fused sweeps equal T single sweeps bit for bit; the
+// cost is the recomputation of the halo (about 2 (T - 1) / W of the columns and
+// 2 (T - 1) / H of the rows) against one read and one write of the populations per T
+// sweeps.  CHECK: the residual partials of the last stage against stage T - 1.
+// --------------------------------------------------------------------------------------
+struct TBLayout {
+    int W, T;
+    __device__ __forceinline__ int width(int s) const { return W + 2 * (T - s); }
+    // float offset of stage s's ring (s = 0 .. T-1)
+    __device__ __forceinline__ int ring(int s) const
+    {
+        int off = 0;
+        for (int q = 0; q < s; ++q)
+            off += 24 * width(q);
+        return off;
+    }
+    __device__ __forceinline__ int rring() const { return ring(T); }
+    __device__ __forceinline__ int dpring() const { return rring() + (T + 2) * width(0); }
+};
+
+__device__ __forceinline__ int wrap_coord(int v, int n) { return ((v % n) + n) % n; }
+
+template <int T, bool CHECK>
+__global__ void __launch_bounds__(128) k_pressure_tb(const __grid_constant__ PressureArgs a, int H)
+{
+    extern __shared__ float sm[];
+    const Geom &g = a.g;
+    const int W = blockDim.x;
+    const TBLayout L{W, T};
+    const int strips = (g.nx + W - 1) / W;
+    const int x0 = (blockIdx.x % strips) * W;
+    const int y0 = (blockIdx.x / strips) * H;
+    const bool perx = g.bc[0] == BC_PERIODIC, pery = g.bc[2] == BC_PERIODIC;
+    const int p = g.pitch;
+    const int tid = threadIdx.x;
+    const int ylo = y0 - T;                        // local row 0
+    const float shift = CHECK ? *a.shift : 0.0f;
+    float sd = 0.0f, sdd = 0.0f, sp = 0.0f, spp = 0.0f;
+
+    // stage-0 (input) row r into its ring slot, with R
+    auto load_row = [&](int r) {
+        const int rl = r - ylo;
+        const bool vy = pery || (r >= 0 && r < g.ny);
+        const int rw = pery ? wrap_coord(r, g.ny) : r;
+        float *ring0 = sm + L.ring(0) + (rl % 3) * 8 * L.width(0);
+        float *rr = sm + L.rring() + (rl % (T + 2)) * L.width(0);
+        for (int c = tid; c < L.width(0); c += W) {
+            const int xl = x0 - T + c;
+            const bool vx = perx || (xl >= 0 && xl < g.nx);
+            if (vx && vy) {
+                const int o = rw * p + (perx ? wrap_coord(xl, g.nx) : xl);
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    ring0[i * L.width(0) + c] = __ldg(a.fin[i] + o);
+                rr[c] = __ldg(a.R + o);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    ring0[i * L.width(0) + c] = 0.0f;
+                rr[c] = 0.0f;
+            }
+        }
+    };
+
+    load_row(ylo);
+    load_row(ylo + 1);
+    const int j0 = y0 - T + 1, j1 = y0 + H + T - 2;
+    for (int j = j0; j <= j1; ++j) {
+        load_row(j + 1);
+        __syncthreads();
+#pragma unroll
+        for (int s = 1; s <= T; ++s) {
+            const int r = j - s + 1;
+            const int halo = T - s;
+            const bool in_range = r >= y0 - halo && r < y0 + H + halo;
+            const bool vy = pery || (r >= 0 && r < g.ny);
+            if (in_range && vy) {
+                const int rw = pery ? wrap_coord(r, g.ny) : r;
+                const int rl = r - ylo;
+                const float *src = sm + L.ring(s - 1);
+                const int ws = L.width(s - 1);
+                const float *rr = sm + L.rring();
+                const int rslot_m = (rl - 1 + (T + 2)) % (T + 2), rslot_0 = rl % (T + 2),
+                          rslot_p = (rl + 1) % (T + 2);
+                const float *srow_m = src + ((rl - 1 + 3) % 3) * 8 * ws;   // row r - 1
+                const float *srow_0 = src + (rl % 3) * 8 * ws;             // row r
+                const float *srow_p = src + ((rl + 1) % 3) * 8 * ws;       // row r + 1
+                const float *Rm = rr + rslot_m * L.width(0), *R0 = rr + rslot_0 * L.width(0),
+                            *Rp = rr + rslot_p * L.width(0);
+                for (int c = tid; c < L.width(s); c += W) {
+                    const int xl = x0 - halo + c;
+                    if (!(perx || (xl >= 0 && xl < g.nx)))
+                        continue;
+                    const int xw = perx ? wrap_coord(xl, g.nx) : xl;
+                    const int cs = c + 1;              // this node in stage s-1 columns
+                    const int c0 = c + s;              // this node in stage-0 (R) columns
+                    const float r0 = R0[c0];
+                    float f[8];
+                    const bool wall = (!perx && (xw == 0 || xw == g.nx - 1)) ||
+                                      (!pery && (rw == 0 || rw == g.ny - 1));
+                    if (!wall) {
+                        // a_i = n_i(x - c_i) + w_i (R(x - c_i) - R(x)), all from shared rows
+                        f[0] = dev1(srow_0[0 * ws + cs - 1], wgt(1), R0[c0 - 1], r0);
+                        f[1] = dev1(srow_m[1 * ws + cs], wgt(2), Rm[c0], r0);
+                        f[2] = dev1(srow_0[2 * ws + cs + 1], wgt(3), R0[c0 + 1], r0);
+                        f[3] = dev1(srow_p[3 * ws + cs], wgt(4), Rp[c0], r0);
+                        f[4] = dev1(srow_m[4 * ws + cs - 1], wgt(5), Rm[c0 - 1], r0);
+                        f[5] = dev1(srow_m[5 * ws + cs + 1], wgt(6), Rm[c0 + 1], r0);
+                        f[6] = dev1(srow_p[6 * ws + cs + 1], wgt(7), Rp[c0 + 1], r0);
+                        f[7] = dev1(srow_p[7 * ws + cs - 1], wgt(8), Rp[c0 - 1], r0);
+                    } else {
+#pragma unroll
+                        for (int i = 1; i <= 8; ++i) {
+                            const int ex = cx(i), ey = cy(i);
+                            int side = -1;
+                            if (!perx && (xw - ex < 0 || xw - ex >= g.nx))
+                                side = xw - ex < 0 ? 0 : 1;
+                            else if (!pery && (rw - ey < 0 || rw - ey >= g.ny))
+                                side = rw - ey < 0 ? 2 : 3;
+                            if (side < 0) {
+                                const float *row = ey == 1 ? srow_m : (ey == -1 ? srow_p : srow_0);
+                                const float *Rrow = ey == 1 ? Rm : (ey == -1 ? Rp : R0);
+                                f[i - 1] = dev1(row[(i - 1) * ws + cs - ex], wgt(i), Rrow[c0 - ex], r0);
+                            } else {
+                                const float b = srow_0[(opp(i) - 1) * ws + cs];
+                                if (g.bc[side] == BC_NOFLUX) {
+                                    f[i - 1] = b;
+                                } else {
+                                    const int k = side < 2 ? 2 * rw + 1 - ey : 2 * xw + 1 - ex;
+                                    f[i - 1] = -b + 2.0f * wgt(i) * (a.Pb[side][k] - r0);
+                                }
+                            }
+                        }
+                    }
+                    const float dP = pressure_of(f);
+                    const int o = rw * p + xw;
+                    const float it = __ldg(a.inv_tau + o);
+                    float F = a.Fp ? __ldg(a.Fp + o) : 0.0f;
+                    for (int k = 0; k < a.w.n; ++k)
+                        if (o == a.w.idx[k])
+                            F += a.w.fp[k];
+                    const float Fq = 0.125f * F;
+                    if (s < T) {
+                        float *dst = sm + L.ring(s) + (rl % 3) * 8 * L.width(s);
+#pragma unroll
+                        for (int i = 0; i < 8; ++i)
+                            dst[i * L.width(s) + c] = collide1(f[i], wgt(i + 1), dP, it, Fq);
+                        if (CHECK && s == T - 1)
+                            sm[L.dpring() + (rl % 3) * L.width(T - 1) + c] = dP;
+                    } else if (xl >= x0 && xl < x0 + W && xl < g.nx && r >= y0 && r < y0 + H &&
+                               r < g.ny && r >= 0) {
+#pragma unroll
+                        for (int i = 0; i < 8; ++i)
+                            a.fout[i][o] = collide1(f[i], wgt(i + 1), dP, it, Fq);
+                        if (CHECK) {
+                            const float d = dP - sm[L.dpring() + (rl % 3) * L.width(T - 1) + c + 1];
+                            const float q = (r0 - shift) + dP;
+                            sd += d;
+                            sdd += d * d;
+                            sp += q;
+                            spp += q * q;
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (CHECK) {
+        const int lane = tid & 31, warp = tid >> 5;
+        sd = warp_sum(sd);
+        sdd = warp_sum(sdd);
+        sp = warp_sum(sp);
+        spp = warp_sum(spp);
+        __shared__ double red[4][4];
+        if (lane == 0) {
+            red[warp][0] = sd;
+            red[warp][1] = sdd;
+            red[warp][2] = sp;
+            red[warp][3] = spp;
+        }
+        __syncthreads();
+        if (tid < 4) {
+            double acc = 0.0;
+            for (int w = 0; w < W / 32; ++w)
+                acc += red[w][tid];
+            a.partials[4 * blockIdx.x + tid] = acc;
+        }
+    }
+}
+
 #ifdef LBM2P_SWEEP_SCALAR
 // One node per thread (row tiles of kBlock nodes): the same sweep with scalar loads.
 template <bool CHECK, bool WRITE_P>
@@ -426,7 +646,7 @@ __global__ void __launch_bounds__(kBlock) k_pressure_scalar(const __grid_constan
             const float Fq = 0.125f * F;
 #pragma unroll
             for (int i = 0; i < 8; ++i)
-                a.fout[i][o] = fmaf(wgt(i + 1) * dP - f[i], it, f[i]) + Fq;
+                a.fout[i][o] = collide1(f[i], wgt(i + 1), dP, it, Fq);
             if (CHECK) {
                 d = dP - a.Pio[o];
                 q = (a.R[o] - shift) + dP;
@@ -824,6 +1044,49 @@ void pressure_sweep(const PressureArgs &a, bool check, bool write_p, int grid, v
         K_SWEEP<false, false><<<grid, kBlock, 0, S(stream)>>>(a);
 }
 
+size_t tb_smem_bytes(int T, int W)
+{
+    size_t floats = 0;
+    for (int s = 0; s < T; ++s)
+        floats += 24 * (size_t)(W + 2 * (T - s));
+    floats += (size_t)(T + 2) * (W + 2 * T) + 3 * (size_t)(W + 2);
+    return floats * sizeof(float);
+}
+
+static void *tb_func(int T, bool check)
+{
+    if (T == 2)
+        return check ? (void *)k_pressure_tb<2, true> : (void *)k_pressure_tb<2, false>;
+    return check ? (void *)k_pressure_tb<4, true> : (void *)k_pressure_tb<4, false>;
+}
+
+cudaError_t tb_prepare(int T, int W)
+{
+    // the opt-in limit is set for the widest tile, so every tile width stays launchable
+    const int bytes = (int)tb_smem_bytes(T, W > 128 ? W : 128);
+    cudaError_t e = cudaSuccess;
+    for (bool c : {false, true}) {
+        e = cudaFuncSetAttribute(tb_func(T, c), cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e != cudaSuccess)
+            return e;
+    }
+    return e;
+}
+
+int tb_blocks_per_sm(int T, int W)
+{
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, tb_func(T, true), W, tb_smem_bytes(T, W));
+    return b;
+}
+
+void pressure_sweeps_fused(const PressureArgs &a, int T, int W, int H, bool check, int grid,
+                           void *stream)
+{
+    void *args[] = {(void *)&a, (void *)&H};
+    cudaLaunchKernel(tb_func(T, check), dim3(grid), dim3(W), args, tb_smem_bytes(T, W), S(stream));
+}
+
 void residual_finalize(const double *partials, int nparts, long long nnodes, float *shift,
                        ResidualOut *out, void *stream)
 {
@@ -896,6 +1159,20 @@ cudaError_t node_pressure(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode
                        : (write_p ? (void *)K_SWEEP<false, true> : (void *)K_SWEEP<false, false>);
     void *args[] = {(void *)&a};
     return add_kernel(n, g, dep, func, grid, kBlock, args);
+}
+
+cudaError_t node_pressure_fused(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
+                                const PressureArgs &a, int T, int W, int H, bool check, int grid)
+{
+    cudaKernelNodeParams p{};
+    p.func = tb_func(T, check);
+    p.gridDim = dim3((unsigned)grid);
+    p.blockDim = dim3((unsigned)W);
+    p.sharedMemBytes = (unsigned)tb_smem_bytes(T, W);
+    void *args[] = {(void *)&a, (void *)&H};
+    p.kernelParams = args;
+    p.extra = nullptr;
+    return cudaGraphAddKernelNode(n, g, dep, dep ? 1 : 0, &p);
 }
 
 cudaError_t node_finalize_loop(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,

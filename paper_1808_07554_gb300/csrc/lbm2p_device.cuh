@@ -192,6 +192,13 @@ int max_blocks_per_sm_pressure(bool check);
 void pressure_sweep(const PressureArgs &a, bool check, bool write_p, int grid, void *stream);
 void residual_finalize(const double *partials, int nparts, long long nnodes, float *shift,
                        ResidualOut *out, void *stream);
+// T pressure sweeps fused in one launch (T = 2 or 4), W threads per block (a multiple of
+// 32, at most 128), H rows per block; grid = ceil(nx / W) * ceil(ny / H)
+size_t tb_smem_bytes(int T, int W);
+cudaError_t tb_prepare(int T, int W);
+int tb_blocks_per_sm(int T, int W);
+void pressure_sweeps_fused(const PressureArgs &a, int T, int W, int H, bool check, int grid,
+                           void *stream);
 void refresh(const RefreshArgs &a, int grid, void *stream);
 void saturation(const SaturationArgs &a, int grid, void *stream);
 void init_g(const InitGArgs &a, int grid, void *stream);
@@ -202,6 +209,8 @@ void fields(const FieldsArgs &a, int grid, void *stream);
 // graph nodes (explicit construction; parameters are copied into the node)
 cudaError_t node_pressure(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
                           const PressureArgs &a, bool check, bool write_p, int grid);
+cudaError_t node_pressure_fused(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
+                                const PressureArgs &a, int T, int W, int H, bool check, int grid);
 cudaError_t node_finalize_loop(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
                                const double *partials, int nparts, long long nnodes, float *shift,
                                ResidualOut *out, LoopCtl *ctl, cudaGraphConditionalHandle h);

@@ -39,6 +39,8 @@ struct lbm2p {
     double s = 0, tau_g = 0, D_ref = 0;
     int grid = 0;              // blocks of every grid-stride lattice launch
     int grid_check = 0;        // blocks of a pressure sweep that accumulates the residual
+    int tb_T = 0, tb_W = 0, tb_H = 0, tb_grid = 0;   // fused sweeps per launch and tile shape
+    int tb_T_graph = 0;        // fused sweeps used inside the graph loop body (0: single sweeps)
     void *stream = nullptr;
     std::vector<Alloc> allocs;
     float *fbuf[2][8] = {};
@@ -293,16 +295,30 @@ lbm2p_status add_loop(lbm2p *h, cudaGraph_t G, const cudaGraphNode_t *dep, int p
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     cudaGraphNode_t prev = nullptr;
     int src = pf;
-    for (int kk = 1; kk <= m; ++kk) {
-        cudaGraphNode_t n;
-        PressureArgs a = pressure_args(h, src);
-        CUDA_TRY(h, lbm2p_launch::node_pressure(&n, body, prev ? &prev : nullptr, a, kk == m,
-                                                kk == m - 1, kk == m ? h->grid_check : h->grid));
-        prev = n;
-        src = 1 - src;
+    int nparts = h->grid_check;
+    if (h->tb_T_graph > 1) {
+        const int T = h->tb_T_graph;
+        for (int kk = T; kk <= m; kk += T) {
+            cudaGraphNode_t n;
+            PressureArgs a = pressure_args(h, src);
+            CUDA_TRY(h, lbm2p_launch::node_pressure_fused(&n, body, prev ? &prev : nullptr, a, T,
+                                                          h->tb_W, h->tb_H, kk == m, h->tb_grid));
+            prev = n;
+            src = 1 - src;
+        }
+        nparts = h->tb_grid;
+    } else {
+        for (int kk = 1; kk <= m; ++kk) {
+            cudaGraphNode_t n;
+            PressureArgs a = pressure_args(h, src);
+            CUDA_TRY(h, lbm2p_launch::node_pressure(&n, body, prev ? &prev : nullptr, a, kk == m,
+                                                    kk == m - 1, kk == m ? h->grid_check : h->grid));
+            prev = n;
+            src = 1 - src;
+        }
     }
     cudaGraphNode_t fin;
-    CUDA_TRY(h, lbm2p_launch::node_finalize_loop(&fin, body, &prev, h->partials, h->grid_check,
+    CUDA_TRY(h, lbm2p_launch::node_finalize_loop(&fin, body, &prev, h->partials, nparts,
                                                  h->nnodes, h->shift, h->res, h->ctl, hd));
     CUDA_TRY(h, cudaGraphAddEventRecordNode(&ev1, G, &wn, 1, h->ev_sw1));
     *last = ev1;
@@ -356,8 +372,9 @@ lbm2p_status read_loop(lbm2p *h, int *k, double *r, float *sweep_ms)
     *k = h->ctl_host->k;
     *r = h->ctl_host->r;
     const int m = h->p.check_every;
+    const int per_launch = h->tb_T_graph > 1 ? h->tb_T_graph : 1;
     h->sweeps += *k;
-    h->launches += 1 + *k + *k / m;   // reset, sweeps, finalizes
+    h->launches += 1 + *k / per_launch + *k / m;   // reset, sweep launches, finalizes
     if (sweep_ms) {
         *sweep_ms = -1.0f;
         if (h->timing)
@@ -393,12 +410,22 @@ lbm2p_status pressure_solve(lbm2p *h, int replay, int *k_out, double *r_out, flo
         return (kk % m == 0) || kk >= cap;
     };
     // run sweeps k+1 .. upto; the last one evaluates the residual when asked
+    int last_nparts = h->grid_check;
+    // run sweeps k+1 .. upto; the last one evaluates the residual when it is a check point.
+    // With fused sweeps the batch is a few single sweeps followed by fused launches, the
+    // last of which computes the residual from its final two stages.
     auto run_batch = [&](int upto) -> lbm2p_status {
         if (h->timing)
             CUDA_TRY(h, cudaEventRecord(h->ev_sw0, st));
-        for (int kk = k + 1; kk <= upto; ++kk) {
-            const bool check = is_check(kk) && kk >= 2;
-            const bool write_p = is_check(kk + 1) && kk + 1 >= 2;
+        const int n = upto - k;
+        const int T = h->tb_T;
+        const int nf = (T > 1 && n >= T) ? n / T : 0;
+        const int ns = n - nf * T;
+        const bool final_check = is_check(upto) && upto >= 2;
+        for (int i = 0; i < ns; ++i) {
+            const int kk = k + 1 + i;
+            const bool check = nf == 0 && is_check(kk) && kk >= 2;
+            const bool write_p = nf == 0 && is_check(kk + 1) && kk + 1 >= 2;
             PressureArgs a = pressure_args(h, h->cur_f);
             lbm2p_launch::pressure_sweep(a, check, write_p, check ? h->grid_check : h->grid,
                                          h->stream);
@@ -406,13 +433,22 @@ lbm2p_status pressure_solve(lbm2p *h, int replay, int *k_out, double *r_out, flo
             h->cur_f = 1 - h->cur_f;
             h->sweeps += 1;
         }
+        for (int q = 0; q < nf; ++q) {
+            PressureArgs a = pressure_args(h, h->cur_f);
+            lbm2p_launch::pressure_sweeps_fused(a, T, h->tb_W, h->tb_H, q == nf - 1 && final_check,
+                                                h->tb_grid, h->stream);
+            LAUNCHED(h, "fused pressure sweeps");
+            h->cur_f = 1 - h->cur_f;
+            h->sweeps += T;
+        }
+        last_nparts = nf > 0 ? h->tb_grid : h->grid_check;
         if (h->timing)
             CUDA_TRY(h, cudaEventRecord(h->ev_sw1, st));
         k = upto;
         return LBM2P_OK;
     };
     auto read_residual = [&]() -> lbm2p_status {
-        lbm2p_launch::residual_finalize(h->partials, h->grid_check, h->nnodes, h->shift, h->res,
+        lbm2p_launch::residual_finalize(h->partials, last_nparts, h->nnodes, h->shift, h->res,
                                         h->stream);
         LAUNCHED(h, "residual finalize");
         CUDA_TRY(h, cudaMemcpyAsync(h->res_host, h->res, sizeof(ResidualOut),
@@ -617,6 +653,8 @@ lbm2p_status check_params(const lbm2p_params *p, const lbm2p_inputs *in)
         return fail(nullptr, LBM2P_EINVAL, "Dirichlet x-sides need nx >= 3");
     if ((p->bc[2] == LBM2P_BC_DIRICHLET || p->bc[3] == LBM2P_BC_DIRICHLET) && p->ny < 3)
         return fail(nullptr, LBM2P_EINVAL, "Dirichlet y-sides need ny >= 3");
+    if (p->fuse_sweeps != 0 && p->fuse_sweeps != 1 && p->fuse_sweeps != 2 && p->fuse_sweeps != 4)
+        return fail(nullptr, LBM2P_EINVAL, "fuse_sweeps must be 0, 1, 2 or 4");
     if (p->storage == LBM2P_STORE_FP16_DEV)
         return fail(nullptr, LBM2P_ENOTIMPL, "FP16 deviation storage is not available");
     if (p->storage != LBM2P_STORE_FP32)
@@ -639,6 +677,68 @@ lbm2p_status check_params(const lbm2p_params *p, const lbm2p_inputs *in)
     }
     if (in->init_replay && *in->init_replay < 0)
         return fail(nullptr, LBM2P_EINVAL, "init_replay must be >= 0");
+    return LBM2P_OK;
+}
+
+// Pick the fused-sweep tile shape by timing every candidate on this lattice.
+lbm2p_status autotune_fused(lbm2p *h, int T)
+{
+    cudaStream_t st = (cudaStream_t)h->stream;
+    int dev = 0, sms = 0;
+    CUDA_TRY(h, cudaGetDevice(&dev));
+    CUDA_TRY(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    for (auto &a : h->allocs)
+        CUDA_TRY(h, cudaMemsetAsync(a.ptr, 0, a.bytes, st));
+    cudaEvent_t e0, e1;
+    CUDA_TRY(h, cudaEventCreate(&e0));
+    CUDA_TRY(h, cudaEventCreate(&e1));
+    float best = 1e30f;
+    lbm2p_status status = LBM2P_OK;
+    for (int W : {128, 64, 32}) {
+        cudaError_t ce = lbm2p_launch::tb_prepare(T, W);
+        if (ce != cudaSuccess || lbm2p_launch::tb_blocks_per_sm(T, W) < 1) {
+            cudaGetLastError();
+            continue;
+        }
+        for (int H : {64, 32, 16, 8}) {
+            const long long blocks = (long long)((h->nx + W - 1) / W) * ((h->ny + H - 1) / H);
+            if (blocks > (1LL << 30))
+                continue;
+            PressureArgs a = pressure_args(h, 0);
+            lbm2p_launch::pressure_sweeps_fused(a, T, W, H, false, (int)blocks, h->stream);
+            cudaEventRecord(e0, st);
+            for (int rep = 0; rep < 3; ++rep) {
+                PressureArgs b = pressure_args(h, rep % 2 == 0 ? 1 : 0);
+                lbm2p_launch::pressure_sweeps_fused(b, T, W, H, false, (int)blocks, h->stream);
+            }
+            cudaEventRecord(e1, st);
+            cudaError_t le = cudaEventSynchronize(e1);
+            if (le != cudaSuccess) {
+                status = fail(h, LBM2P_ECUDA, "fused sweep (W %d, H %d) failed: %s", W, H,
+                              cudaGetErrorString(le));
+                break;
+            }
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                h->tb_T = T;
+                h->tb_W = W;
+                h->tb_H = H;
+                h->tb_grid = (int)blocks;
+            }
+        }
+        if (status != LBM2P_OK)
+            break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (status != LBM2P_OK)
+        return status;
+    CUDA_TRY(h, cudaGetLastError());
+    for (auto &a : h->allocs)
+        CUDA_TRY(h, cudaMemsetAsync(a.ptr, 0, a.bytes, st));
+    CUDA_TRY(h, cudaStreamSynchronize(st));
     return LBM2P_OK;
 }
 
@@ -745,7 +845,24 @@ lbm2p_status build(lbm2p *h, const lbm2p_inputs *in, lbm2p_step_stats *init_stat
             ok = ok && h->Pb[s] && h->Sb[s];
         }
     }
-    h->partials = (double *)dev_alloc(h, (size_t)(h->grid > h->grid_check ? h->grid : h->grid_check) * 4 * sizeof(double));
+    if (!ok)
+        return fail(h, LBM2P_ENOMEM, "device allocation of %.1f MiB failed",
+                    (double)pb * 45 / (1 << 20));
+    // fused sweeps: time each tile shape (W columns, H rows) with real launches on the
+    // zeroed buffers and keep the fastest; the buffers are zeroed again afterwards
+    {
+        const int T = p.fuse_sweeps == 0 ? 2 : p.fuse_sweeps;
+        if (T > 1) {
+            lbm2p_status e = autotune_fused(h, T);
+            if (e != LBM2P_OK)
+                return e;
+        }
+    }
+    {
+        int np = h->grid > h->grid_check ? h->grid : h->grid_check;
+        np = np > h->tb_grid ? np : h->tb_grid;
+        h->partials = (double *)dev_alloc(h, (size_t)np * 4 * sizeof(double));
+    }
     h->mean = (double *)dev_alloc(h, 64);
     h->shift = (float *)dev_alloc(h, 64);
     h->res = (ResidualOut *)dev_alloc(h, sizeof(ResidualOut));
@@ -765,6 +882,10 @@ lbm2p_status build(lbm2p *h, const lbm2p_inputs *in, lbm2p_step_stats *init_stat
     // the loop body holds check_every sweeps and must return to the same f buffer
     h->graph_ok = p.check_every >= 2 && p.check_every % 2 == 0 &&
                   p.max_sub_iters % p.check_every == 0;
+    if (h->tb_T > 1 && p.check_every % (2 * h->tb_T) != 0)
+        h->tb_T_graph = 0;
+    else
+        h->tb_T_graph = h->tb_T;
     {
         LoopCtl c{};
         c.m = p.check_every;
@@ -881,7 +1002,8 @@ void lbm2p_default_params(lbm2p_params *p)
     p->D_ref = 0.0;
     p->tol = 1e-8;
     p->max_sub_iters = 10000000;
-    p->check_every = 10;
+    p->check_every = 8;
+    p->fuse_sweeps = 0;
     for (int s = 0; s < 4; ++s)
         p->bc[s] = LBM2P_BC_NOFLUX;
     p->storage = LBM2P_STORE_FP32;

@@ -1,0 +1,68 @@
+"""Pressure sweeps fused in time (several sweeps per kernel launch) against one sweep per
+launch: identical populations bit for bit, on every wall kind and on ragged and tiny
+lattices, and the same residual up to the grouping of its partial sums."""
+import numpy as np
+import pytest
+
+import workloads as W
+from _problems import uniform
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1808_07554_gb300 import build
+    build.build()
+    import paper_1808_07554_gb300 as pkg
+    pkg.load_library()
+
+
+def _problem(kind):
+    rng = np.random.default_rng(hash(kind) % 2 ** 32)
+    if kind == "five_spot_ragged":
+        return W.quarter_five_spot(300, 200, seed=5, corr_len=8.0)
+    if kind == "wide_ragged":
+        return W.quarter_five_spot(2049, 17, seed=6, corr_len=4.0)
+    if kind == "periodic":
+        return W.manufactured_periodic(96)
+    nx, ny, bc = {"dirichlet": (97, 70, (2, 2, 2, 2)), "mixed": (65, 129, (0, 0, 2, 2)),
+                  "tiny": (5, 3, (1, 1, 0, 0)), "column": (1, 7, (0, 0, 0, 0)),
+                  "tall": (31, 300, (2, 2, 1, 1))}[kind]
+    Pb = [rng.random(2 * (ny if s < 2 else nx) + 1) for s in range(4)]
+    return uniform(nx, ny, bc=bc, K=np.exp(rng.standard_normal((ny, nx))),
+                   S0=0.2 + 0.5 * rng.random((ny, nx)), Fp=rng.standard_normal((ny, nx)),
+                   wells=[(0, 0, 1e-3, 0), (nx - 1, ny - 1, 1e-3, 1)] if nx * ny > 1 else [],
+                   P_b=Pb, S_b=[0.3 + 0.0 * t for t in Pb])
+
+
+@pytest.mark.parametrize("kind", ["five_spot_ragged", "wide_ragged", "periodic", "dirichlet",
+                                  "mixed", "tiny", "column", "tall"])
+@pytest.mark.parametrize("T", [2, 4])
+def test_fused_equals_single_sweeps(kind, T):
+    import paper_1808_07554_gb300 as pkg
+    prob = _problem(kind)
+    single = pkg.Solver.from_problem(prob, init_replay=0, fuse_sweeps=1)
+    fused = pkg.Solver.from_problem(prob, init_replay=0, fuse_sweeps=T)
+    rng = np.random.default_rng(3)
+    state = single.get_state()
+    state[:8] = 0.01 * rng.standard_normal(state[:8].shape)
+    state[17] = 1.0 / (0.55 + 2.0 * rng.random(state[17].shape))
+    state[19] = rng.standard_normal(state[19].shape)
+    single.set_state(state)
+    fused.set_state(state)
+    for n in (3 * T + 1, T, 2 * T):
+        r1 = single.pressure_sweeps(n)
+        r2 = fused.pressure_sweeps(n)
+        a, b = single.get_state(), fused.get_state()
+        assert np.array_equal(a, b), (kind, T, n, float(np.max(np.abs(a - b))))
+        assert r2 == pytest.approx(r1, rel=1e-5, abs=1e-30)
+    # and through whole steps (graph-resident loop with fused bodies)
+    s1 = single.step(2, replay=[4 * T, 2 * T])
+    s2 = fused.step(2, replay=[4 * T, 2 * T])
+    assert np.array_equal(single.get_state(), fused.get_state())
+    single.close()
+    fused.close()
