@@ -274,7 +274,8 @@ __global__ void __launch_bounds__(kBlock) k_pressure(const __grid_constant__ Pre
     const int lane = threadIdx.x & 31;
     const int p = g.pitch;
     double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
-    const float shift = CHECK ? *a.shift : 0.0f;
+    const float shift = CHECK ? a.shift[0] : 0.0f;    // constant subtracted from P
+    const float dshift = CHECK ? a.shift[1] : 0.0f;   // constant subtracted from dP - dP_prev
     const int tiles_x = (g.nx + 4 * kBlock - 1) / (4 * kBlock);
     const int ntiles = tiles_x * g.ny;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -343,7 +344,7 @@ __global__ void __launch_bounds__(kBlock) k_pressure(const __grid_constant__ Pre
                 const float4 Pp = ld4(a.Pio, o);
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
-                    const float d = dPv[c] - (&Pp.x)[c], q = ((&r0.x)[c] - shift) + dPv[c];
+                    const float d = (dPv[c] - (&Pp.x)[c]) - dshift, q = ((&r0.x)[c] - shift) + dPv[c];
                     sd += d;
                     sdd += d * d;
                     sp += q;
@@ -372,7 +373,7 @@ __global__ void __launch_bounds__(kBlock) k_pressure(const __grid_constant__ Pre
                 for (int i = 0; i < 8; ++i)
                     a.fout[i][oc] = collide1(fc[i], wgt(i + 1), dP, itc, Fq);
                 if (CHECK) {
-                    const float d = dP - a.Pio[oc], q = (a.R[oc] - shift) + dP;
+                    const float d = (dP - a.Pio[oc]) - dshift, q = (a.R[oc] - shift) + dP;
                     sd += d;
                     sdd += d * d;
                     sp += q;
@@ -465,7 +466,8 @@ __global__ void __launch_bounds__(128) k_pressure_tb(const __grid_constant__ Pre
     const int p = g.pitch;
     const int tid = threadIdx.x;
     const int ylo = y0 - T;                        // local row 0
-    const float shift = CHECK ? *a.shift : 0.0f;
+    const float shift = CHECK ? a.shift[0] : 0.0f;
+    const float dshift = CHECK ? a.shift[1] : 0.0f;
     float sd = 0.0f, sdd = 0.0f, sp = 0.0f, spp = 0.0f;
 
     // stage-0 (input) row r into its ring slot, with R
@@ -584,7 +586,7 @@ __global__ void __launch_bounds__(128) k_pressure_tb(const __grid_constant__ Pre
                         for (int i = 0; i < 8; ++i)
                             a.fout[i][o] = collide1(f[i], wgt(i + 1), dP, it, Fq);
                         if (CHECK) {
-                            const float d = dP - sm[L.dpring() + (rl % 3) * L.width(T - 1) + c + 1];
+                            const float d = (dP - sm[L.dpring() + (rl % 3) * L.width(T - 1) + c + 1]) - dshift;
                             const float q = (r0 - shift) + dP;
                             sd += d;
                             sdd += d * d;
@@ -628,7 +630,8 @@ __global__ void __launch_bounds__(kBlock) k_pressure_scalar(const __grid_constan
     const Geom &g = a.g;
     const int lane = threadIdx.x & 31;
     double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
-    const float shift = CHECK ? *a.shift : 0.0f;
+    const float shift = CHECK ? a.shift[0] : 0.0f;
+    const float dshift = CHECK ? a.shift[1] : 0.0f;
     for (int t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
         const int y = t / g.tiles_x;
         const int x = (t - y * g.tiles_x) * kBlock + threadIdx.x;
@@ -648,7 +651,7 @@ __global__ void __launch_bounds__(kBlock) k_pressure_scalar(const __grid_constan
             for (int i = 0; i < 8; ++i)
                 a.fout[i][o] = collide1(f[i], wgt(i + 1), dP, it, Fq);
             if (CHECK) {
-                d = dP - a.Pio[o];
+                d = (dP - a.Pio[o]) - dshift;
                 q = (a.R[o] - shift) + dP;
             }
             if (WRITE_P)
@@ -713,16 +716,18 @@ __device__ double finalize_residual(const double *__restrict__ partials, int npa
     if (threadIdx.x == 0) {
         const double N = (double)nnodes;
         const double sd = red[0][0], sdd = red[0][1], sp = red[0][2], spp = red[0][3];
-        const double c = (double)*shift;
+        const double c = (double)shift[0], cd = (double)shift[1];
         if (!isfinite(sd) || !isfinite(sdd) || !isfinite(sp) || !isfinite(spp)) {
             r = nan("");
         } else {
+            // sums of (dP - dP_prev - cd) and (P - c): variances are shift invariant
             double num = sdd - sd * sd / N;
             double den = spp - sp * sp / N;
             num = num > 0.0 ? num : 0.0;
             den = den > 0.0 ? den : 0.0;
             r = den > 0.0 ? sqrt(num / den) : (num > 0.0 ? INFINITY : 0.0);
-            *shift = (float)(c + sp / N);
+            shift[0] = (float)(c + sp / N);
+            shift[1] = (float)(cd + sd / N);
         }
         out->r = r;
         out->mean_P = c + sp / N;

@@ -92,7 +92,7 @@ struct PressureArgs {
     const float *Fp;         // dense F~_p plane (lattice units) or nullptr
     float *Pio;              // pressure plane written (WRITE_P) / read (CHECK)
     double *partials;        // CHECK: 4 doubles per block
-    const float *shift;      // CHECK: constant subtracted from P before squaring
+    const float *shift;      // CHECK: [0] subtracted from P, [1] from dP - dP_prev, before squaring
     const float *Pb[4];      // Dirichlet traces (device FP32) or nullptr
     Geom g;
     Wells w;

@@ -26,7 +26,7 @@ namespace {
 // tile; then the finalize output (ResidualOut); then the shift (a float in one slot).
 constexpr size_t kPartials = 4 * (size_t)LBM2P_NOALLOC_MAX_TILES;
 constexpr size_t kOutSlots = (sizeof(ResidualOut) + sizeof(double) - 1) / sizeof(double);
-constexpr size_t kScratchDoubles = kPartials + kOutSlots + 1;
+constexpr size_t kScratchDoubles = kPartials + kOutSlots + 1;   // last slot: two float shifts
 
 static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
 
@@ -132,8 +132,8 @@ extern "C" lbm2p_status lbm2p_pressure_sweep_noalloc(int nx, int ny, int pitch, 
     a.w.n = 0;
 
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
-    // the shift starts at zero on every call; the partials and the output are overwritten
-    cudaError_t e = cudaMemsetAsync(shift, 0, sizeof(float), cs);
+    // the two shifts start at zero on every call; the partials and the output are overwritten
+    cudaError_t e = cudaMemsetAsync(shift, 0, 2 * sizeof(float), cs);
     if (e != cudaSuccess)
         return set_global_error(LBM2P_ECUDA, "clearing the sweep scratch failed: %s", cudaGetErrorString(e));
     // one block per row tile, so every tile owns one slot of partials
