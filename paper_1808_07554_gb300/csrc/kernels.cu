@@ -438,7 +438,7 @@ __global__ void __launch_bounds__(kBlock) k_pressure(const __grid_constant__ Pre
 struct TBLayout {
     int W, T;
     __device__ __forceinline__ int width(int s) const { return W + 2 * (T - s); }
-    // float offset of stage s's ring (s = 0 .. T-1)
+    // float offset of stage s's ring (s = 0 .. T-1): 3 rows x 8 planes x width(s)
     __device__ __forceinline__ int ring(int s) const
     {
         int off = 0;
@@ -446,11 +446,19 @@ struct TBLayout {
             off += 24 * width(q);
         return off;
     }
+    // per-row fields of the last T + 2 input rows (width(0) each): R, 1/tau_f, F~_p
     __device__ __forceinline__ int rring() const { return ring(T); }
-    __device__ __forceinline__ int dpring() const { return rring() + (T + 2) * width(0); }
+    __device__ __forceinline__ int tring() const { return rring() + (T + 2) * width(0); }
+    __device__ __forceinline__ int fring() const { return tring() + (T + 2) * width(0); }
+    __device__ __forceinline__ int dpring() const { return fring() + (T + 2) * width(0); }
 };
 
 __device__ __forceinline__ int wrap_coord(int v, int n) { return ((v % n) + n) % n; }
+
+// one input row's values for the (at most two) columns a thread stages
+struct TBRow {
+    float v[2][11];
+};
 
 template <int T, bool CHECK>
 __global__ void __launch_bounds__(128) k_pressure_tb(const __grid_constant__ PressureArgs a, int H)
@@ -466,41 +474,70 @@ __global__ void __launch_bounds__(128) k_pressure_tb(const __grid_constant__ Pre
     const int p = g.pitch;
     const int tid = threadIdx.x;
     const int ylo = y0 - T;                        // local row 0
+    const int w0 = L.width(0);
     const float shift = CHECK ? a.shift[0] : 0.0f;
     const float dshift = CHECK ? a.shift[1] : 0.0f;
     float sd = 0.0f, sdd = 0.0f, sp = 0.0f, spp = 0.0f;
 
-    // stage-0 (input) row r into its ring slot, with R
-    auto load_row = [&](int r) {
-        const int rl = r - ylo;
+    // global loads of input row r (8 planes, R, 1/tau_f, F~_p) into registers
+    auto fetch = [&](int r, TBRow &row) {
         const bool vy = pery || (r >= 0 && r < g.ny);
         const int rw = pery ? wrap_coord(r, g.ny) : r;
-        float *ring0 = sm + L.ring(0) + (rl % 3) * 8 * L.width(0);
-        float *rr = sm + L.rring() + (rl % (T + 2)) * L.width(0);
-        for (int c = tid; c < L.width(0); c += W) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int c = tid + q * W;
             const int xl = x0 - T + c;
-            const bool vx = perx || (xl >= 0 && xl < g.nx);
+            const bool vx = c < w0 && (perx || (xl >= 0 && xl < g.nx));
             if (vx && vy) {
                 const int o = rw * p + (perx ? wrap_coord(xl, g.nx) : xl);
 #pragma unroll
                 for (int i = 0; i < 8; ++i)
-                    ring0[i * L.width(0) + c] = __ldg(a.fin[i] + o);
-                rr[c] = __ldg(a.R + o);
+                    row.v[q][i] = __ldg(a.fin[i] + o);
+                row.v[q][8] = __ldg(a.R + o);
+                row.v[q][9] = __ldg(a.inv_tau + o);
+                float F = a.Fp ? __ldg(a.Fp + o) : 0.0f;
+                for (int k = 0; k < a.w.n; ++k)
+                    if (o == a.w.idx[k])
+                        F += a.w.fp[k];
+                row.v[q][10] = 0.125f * F;          // w_bar_i F~_p, w_bar_i = 1/8 (Eq. 3-5a)
             } else {
 #pragma unroll
+                for (int i = 0; i < 11; ++i)
+                    row.v[q][i] = 0.0f;
+            }
+        }
+    };
+    // registers of input row r into the shared rings
+    auto stage_in = [&](int r, const TBRow &row) {
+        const int rl = r - ylo;
+        float *ring0 = sm + L.ring(0) + (rl % 3) * 8 * w0;
+        const int fs = (rl % (T + 2)) * w0;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int c = tid + q * W;
+            if (c < w0) {
+#pragma unroll
                 for (int i = 0; i < 8; ++i)
-                    ring0[i * L.width(0) + c] = 0.0f;
-                rr[c] = 0.0f;
+                    ring0[i * w0 + c] = row.v[q][i];
+                sm[L.rring() + fs + c] = row.v[q][8];
+                sm[L.tring() + fs + c] = row.v[q][9];
+                sm[L.fring() + fs + c] = row.v[q][10];
             }
         }
     };
 
-    load_row(ylo);
-    load_row(ylo + 1);
+    TBRow nxt;
+    fetch(ylo, nxt);
+    stage_in(ylo, nxt);
+    fetch(ylo + 1, nxt);
+    stage_in(ylo + 1, nxt);
     const int j0 = y0 - T + 1, j1 = y0 + H + T - 2;
+    fetch(j0 + 1, nxt);
     for (int j = j0; j <= j1; ++j) {
-        load_row(j + 1);
+        stage_in(j + 1, nxt);                  // row j + 1 was fetched one iteration ahead
         __syncthreads();
+        if (j + 1 <= j1)
+            fetch(j + 2, nxt);                 // in flight while this iteration computes
 #pragma unroll
         for (int s = 1; s <= T; ++s) {
             const int r = j - s + 1;
@@ -512,21 +549,21 @@ __global__ void __launch_bounds__(128) k_pressure_tb(const __grid_constant__ Pre
                 const int rl = r - ylo;
                 const float *src = sm + L.ring(s - 1);
                 const int ws = L.width(s - 1);
-                const float *rr = sm + L.rring();
-                const int rslot_m = (rl - 1 + (T + 2)) % (T + 2), rslot_0 = rl % (T + 2),
-                          rslot_p = (rl + 1) % (T + 2);
+                const int fs_m = ((rl - 1 + (T + 2)) % (T + 2)) * w0, fs_0 = (rl % (T + 2)) * w0,
+                          fs_p = ((rl + 1) % (T + 2)) * w0;
                 const float *srow_m = src + ((rl - 1 + 3) % 3) * 8 * ws;   // row r - 1
                 const float *srow_0 = src + (rl % 3) * 8 * ws;             // row r
                 const float *srow_p = src + ((rl + 1) % 3) * 8 * ws;       // row r + 1
-                const float *Rm = rr + rslot_m * L.width(0), *R0 = rr + rslot_0 * L.width(0),
-                            *Rp = rr + rslot_p * L.width(0);
+                const float *Rm = sm + L.rring() + fs_m, *R0 = sm + L.rring() + fs_0,
+                            *Rp = sm + L.rring() + fs_p;
+                const float *IT = sm + L.tring() + fs_0, *FQ = sm + L.fring() + fs_0;
                 for (int c = tid; c < L.width(s); c += W) {
                     const int xl = x0 - halo + c;
                     if (!(perx || (xl >= 0 && xl < g.nx)))
                         continue;
                     const int xw = perx ? wrap_coord(xl, g.nx) : xl;
                     const int cs = c + 1;              // this node in stage s-1 columns
-                    const int c0 = c + s;              // this node in stage-0 (R) columns
+                    const int c0 = c + s;              // this node in input-row columns
                     const float r0 = R0[c0];
                     float f[8];
                     const bool wall = (!perx && (xw == 0 || xw == g.nx - 1)) ||
@@ -566,13 +603,8 @@ __global__ void __launch_bounds__(128) k_pressure_tb(const __grid_constant__ Pre
                         }
                     }
                     const float dP = pressure_of(f);
-                    const int o = rw * p + xw;
-                    const float it = __ldg(a.inv_tau + o);
-                    float F = a.Fp ? __ldg(a.Fp + o) : 0.0f;
-                    for (int k = 0; k < a.w.n; ++k)
-                        if (o == a.w.idx[k])
-                            F += a.w.fp[k];
-                    const float Fq = 0.125f * F;
+                    const float it = IT[c0];
+                    const float Fq = FQ[c0];
                     if (s < T) {
                         float *dst = sm + L.ring(s) + (rl % 3) * 8 * L.width(s);
 #pragma unroll
@@ -582,6 +614,7 @@ __global__ void __launch_bounds__(128) k_pressure_tb(const __grid_constant__ Pre
                             sm[L.dpring() + (rl % 3) * L.width(T - 1) + c] = dP;
                     } else if (xl >= x0 && xl < x0 + W && xl < g.nx && r >= y0 && r < y0 + H &&
                                r < g.ny && r >= 0) {
+                        const int o = rw * p + xw;
 #pragma unroll
                         for (int i = 0; i < 8; ++i)
                             a.fout[i][o] = collide1(f[i], wgt(i + 1), dP, it, Fq);
@@ -596,8 +629,10 @@ __global__ void __launch_bounds__(128) k_pressure_tb(const __grid_constant__ Pre
                     }
                 }
             }
-            __syncthreads();
+            if (s < T)
+                __syncthreads();
         }
+        __syncthreads();
     }
     if (CHECK) {
         const int lane = tid & 31, warp = tid >> 5;
@@ -1054,7 +1089,7 @@ size_t tb_smem_bytes(int T, int W)
     size_t floats = 0;
     for (int s = 0; s < T; ++s)
         floats += 24 * (size_t)(W + 2 * (T - s));
-    floats += (size_t)(T + 2) * (W + 2 * T) + 3 * (size_t)(W + 2);
+    floats += 3 * (size_t)(T + 2) * (W + 2 * T) + 3 * (size_t)(W + 2);
     return floats * sizeof(float);
 }
 

@@ -680,57 +680,78 @@ lbm2p_status check_params(const lbm2p_params *p, const lbm2p_inputs *in)
     return LBM2P_OK;
 }
 
-// Pick the fused-sweep tile shape by timing every candidate on this lattice.
-lbm2p_status autotune_fused(lbm2p *h, int T)
+// Pick how the pressure sweeps run on this lattice by timing every candidate: one sweep
+// per launch, and (when allowed) T = 2 and 4 fused sweeps over each tile shape (W columns,
+// H rows).  Runs on the zeroed buffers before initialisation; they are zeroed again after.
+lbm2p_status autotune_sweeps(lbm2p *h)
 {
     cudaStream_t st = (cudaStream_t)h->stream;
-    int dev = 0, sms = 0;
-    CUDA_TRY(h, cudaGetDevice(&dev));
-    CUDA_TRY(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     for (auto &a : h->allocs)
         CUDA_TRY(h, cudaMemsetAsync(a.ptr, 0, a.bytes, st));
     cudaEvent_t e0, e1;
     CUDA_TRY(h, cudaEventCreate(&e0));
     CUDA_TRY(h, cudaEventCreate(&e1));
-    float best = 1e30f;
     lbm2p_status status = LBM2P_OK;
-    for (int W : {128, 64, 32}) {
-        cudaError_t ce = lbm2p_launch::tb_prepare(T, W);
-        if (ce != cudaSuccess || lbm2p_launch::tb_blocks_per_sm(T, W) < 1) {
-            cudaGetLastError();
-            continue;
+    auto timed = [&](auto launch, int reps, float *ms) -> bool {
+        launch(0);
+        cudaEventRecord(e0, st);
+        for (int rep = 0; rep < reps; ++rep)
+            launch(rep + 1);
+        cudaEventRecord(e1, st);
+        cudaError_t le = cudaEventSynchronize(e1);
+        if (le != cudaSuccess) {
+            status = fail(h, LBM2P_ECUDA, "sweep timing failed: %s", cudaGetErrorString(le));
+            return false;
         }
-        for (int H : {64, 32, 16, 8}) {
-            const long long blocks = (long long)((h->nx + W - 1) / W) * ((h->ny + H - 1) / H);
-            if (blocks > (1LL << 30))
-                continue;
-            PressureArgs a = pressure_args(h, 0);
-            lbm2p_launch::pressure_sweeps_fused(a, T, W, H, false, (int)blocks, h->stream);
-            cudaEventRecord(e0, st);
-            for (int rep = 0; rep < 3; ++rep) {
-                PressureArgs b = pressure_args(h, rep % 2 == 0 ? 1 : 0);
-                lbm2p_launch::pressure_sweeps_fused(b, T, W, H, false, (int)blocks, h->stream);
-            }
-            cudaEventRecord(e1, st);
-            cudaError_t le = cudaEventSynchronize(e1);
-            if (le != cudaSuccess) {
-                status = fail(h, LBM2P_ECUDA, "fused sweep (W %d, H %d) failed: %s", W, H,
-                              cudaGetErrorString(le));
-                break;
-            }
-            float ms = 0.0f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < best) {
-                best = ms;
-                h->tb_T = T;
-                h->tb_W = W;
-                h->tb_H = H;
-                h->tb_grid = (int)blocks;
-            }
-        }
-        if (status != LBM2P_OK)
-            break;
+        cudaEventElapsedTime(ms, e0, e1);
+        return true;
+    };
+    const int reps = 4;
+    float best = 1e30f;   // per-sweep time
+    h->tb_T = 0;
+    if (h->p.fuse_sweeps != 2 && h->p.fuse_sweeps != 4) {
+        float ms = 0.0f;
+        if (!timed([&](int k) {
+                PressureArgs a = pressure_args(h, k % 2);
+                lbm2p_launch::pressure_sweep(a, false, false, h->grid, h->stream);
+            }, reps, &ms))
+            goto done;
+        best = ms / reps;
     }
+    if (h->p.fuse_sweeps != 1) {
+        for (int T : {2, 4}) {
+            if (h->p.fuse_sweeps != 0 && h->p.fuse_sweeps != T)
+                continue;
+            for (int W : {128, 64, 32}) {
+                cudaError_t ce = lbm2p_launch::tb_prepare(T, W);
+                if (ce != cudaSuccess || lbm2p_launch::tb_blocks_per_sm(T, W) < 1) {
+                    cudaGetLastError();
+                    continue;
+                }
+                for (int H : {64, 32, 16, 8}) {
+                    const long long blocks =
+                        (long long)((h->nx + W - 1) / W) * ((h->ny + H - 1) / H);
+                    if (blocks > (1LL << 30))
+                        continue;
+                    float ms = 0.0f;
+                    if (!timed([&](int k) {
+                            PressureArgs a = pressure_args(h, k % 2);
+                            lbm2p_launch::pressure_sweeps_fused(a, T, W, H, false, (int)blocks,
+                                                                h->stream);
+                        }, reps, &ms))
+                        goto done;
+                    if (ms / (reps * T) < best) {
+                        best = ms / (reps * T);
+                        h->tb_T = T;
+                        h->tb_W = W;
+                        h->tb_H = H;
+                        h->tb_grid = (int)blocks;
+                    }
+                }
+            }
+        }
+    }
+done:
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (status != LBM2P_OK)
@@ -848,15 +869,11 @@ lbm2p_status build(lbm2p *h, const lbm2p_inputs *in, lbm2p_step_stats *init_stat
     if (!ok)
         return fail(h, LBM2P_ENOMEM, "device allocation of %.1f MiB failed",
                     (double)pb * 45 / (1 << 20));
-    // fused sweeps: time each tile shape (W columns, H rows) with real launches on the
-    // zeroed buffers and keep the fastest; the buffers are zeroed again afterwards
-    {
-        const int T = p.fuse_sweeps == 0 ? 2 : p.fuse_sweeps;
-        if (T > 1) {
-            lbm2p_status e = autotune_fused(h, T);
-            if (e != LBM2P_OK)
-                return e;
-        }
+    // single or fused sweeps, and the fused tile shape: timed on this lattice
+    if (p.fuse_sweeps != 1) {
+        lbm2p_status e = autotune_sweeps(h);
+        if (e != LBM2P_OK)
+            return e;
     }
     {
         int np = h->grid > h->grid_check ? h->grid : h->grid_check;
