@@ -103,9 +103,11 @@ typedef struct {
                                    periodic side must be paired with its opposite */
     int storage;                /* lbm2p_storage */
     int fuse_sweeps;            /* pressure sweeps fused per kernel launch: 0 = automatic,
-                                   1 = one sweep per launch, 2 or 4 = that many (results are
-                                   identical bit for bit; fusion reads and writes the
-                                   populations once per fused group of sweeps) */
+                                   1 = one sweep per launch, 2 or 4 = that many.  Results are
+                                   identical bit for bit whatever the choice; fusion reads and
+                                   writes the populations once per fused group of sweeps.
+                                   Within the choice, create times the candidate kernels and
+                                   tile shapes on the lattice and keeps the fastest. */
     void *stream;               /* cudaStream_t the work is enqueued on */
     void *(*alloc)(size_t bytes, void *ctx);            /* optional device allocator */
     void (*release)(void *ptr, size_t bytes, void *ctx); /* its matching free */

@@ -260,6 +260,25 @@ __device__ __forceinline__ float4 shift_in_right(float4 v, const float *row, int
     return make_float4(v.y, v.z, v.w, r);
 }
 
+// (left neighbour of v.x, v.x, v.y, v.z): the row shifted right by one node; lane 0 takes
+// the element left of the warp from `edge`
+__device__ __forceinline__ float4 shl(float4 v, float edge, int lane)
+{
+    float l = __shfl_up_sync(0xffffffffu, v.w, 1);
+    if (lane == 0)
+        l = edge;
+    return make_float4(l, v.x, v.y, v.z);
+}
+
+// (v.y, v.z, v.w, right neighbour of v.w); lane 31 takes the element right of the warp
+__device__ __forceinline__ float4 shr(float4 v, float edge, int lane)
+{
+    float r = __shfl_down_sync(0xffffffffu, v.x, 1);
+    if (lane == 31)
+        r = edge;
+    return make_float4(v.y, v.z, v.w, r);
+}
+
 // n + w (r - r0), elementwise
 __device__ __forceinline__ float4 dev4(float4 n, float w, float4 r, float4 r0)
 {
@@ -267,8 +286,11 @@ __device__ __forceinline__ float4 dev4(float4 n, float w, float4 r, float4 r0)
                        dev1(n.w, w, r.w, r0.w));
 }
 
+#ifndef LBM2P_SWEEP_MINB
+#define LBM2P_SWEEP_MINB 4
+#endif
 template <bool CHECK, bool WRITE_P>
-__global__ void __launch_bounds__(kBlock) k_pressure(const __grid_constant__ PressureArgs a)
+__global__ void __launch_bounds__(kBlock, LBM2P_SWEEP_MINB) k_pressure(const __grid_constant__ PressureArgs a)
 {
     const Geom &g = a.g;
     const int lane = threadIdx.x & 31;
@@ -285,32 +307,70 @@ __global__ void __launch_bounds__(kBlock) k_pressure(const __grid_constant__ Pre
         float sd = 0.0f, sdd = 0.0f, sp = 0.0f, spp = 0.0f;
         const bool row_inner = y > 0 && y < g.ny - 1;     // uniform over the block
         bool fast = false;
-        float4 f[8], r0;
+        float4 f[8], r0, it, F;
         if (row_inner) {
-            // every lane takes part in the shuffles; lanes past the padded row load nothing
+            // every lane takes part in the shuffles; lanes past the padded row load nothing.
+            // All global loads of the tile are issued before any of them is used.
             const bool in_row = x0 < p;
             const bool hl = x0 >= 1 && in_row, hr = x0 + 4 < g.nx;
             const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
             const float *R = a.R;
-            r0 = in_row ? ld4(R, o) : z;
-            const float4 rm = in_row ? ld4(R, o - p) : z, rp = in_row ? ld4(R, o + p) : z;
-            const float4 rl = shift_in_left(r0, R, o, lane, hl), rr = shift_in_right(r0, R, o, lane, hr);
-            const float4 rml = shift_in_left(rm, R, o - p, lane, hl), rmr = shift_in_right(rm, R, o - p, lane, hr);
-            const float4 rpl = shift_in_left(rp, R, o + p, lane, hl), rpr = shift_in_right(rp, R, o + p, lane, hr);
+            float4 v[11];
+            if (in_row) {
+                v[0] = ld4(a.fin[0], o);          // c = ( 1, 0): row y, shifted right
+                v[1] = ld4(a.fin[1], o - p);      // c = ( 0, 1): row y - 1
+                v[2] = ld4(a.fin[2], o);          // c = (-1, 0): row y, shifted left
+                v[3] = ld4(a.fin[3], o + p);      // c = ( 0,-1): row y + 1
+                v[4] = ld4(a.fin[4], o - p);      // c = ( 1, 1)
+                v[5] = ld4(a.fin[5], o - p);      // c = (-1, 1)
+                v[6] = ld4(a.fin[6], o + p);      // c = (-1,-1)
+                v[7] = ld4(a.fin[7], o + p);      // c = ( 1,-1)
+                v[8] = ld4(R, o - p);
+                v[9] = ld4(R, o);
+                v[10] = ld4(R, o + p);
+                it = ld4(a.inv_tau, o);
+                F = a.Fp ? ld4(a.Fp, o) : z;
+            } else {
+#pragma unroll
+                for (int i = 0; i < 11; ++i)
+                    v[i] = z;
+                it = z;
+                F = z;
+            }
+            // the elements just left / right of this warp's 128 nodes (lanes 0 and 31)
+            float el[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, er[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (lane == 0 && hl) {
+                el[0] = __ldg(a.fin[0] + o - 1);
+                el[1] = __ldg(a.fin[4] + o - p - 1);
+                el[2] = __ldg(a.fin[7] + o + p - 1);
+                el[3] = __ldg(R + o - p - 1);
+                el[4] = __ldg(R + o - 1);
+                el[5] = __ldg(R + o + p - 1);
+            }
+            if (lane == 31 && hr) {
+                er[0] = __ldg(a.fin[2] + o + 4);
+                er[1] = __ldg(a.fin[5] + o - p + 4);
+                er[2] = __ldg(a.fin[6] + o + p + 4);
+                er[3] = __ldg(R + o - p + 4);
+                er[4] = __ldg(R + o + 4);
+                er[5] = __ldg(R + o + p + 4);
+            }
+            r0 = v[9];
+            const float4 rl = shl(v[9], el[4], lane), rr = shr(v[9], er[4], lane);
+            const float4 rml = shl(v[8], el[3], lane), rmr = shr(v[8], er[3], lane);
+            const float4 rpl = shl(v[10], el[5], lane), rpr = shr(v[10], er[5], lane);
             // a_i = n_i(x - c_i) + w_i (R(x - c_i) - R(x))
-            f[0] = dev4(shift_in_left(in_row ? ld4(a.fin[0], o) : z, a.fin[0], o, lane, hl), wgt(1), rl, r0);
-            f[1] = dev4(in_row ? ld4(a.fin[1], o - p) : z, wgt(2), rm, r0);
-            f[2] = dev4(shift_in_right(in_row ? ld4(a.fin[2], o) : z, a.fin[2], o, lane, hr), wgt(3), rr, r0);
-            f[3] = dev4(in_row ? ld4(a.fin[3], o + p) : z, wgt(4), rp, r0);
-            f[4] = dev4(shift_in_left(in_row ? ld4(a.fin[4], o - p) : z, a.fin[4], o - p, lane, hl), wgt(5), rml, r0);
-            f[5] = dev4(shift_in_right(in_row ? ld4(a.fin[5], o - p) : z, a.fin[5], o - p, lane, hr), wgt(6), rmr, r0);
-            f[6] = dev4(shift_in_right(in_row ? ld4(a.fin[6], o + p) : z, a.fin[6], o + p, lane, hr), wgt(7), rpr, r0);
-            f[7] = dev4(shift_in_left(in_row ? ld4(a.fin[7], o + p) : z, a.fin[7], o + p, lane, hl), wgt(8), rpl, r0);
+            f[0] = dev4(shl(v[0], el[0], lane), wgt(1), rl, r0);
+            f[1] = dev4(v[1], wgt(2), v[8], r0);
+            f[2] = dev4(shr(v[2], er[0], lane), wgt(3), rr, r0);
+            f[3] = dev4(v[3], wgt(4), v[10], r0);
+            f[4] = dev4(shl(v[4], el[1], lane), wgt(5), rml, r0);
+            f[5] = dev4(shr(v[5], er[1], lane), wgt(6), rmr, r0);
+            f[6] = dev4(shr(v[6], er[2], lane), wgt(7), rpr, r0);
+            f[7] = dev4(shl(v[7], el[2], lane), wgt(8), rpl, r0);
             fast = hl && x0 + 4 <= g.nx - 1;
         }
         if (fast) {
-            const float4 it = ld4(a.inv_tau, o);
-            float4 F = a.Fp ? ld4(a.Fp, o) : make_float4(0.f, 0.f, 0.f, 0.f);
             for (int k = 0; k < a.w.n; ++k) {
                 const int d = a.w.idx[k] - o;
                 if (d >= 0 && d < 4) {
@@ -436,8 +496,10 @@ __global__ void __launch_bounds__(kBlock) k_pressure(const __grid_constant__ Pre
 // sweeps.  CHECK: the residual partials of the last stage against stage T - 1.
 // --------------------------------------------------------------------------------------
 struct TBLayout {
-    int W, T;
-    __device__ __forceinline__ int width(int s) const { return W + 2 * (T - s); }
+    int Wt, T;                                     // threads per block, fused sweeps
+    // stage s is computed on Wt - 2 s columns: the input row spans all threads and the last
+    // stage the Wt - 2 T columns the block owns, so every stage is one pass of the block
+    __device__ __forceinline__ int width(int s) const { return Wt - 2 * s; }
     // float offset of stage s's ring (s = 0 .. T-1): 3 rows x 8 planes x width(s)
     __device__ __forceinline__ int ring(int s) const
     {
@@ -455,9 +517,9 @@ struct TBLayout {
 
 __device__ __forceinline__ int wrap_coord(int v, int n) { return ((v % n) + n) % n; }
 
-// one input row's values for the (at most two) columns a thread stages
+// one input row's values for the column a thread stages
 struct TBRow {
-    float v[2][11];
+    float v[11];
 };
 
 template <int T, bool CHECK>
@@ -465,8 +527,9 @@ __global__ void __launch_bounds__(128) k_pressure_tb(const __grid_constant__ Pre
 {
     extern __shared__ float sm[];
     const Geom &g = a.g;
-    const int W = blockDim.x;
-    const TBLayout L{W, T};
+    const int Wt = blockDim.x;
+    const int W = Wt - 2 * T;                      // columns owned by the block
+    const TBLayout L{Wt, T};
     const int strips = (g.nx + W - 1) / W;
     const int x0 = (blockIdx.x % strips) * W;
     const int y0 = (blockIdx.x / strips) * H;
@@ -479,32 +542,28 @@ __global__ void __launch_bounds__(128) k_pressure_tb(const __grid_constant__ Pre
     const float dshift = CHECK ? a.shift[1] : 0.0f;
     float sd = 0.0f, sdd = 0.0f, sp = 0.0f, spp = 0.0f;
 
-    // global loads of input row r (8 planes, R, 1/tau_f, F~_p) into registers
+    // global loads of input row r (8 planes, R, 1/tau_f, F~_p) at this thread's column
     auto fetch = [&](int r, TBRow &row) {
         const bool vy = pery || (r >= 0 && r < g.ny);
         const int rw = pery ? wrap_coord(r, g.ny) : r;
+        const int xl = x0 - T + tid;
+        const bool vx = perx || (xl >= 0 && xl < g.nx);
+        if (vx && vy) {
+            const int o = rw * p + (perx ? wrap_coord(xl, g.nx) : xl);
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int c = tid + q * W;
-            const int xl = x0 - T + c;
-            const bool vx = c < w0 && (perx || (xl >= 0 && xl < g.nx));
-            if (vx && vy) {
-                const int o = rw * p + (perx ? wrap_coord(xl, g.nx) : xl);
+            for (int i = 0; i < 8; ++i)
+                row.v[i] = __ldg(a.fin[i] + o);
+            row.v[8] = __ldg(a.R + o);
+            row.v[9] = __ldg(a.inv_tau + o);
+            float F = a.Fp ? __ldg(a.Fp + o) : 0.0f;
+            for (int k = 0; k < a.w.n; ++k)
+                if (o == a.w.idx[k])
+                    F += a.w.fp[k];
+            row.v[10] = 0.125f * F;                // w_bar_i F~_p, w_bar_i = 1/8 (Eq. 3-5a)
+        } else {
 #pragma unroll
-                for (int i = 0; i < 8; ++i)
-                    row.v[q][i] = __ldg(a.fin[i] + o);
-                row.v[q][8] = __ldg(a.R + o);
-                row.v[q][9] = __ldg(a.inv_tau + o);
-                float F = a.Fp ? __ldg(a.Fp + o) : 0.0f;
-                for (int k = 0; k < a.w.n; ++k)
-                    if (o == a.w.idx[k])
-                        F += a.w.fp[k];
-                row.v[q][10] = 0.125f * F;          // w_bar_i F~_p, w_bar_i = 1/8 (Eq. 3-5a)
-            } else {
-#pragma unroll
-                for (int i = 0; i < 11; ++i)
-                    row.v[q][i] = 0.0f;
-            }
+            for (int i = 0; i < 11; ++i)
+                row.v[i] = 0.0f;
         }
     };
     // registers of input row r into the shared rings
@@ -513,17 +572,11 @@ __global__ void __launch_bounds__(128) k_pressure_tb(const __grid_constant__ Pre
         float *ring0 = sm + L.ring(0) + (rl % 3) * 8 * w0;
         const int fs = (rl % (T + 2)) * w0;
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int c = tid + q * W;
-            if (c < w0) {
-#pragma unroll
-                for (int i = 0; i < 8; ++i)
-                    ring0[i * w0 + c] = row.v[q][i];
-                sm[L.rring() + fs + c] = row.v[q][8];
-                sm[L.tring() + fs + c] = row.v[q][9];
-                sm[L.fring() + fs + c] = row.v[q][10];
-            }
-        }
+        for (int i = 0; i < 8; ++i)
+            ring0[i * w0 + tid] = row.v[i];
+        sm[L.rring() + fs + tid] = row.v[8];
+        sm[L.tring() + fs + tid] = row.v[9];
+        sm[L.fring() + fs + tid] = row.v[10];
     };
 
     TBRow nxt;
@@ -557,10 +610,9 @@ __global__ void __launch_bounds__(128) k_pressure_tb(const __grid_constant__ Pre
                 const float *Rm = sm + L.rring() + fs_m, *R0 = sm + L.rring() + fs_0,
                             *Rp = sm + L.rring() + fs_p;
                 const float *IT = sm + L.tring() + fs_0, *FQ = sm + L.fring() + fs_0;
-                for (int c = tid; c < L.width(s); c += W) {
-                    const int xl = x0 - halo + c;
-                    if (!(perx || (xl >= 0 && xl < g.nx)))
-                        continue;
+                const int c = tid;
+                const int xl = x0 - halo + c;
+                if (c < L.width(s) && (perx || (xl >= 0 && xl < g.nx))) {
                     const int xw = perx ? wrap_coord(xl, g.nx) : xl;
                     const int cs = c + 1;              // this node in stage s-1 columns
                     const int c0 = c + s;              // this node in input-row columns
@@ -650,15 +702,15 @@ __global__ void __launch_bounds__(128) k_pressure_tb(const __grid_constant__ Pre
         __syncthreads();
         if (tid < 4) {
             double acc = 0.0;
-            for (int w = 0; w < W / 32; ++w)
+            for (int w = 0; w < Wt / 32; ++w)
                 acc += red[w][tid];
             a.partials[4 * blockIdx.x + tid] = acc;
         }
     }
 }
 
-#ifdef LBM2P_SWEEP_SCALAR
-// One node per thread (row tiles of kBlock nodes): the same sweep with scalar loads.
+// One node per thread (row tiles of kBlock nodes): the same sweep with scalar loads and a
+// small register footprint (more resident warps); faster where the sweep is latency-bound.
 template <bool CHECK, bool WRITE_P>
 __global__ void __launch_bounds__(kBlock) k_pressure_scalar(const __grid_constant__ PressureArgs a)
 {
@@ -720,10 +772,6 @@ __global__ void __launch_bounds__(kBlock) k_pressure_scalar(const __grid_constan
         }
     }
 }
-#define K_SWEEP k_pressure_scalar
-#else
-#define K_SWEEP k_pressure
-#endif
 
 // r = ||dP - mean dP|| / ||P - mean P|| from the block partials (FP64, fixed order).
 // Called by all 256 threads of one block; returns r in thread 0.
@@ -1056,41 +1104,45 @@ namespace lbm2p_launch {
 
 static cudaStream_t S(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
-int max_blocks_per_sm_pressure(bool check)
+static void *sweep_func(int kind, bool check, bool write_p)
+{
+    if (kind == 1)
+        return check ? (write_p ? (void *)k_pressure_scalar<true, true> : (void *)k_pressure_scalar<true, false>)
+                     : (write_p ? (void *)k_pressure_scalar<false, true> : (void *)k_pressure_scalar<false, false>);
+    return check ? (write_p ? (void *)k_pressure<true, true> : (void *)k_pressure<true, false>)
+                 : (write_p ? (void *)k_pressure<false, true> : (void *)k_pressure<false, false>);
+}
+
+int max_blocks_per_sm_pressure(bool check, int kind)
 {
     int a = 0, b = 0;
-    if (check) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, K_SWEEP<true, true>, kBlock, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, K_SWEEP<true, false>, kBlock, 0);
-    } else {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, K_SWEEP<false, false>, kBlock, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, K_SWEEP<false, true>, kBlock, 0);
-    }
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, sweep_func(kind, check, true), kBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, sweep_func(kind, check, false), kBlock, 0);
     int m = a < b ? a : b;
     return m > 0 ? m : 1;
 }
 
-void pressure_sweep(const PressureArgs &a, bool check, bool write_p, int grid, void *stream)
+void pressure_sweep(const PressureArgs &a, bool check, bool write_p, int grid, void *stream,
+                    int kind)
 {
-    // grid: resident capacity of the plain sweep; check sweeps use the capacity of theirs
-    
-    if (check && write_p)
-        K_SWEEP<true, true><<<grid, kBlock, 0, S(stream)>>>(a);
-    else if (check)
-        K_SWEEP<true, false><<<grid, kBlock, 0, S(stream)>>>(a);
-    else if (write_p)
-        K_SWEEP<false, true><<<grid, kBlock, 0, S(stream)>>>(a);
-    else
-        K_SWEEP<false, false><<<grid, kBlock, 0, S(stream)>>>(a);
+    // grid: resident capacity of the chosen kernel; check sweeps use the capacity of theirs
+    void *args[] = {(void *)&a};
+    cudaLaunchKernel(sweep_func(kind, check, write_p), dim3(grid), dim3(kBlock), args, 0, S(stream));
 }
 
-size_t tb_smem_bytes(int T, int W)
+size_t tb_smem_bytes(int T, int Wt)
 {
     size_t floats = 0;
     for (int s = 0; s < T; ++s)
-        floats += 24 * (size_t)(W + 2 * (T - s));
-    floats += 3 * (size_t)(T + 2) * (W + 2 * T) + 3 * (size_t)(W + 2);
+        floats += 24 * (size_t)(Wt - 2 * s);
+    floats += 3 * (size_t)(T + 2) * Wt + 3 * (size_t)(Wt - 2 * T + 2);
     return floats * sizeof(float);
+}
+
+long long tb_grid(int T, int Wt, int H, int nx, int ny)
+{
+    const int W = Wt - 2 * T;
+    return (long long)((nx + W - 1) / W) * ((ny + H - 1) / H);
 }
 
 static void *tb_func(int T, bool check)
@@ -1193,12 +1245,10 @@ static cudaError_t add_kernel(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraph
 }
 
 cudaError_t node_pressure(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
-                          const PressureArgs &a, bool check, bool write_p, int grid)
+                          const PressureArgs &a, bool check, bool write_p, int grid, int kind)
 {
-    void *func = check ? (write_p ? (void *)K_SWEEP<true, true> : (void *)K_SWEEP<true, false>)
-                       : (write_p ? (void *)K_SWEEP<false, true> : (void *)K_SWEEP<false, false>);
     void *args[] = {(void *)&a};
-    return add_kernel(n, g, dep, func, grid, kBlock, args);
+    return add_kernel(n, g, dep, sweep_func(kind, check, write_p), grid, kBlock, args);
 }
 
 cudaError_t node_pressure_fused(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,

@@ -188,13 +188,16 @@ lbm2p_status set_global_error(lbm2p_status st, const char *fmt, ...);
 // Launchers implemented in kernels.cu (all asynchronous on `stream`).
 namespace lbm2p_launch {
 using namespace lbm2p_dev;
-int max_blocks_per_sm_pressure(bool check);
-void pressure_sweep(const PressureArgs &a, bool check, bool write_p, int grid, void *stream);
+// single-sweep kernels: kind 0 = four nodes per thread (float4), kind 1 = one node per thread
+int max_blocks_per_sm_pressure(bool check, int kind);
+void pressure_sweep(const PressureArgs &a, bool check, bool write_p, int grid, void *stream,
+                    int kind = 0);
 void residual_finalize(const double *partials, int nparts, long long nnodes, float *shift,
                        ResidualOut *out, void *stream);
 // T pressure sweeps fused in one launch (T = 2 or 4), W threads per block (a multiple of
-// 32, at most 128), H rows per block; grid = ceil(nx / W) * ceil(ny / H)
+// 32, at most 128) owning W - 2T columns, H rows per block; grid = tb_grid(...)
 size_t tb_smem_bytes(int T, int W);
+long long tb_grid(int T, int W, int H, int nx, int ny);
 cudaError_t tb_prepare(int T, int W);
 int tb_blocks_per_sm(int T, int W);
 void pressure_sweeps_fused(const PressureArgs &a, int T, int W, int H, bool check, int grid,
@@ -208,7 +211,7 @@ void tau_from_S(float *inv_tau, const float *S, const float *K, Geom g, Model m,
 void fields(const FieldsArgs &a, int grid, void *stream);
 // graph nodes (explicit construction; parameters are copied into the node)
 cudaError_t node_pressure(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
-                          const PressureArgs &a, bool check, bool write_p, int grid);
+                          const PressureArgs &a, bool check, bool write_p, int grid, int kind);
 cudaError_t node_pressure_fused(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
                                 const PressureArgs &a, int T, int W, int H, bool check, int grid);
 cudaError_t node_finalize_loop(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,

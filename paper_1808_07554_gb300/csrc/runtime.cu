@@ -39,6 +39,8 @@ struct lbm2p {
     double s = 0, tau_g = 0, D_ref = 0;
     int grid = 0;              // blocks of every grid-stride lattice launch
     int grid_check = 0;        // blocks of a pressure sweep that accumulates the residual
+    int sweep_kind = 0;        // single-sweep kernel: 0 = four nodes per thread, 1 = one
+    int grid_k[2] = {}, grid_check_k[2] = {};
     int tb_T = 0, tb_W = 0, tb_H = 0, tb_grid = 0;   // fused sweeps per launch and tile shape
     int tb_T_graph = 0;        // fused sweeps used inside the graph loop body (0: single sweeps)
     void *stream = nullptr;
@@ -312,7 +314,8 @@ lbm2p_status add_loop(lbm2p *h, cudaGraph_t G, const cudaGraphNode_t *dep, int p
             cudaGraphNode_t n;
             PressureArgs a = pressure_args(h, src);
             CUDA_TRY(h, lbm2p_launch::node_pressure(&n, body, prev ? &prev : nullptr, a, kk == m,
-                                                    kk == m - 1, kk == m ? h->grid_check : h->grid));
+                                                    kk == m - 1, kk == m ? h->grid_check : h->grid,
+                                                    h->sweep_kind));
             prev = n;
             src = 1 - src;
         }
@@ -428,7 +431,7 @@ lbm2p_status pressure_solve(lbm2p *h, int replay, int *k_out, double *r_out, flo
             const bool write_p = nf == 0 && is_check(kk + 1) && kk + 1 >= 2;
             PressureArgs a = pressure_args(h, h->cur_f);
             lbm2p_launch::pressure_sweep(a, check, write_p, check ? h->grid_check : h->grid,
-                                         h->stream);
+                                         h->stream, h->sweep_kind);
             LAUNCHED(h, "pressure sweep");
             h->cur_f = 1 - h->cur_f;
             h->sweeps += 1;
@@ -710,13 +713,18 @@ lbm2p_status autotune_sweeps(lbm2p *h)
     float best = 1e30f;   // per-sweep time
     h->tb_T = 0;
     if (h->p.fuse_sweeps != 2 && h->p.fuse_sweeps != 4) {
-        float ms = 0.0f;
-        if (!timed([&](int k) {
-                PressureArgs a = pressure_args(h, k % 2);
-                lbm2p_launch::pressure_sweep(a, false, false, h->grid, h->stream);
-            }, reps, &ms))
-            goto done;
-        best = ms / reps;
+        for (int kind = 0; kind < 2; ++kind) {
+            float ms = 0.0f;
+            if (!timed([&](int k) {
+                    PressureArgs a = pressure_args(h, k % 2);
+                    lbm2p_launch::pressure_sweep(a, false, false, h->grid_k[kind], h->stream, kind);
+                }, reps, &ms))
+                goto done;
+            if (ms / reps < best) {
+                best = ms / reps;
+                h->sweep_kind = kind;
+            }
+        }
     }
     if (h->p.fuse_sweeps != 1) {
         for (int T : {2, 4}) {
@@ -729,8 +737,7 @@ lbm2p_status autotune_sweeps(lbm2p *h)
                     continue;
                 }
                 for (int H : {64, 32, 16, 8}) {
-                    const long long blocks =
-                        (long long)((h->nx + W - 1) / W) * ((h->ny + H - 1) / H);
+                    const long long blocks = lbm2p_launch::tb_grid(T, W, H, h->nx, h->ny);
                     if (blocks > (1LL << 30))
                         continue;
                     float ms = 0.0f;
@@ -839,8 +846,13 @@ lbm2p_status build(lbm2p *h, const lbm2p_inputs *in, lbm2p_step_stats *init_stat
             blocks = tiles;
         return (int)(blocks > 0 ? blocks : 1);
     };
-    h->grid = cap_grid((long long)sms * lbm2p_launch::max_blocks_per_sm_pressure(false));
-    h->grid_check = cap_grid((long long)sms * lbm2p_launch::max_blocks_per_sm_pressure(true));
+    for (int kind = 0; kind < 2; ++kind) {
+        h->grid_k[kind] = cap_grid((long long)sms * lbm2p_launch::max_blocks_per_sm_pressure(false, kind));
+        h->grid_check_k[kind] = cap_grid((long long)sms * lbm2p_launch::max_blocks_per_sm_pressure(true, kind));
+    }
+    h->sweep_kind = 0;
+    h->grid = h->grid_k[0];
+    h->grid_check = h->grid_check_k[0];
     const size_t pb = (size_t)h->plane * sizeof(float);
     auto plane_alloc = [&](float **dst) -> bool {
         *dst = (float *)dev_alloc(h, pb);
@@ -869,15 +881,21 @@ lbm2p_status build(lbm2p *h, const lbm2p_inputs *in, lbm2p_step_stats *init_stat
     if (!ok)
         return fail(h, LBM2P_ENOMEM, "device allocation of %.1f MiB failed",
                     (double)pb * 45 / (1 << 20));
-    // single or fused sweeps, and the fused tile shape: timed on this lattice
-    if (p.fuse_sweeps != 1) {
+    // which single-sweep kernel, single or fused sweeps, and the fused tile shape: timed
+    // on this lattice (within what fuse_sweeps allows)
+    {
         lbm2p_status e = autotune_sweeps(h);
         if (e != LBM2P_OK)
             return e;
     }
+    h->grid = h->grid_k[h->sweep_kind];
+    h->grid_check = h->grid_check_k[h->sweep_kind];
     {
-        int np = h->grid > h->grid_check ? h->grid : h->grid_check;
-        np = np > h->tb_grid ? np : h->tb_grid;
+        int np = h->tb_grid;
+        for (int kind = 0; kind < 2; ++kind) {
+            np = np > h->grid_k[kind] ? np : h->grid_k[kind];
+            np = np > h->grid_check_k[kind] ? np : h->grid_check_k[kind];
+        }
         h->partials = (double *)dev_alloc(h, (size_t)np * 4 * sizeof(double));
     }
     h->mean = (double *)dev_alloc(h, 64);

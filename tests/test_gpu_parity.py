@@ -199,6 +199,14 @@ def test_example2_parity():
     assert_parity(err)
 
 
+def test_example2_phi_half_parity():
+    prob = W.example2(48, phi=0.5, beta=0.5)
+    orc, gpu, log = run_pair(prob, 20, replay=[200] * 20, init_replay=600)
+    err = compare(orc, gpu, gauge_free=False)
+    gpu.close()
+    assert_parity(err)
+
+
 def test_linear_pressure_exact_on_gpu():
     nx, ny = 40, 24
     dx = 1.0 / nx

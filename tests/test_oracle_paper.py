@@ -49,3 +49,11 @@ def test_example2_error_bound():
     err = _errors(prob, 1e-8)
     for k, e in err.items():
         assert e < g["bound"], (k, e)
+
+
+def test_example2_errors_fall_with_beta_at_phi_half():
+    g = GOLD["example2_beta_sweep"]
+    errs = [_errors(W.example2(48, phi=g["phi"], beta=b), 1e-8) for b in g["betas"]]
+    for k in ("P", "ux", "S"):
+        seq = [e[k] for e in errs]
+        assert all(a > b for a, b in zip(seq, seq[1:])), (k, seq)
