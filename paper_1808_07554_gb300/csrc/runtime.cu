@@ -854,8 +854,17 @@ lbm2p_status build(lbm2p *h, const lbm2p_inputs *in, lbm2p_step_stats *init_stat
     h->grid = h->grid_k[0];
     h->grid_check = h->grid_check_k[0];
     const size_t pb = (size_t)h->plane * sizeof(float);
+    // Planes of power-of-two size come back with identical low address bits, so the same
+    // node of different planes would fall on the same memory channels and cache sets.
+    // Each plane starts at a different multiple of 1280 B (128-B aligned) past its block.
+#ifndef LBM2P_PLANE_STAGGER
+#define LBM2P_PLANE_STAGGER 1280
+#endif
+    int plane_no = 0;
     auto plane_alloc = [&](float **dst) -> bool {
-        *dst = (float *)dev_alloc(h, pb);
+        const size_t off = (size_t)LBM2P_PLANE_STAGGER * (size_t)(plane_no++ % 24);
+        char *raw = (char *)dev_alloc(h, pb + off);
+        *dst = raw ? (float *)(raw + off) : nullptr;
         return *dst != nullptr;
     };
     bool ok = true;
