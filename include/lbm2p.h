@@ -197,6 +197,12 @@ lbm2p_status lbm2p_set_state(lbm2p *h, const float *buf, size_t count, int on_de
 /* Record CUDA events around each step and its sweeps (fills sweep_ms / step_ms). */
 lbm2p_status lbm2p_set_timing(lbm2p *h, int enable);
 
+/* How the pressure sweeps run on this handle, as chosen at create: sweeps fused per launch
+   (1, 2 or 4); the single-sweep kernel (0: four nodes per thread with 128-bit accesses,
+   1: one node per thread); the fused kernel's threads per block and rows per block (0 when
+   not fused). */
+lbm2p_status lbm2p_sweep_config(const lbm2p *h, int *fused, int *kind, int *tile_w, int *tile_h);
+
 /* Running totals since creation: kernels launched by the library, pressure sweeps run. */
 lbm2p_status lbm2p_counters(const lbm2p *h, long long *launches, long long *sweeps);
 

@@ -101,6 +101,7 @@ def load_library(path: str = LIB_PATH):
         "lbm2p_set_state": (C.c_int, [H, fp, C.c_size_t, C.c_int]),
         "lbm2p_set_timing": (C.c_int, [H, C.c_int]),
         "lbm2p_counters": (C.c_int, [H, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
+        "lbm2p_sweep_config": (C.c_int, [H] + [C.POINTER(C.c_int)] * 4),
         "lbm2p_pressure_sweep_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int),
                                                    C.POINTER(fp), C.POINTER(fp), fp, fp, fp,
                                                    C.POINTER(fp), fp, C.POINTER(C.c_double),
@@ -219,6 +220,13 @@ def lbm2p_pressure_sweep_noalloc(nx, ny, pitch, bc, n_in, n_out, R, inv_tau, Fp,
         cast(dP), C.byref(r), C.c_void_p(stream) if stream else None)
     _check(st, None)
     return r.value
+
+
+def lbm2p_sweep_config(h):
+    """(sweeps fused per launch, single-sweep kernel kind, fused tile threads, fused tile rows)"""
+    v = [C.c_int(0) for _ in range(4)]
+    _check(_lib_or_raise().lbm2p_sweep_config(h, *[C.byref(x) for x in v]), h)
+    return tuple(x.value for x in v)
 
 
 def lbm2p_destroy(h):
@@ -394,6 +402,9 @@ class Solver:
 
     def counters(self):
         return lbm2p_counters(self.h)
+
+    def sweep_config(self):
+        return lbm2p_sweep_config(self.h)
 
     # -- outputs --------------------------------------------------------------------------
     def fields(self, mean_free_P=False):

@@ -854,17 +854,8 @@ lbm2p_status build(lbm2p *h, const lbm2p_inputs *in, lbm2p_step_stats *init_stat
     h->grid = h->grid_k[0];
     h->grid_check = h->grid_check_k[0];
     const size_t pb = (size_t)h->plane * sizeof(float);
-    // Planes of power-of-two size come back with identical low address bits, so the same
-    // node of different planes would fall on the same memory channels and cache sets.
-    // Each plane starts at a different multiple of 1280 B (128-B aligned) past its block.
-#ifndef LBM2P_PLANE_STAGGER
-#define LBM2P_PLANE_STAGGER 1280
-#endif
-    int plane_no = 0;
     auto plane_alloc = [&](float **dst) -> bool {
-        const size_t off = (size_t)LBM2P_PLANE_STAGGER * (size_t)(plane_no++ % 24);
-        char *raw = (char *)dev_alloc(h, pb + off);
-        *dst = raw ? (float *)(raw + off) : nullptr;
+        *dst = (float *)dev_alloc(h, pb);
         return *dst != nullptr;
     };
     bool ok = true;
@@ -1262,6 +1253,21 @@ lbm2p_status lbm2p_set_timing(lbm2p *h, int enable)
     if (!h)
         return fail(nullptr, LBM2P_EINVAL, "NULL handle");
     h->timing = enable != 0;
+    return LBM2P_OK;
+}
+
+lbm2p_status lbm2p_sweep_config(const lbm2p *h, int *fused, int *kind, int *tile_w, int *tile_h)
+{
+    if (!h)
+        return fail(nullptr, LBM2P_EINVAL, "NULL handle");
+    if (fused)
+        *fused = h->tb_T > 1 ? h->tb_T : 1;
+    if (kind)
+        *kind = h->sweep_kind;
+    if (tile_w)
+        *tile_w = h->tb_T > 1 ? h->tb_W : 0;
+    if (tile_h)
+        *tile_h = h->tb_T > 1 ? h->tb_H : 0;
     return LBM2P_OK;
 }
 

@@ -47,6 +47,9 @@ def test_fused_equals_single_sweeps(kind, T):
     prob = _problem(kind)
     single = pkg.Solver.from_problem(prob, init_replay=0, fuse_sweeps=1)
     fused = pkg.Solver.from_problem(prob, init_replay=0, fuse_sweeps=T)
+    assert single.sweep_config()[0] == 1 and single.sweep_config()[1] in (0, 1)
+    cfg = fused.sweep_config()
+    assert cfg[0] == T and cfg[2] in (32, 64, 128) and cfg[3] in (8, 16, 32, 64)
     rng = np.random.default_rng(3)
     state = single.get_state()
     state[:8] = 0.01 * rng.standard_normal(state[:8].shape)
