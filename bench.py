@@ -12,8 +12,13 @@ Metric: MLUPS = nodes x (pressure sweeps + 1 saturation update) / time, summed o
 timed steps (and over ranks).  L2 is flushed before every timed step; each step is timed
 with CUDA events on the solver's stream.
 
+Workload batch_five_spot_64: 64 independent five-spot realisations with sizes drawn from
+{128, 256, 512}^2 (sigma, correlation length and viscosity ratio drawn per member), advanced
+together by one lbm2p_batch per step; the line also reports the same members stepped one
+after another.
+
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload five_spot_1024|five_spot_4096|manufactured_64]
+                    [--workload five_spot_1024|five_spot_4096|manufactured_64|batch_five_spot_64]
 """
 from __future__ import annotations
 
@@ -41,14 +46,37 @@ WORKLOADS = {
     "five_spot_1024": dict(kind="five_spot", n=1024),
     "five_spot_4096": dict(kind="five_spot", n=4096),
     "manufactured_64": dict(kind="manufactured", n=64),
+    # independent five-spot realisations of uneven sizes advanced by one batch (lbm2p_batch)
+    "batch_five_spot_64": dict(kind="batch", count=64, sizes=(128, 256, 512)),
 }
+SWEEP_KERNEL_NAMES = {1: "four nodes per thread (128-bit accesses)", 2: "one node per thread",
+                      3: "rows staged in shared memory by bulk async copies"}
 # DRAM bytes per pressure-sweep launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum),
 # keyed by workload; None until captured for the current kernel.
-NCU_TRAFFIC_PER_SWEEP = {"five_spot_1024": None, "five_spot_4096": None, "manufactured_64": None}
+NCU_TRAFFIC_PER_SWEEP = {"five_spot_1024": None, "five_spot_4096": None, "manufactured_64": None,
+                         "batch_five_spot_64": None}
+
+
+def batch_members(name: str, rank: int = 0):
+    """Realisations of a batch workload: sizes drawn uniformly from the workload's list,
+    sigma of ln K in [0.5, 2], correlation length in [8, 32] cells, viscosity ratio
+    mu_n / mu_w in [0.5, 10] (mu_w = 1), GRF seeds 4000 + member index."""
+    w = WORKLOADS[name]
+    rng = np.random.default_rng(4000 + rank)
+    out = []
+    for r in range(w["count"]):
+        n = int(rng.choice(w["sizes"]))
+        sigma, corr = float(rng.uniform(0.5, 2.0)), float(rng.uniform(8.0, 32.0))
+        ratio = float(rng.uniform(0.5, 10.0))
+        out.append(W.quarter_five_spot(n, seed=4000 + rank * w["count"] + r, sigma=sigma,
+                                       corr_len=corr, mu_w=1.0, mu_n=ratio))
+    return out
 
 
 def make_problem(name: str, rank: int = 0):
     w = WORKLOADS[name]
+    if w["kind"] == "batch":
+        return batch_members(name, rank)[0]
     if w["kind"] == "five_spot":
         return W.quarter_five_spot(w["n"], seed=2 + rank)
     return W.manufactured_periodic(w["n"])
@@ -237,7 +265,8 @@ def run_ours(args):
         if P0 is not None:
             prob.P0 = P0
     solver = pkg.Solver.from_problem(prob, tol=1e-8, check_every=args.check_every,
-                                     max_sub_iters=args.max_sub_iters, fuse_sweeps=args.fuse_sweeps)
+                                     max_sub_iters=args.max_sub_iters, fuse_sweeps=args.fuse_sweeps,
+                                     sweep_kernel=args.sweep_kernel)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t_setup
     init_sweeps = solver.init_stats.sub_iters
@@ -323,6 +352,7 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "nx": prob.nx, "ny": prob.ny, "tol": 1e-8,
                    "check_every": args.check_every, "fuse_sweeps": args.fuse_sweeps,
+                   "sweep_kernel": sweep_cfg[1], "sweep_tile": [sweep_cfg[2], sweep_cfg[3]],
                    "l2": "flushed before every timed step",
                    "sub_iters_per_step": ksub, "statuses": statuses,
                    "init_sweeps": init_sweeps, "setup_s": round(setup_s, 2),
@@ -335,8 +365,8 @@ def run_ours(args):
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": ("pressure sweep (fused stream + collide, Eq. 3-1), "
                                 + (f"{fused} sweeps per launch" if fused > 1 else
-                                   ("one node per thread" if sweep_cfg[1] == 1 else
-                                    "four nodes per thread")) + ", autotuned"),
+                                   SWEEP_KERNEL_NAMES.get(sweep_cfg[1], "?"))
+                                + (", autotuned" if args.sweep_kernel == 0 else "")),
                      "bytes_per_launch": BYTES_PER_SWEEP_NODE * nodes,
                      "avg_launch_us": avg_launch_s * 1e6,
                      "launch_time_includes": "the residual finalize kernel of every 8th sweep",
@@ -349,6 +379,152 @@ def run_ours(args):
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = {k: v for k, v in cpu_baseline(args.workload).items()
                                 if k != "seconds"}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+# bytes per node of the once-per-step kernels: S refresh 44, saturation update 124, rebase 76
+BYTES_PER_STEP_NODE = 244
+
+
+def run_batch(args):
+    """Batched realisations: every member created (and its t = 0 pressure solved) alone,
+    then all advanced by one lbm2p_batch per step; afterwards the same members stepped one
+    after another through their own handles, for comparison."""
+    import torch
+    import paper_1808_07554_gb300 as pkg
+    from paper_1808_07554_gb300 import build
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0 or not os.path.exists(build.LIB):
+        build.build()
+    if dist is not None:
+        dist.barrier()
+    pkg.load_library()
+
+    probs = batch_members(args.workload, rank)
+    nodes = np.array([p.nx * p.ny for p in probs], dtype=np.int64)
+    stream = torch.cuda.current_stream()
+    t_setup = time.perf_counter()
+    solvers, init_sweeps = [], 0
+    for p in probs:
+        if not args.cold_start:
+            P0 = coarse_initial_pressure(p, pkg)
+            if P0 is not None:
+                p.P0 = P0
+        s = pkg.Solver.from_problem(p, tol=1e-8, check_every=args.check_every,
+                                    max_sub_iters=args.max_sub_iters,
+                                    sweep_kernel=args.sweep_kernel)
+        init_sweeps += s.init_stats.sub_iters
+        solvers.append(s)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t_setup
+    batch = pkg.Batch(solvers)
+    for _ in range(args.warmup):
+        batch.step(1)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    launches0, tiles = batch.counters()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    step_ms, kmat, statuses = [], [], []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        ev0.record(stream)
+        st, stats = batch.step(1)
+        ev1.record(stream)
+        ev1.synchronize()
+        step_ms.append(ev0.elapsed_time(ev1))
+        kmat.append([x.sub_iters for x in stats[0]])
+        statuses.append(st)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clk = clocks.stop()
+    gpu_launches = batch.counters()[0] - launches0
+    k = np.array(kmat, dtype=np.int64)                       # [steps, members]
+    updates = int(np.sum(k * nodes[None, :]) + args.steps * nodes.sum())
+    step_bytes = float(np.sum((BYTES_PER_SWEEP_NODE * k + BYTES_PER_STEP_NODE) * nodes[None, :]))
+    total_ms = float(np.sum(step_ms))
+
+    # end to end: batch step + P and S of every member read back to host memory
+    e2e_steps = max(1, min(args.steps, 3))
+    e2e_updates = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        st, stats = batch.step(1)
+        for s in solvers:
+            s.fields()
+        e2e_updates += int(sum((x.sub_iters + 1) * n for x, n in zip(stats[0], nodes)))
+    e2e_s = time.perf_counter() - t0
+    batch.close()
+
+    # the same members one after another (each its own graph-resident step)
+    seq_steps = max(1, min(args.steps, 3))
+    seq_updates = 0
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(seq_steps):
+        for s, n in zip(solvers, nodes):
+            st, stats = s.step(1)
+            seq_updates += int(n) * (stats[0].sub_iters + 1)
+    ev1.record(stream)
+    ev1.synchronize()
+    seq_s = ev0.elapsed_time(ev1) / 1e3
+    for s in solvers:
+        s.close()
+
+    updates_all, time_max, e2e_all, e2e_max = aggregate(
+        [updates, total_ms / 1e3, e2e_updates, e2e_s], dist, device="cuda")
+    if rank != 0:
+        return 0
+    peak, peak_kind = peaks()
+    achieved = step_bytes / (total_ms / 1e3) / 1e9
+    sizes = {int(n): int(c) for n, c in zip(*np.unique([p.nx for p in probs], return_counts=True))}
+    line = {
+        "metric": "MLUPS", "value": updates_all / time_max / 1e6, "unit": "MLUPS",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "members": len(probs),
+                   "sizes": {f"{n}x{n}": c for n, c in sizes.items()},
+                   "nodes": int(nodes.sum()), "tol": 1e-8, "check_every": args.check_every,
+                   "l2": "flushed before every timed step",
+                   "sub_iters_max_per_step": [int(x) for x in k.max(axis=1)],
+                   "sub_iters_mean_per_step": [round(float(x), 1) for x in k.mean(axis=1)],
+                   "statuses": statuses, "init_sweeps_total": int(init_sweeps),
+                   "setup_s": round(setup_s, 2), "tiles_per_batched_sweep": int(tiles),
+                   "one_at_a_time_mlups": seq_updates / seq_s / 1e6,
+                   "one_at_a_time_steps": seq_steps,
+                   "parallelism": f"{world} x {len(probs)} independent realisations"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak,
+                     "traffic": NCU_TRAFFIC_PER_SWEEP.get(args.workload),
+                     "kernel": "whole batched step (kb_sweep dominant): algorithmic bytes of "
+                               "every kernel / step time",
+                     "bytes_per_step": step_bytes / args.steps, "peak_kind": peak_kind},
+        "e2e": {"value": e2e_all / e2e_max / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": int(8 * nodes.sum())},
+        "gpu_launches": int(gpu_launches),
+        "clocks": clk,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = {k2: v for k2, v in cpu_baseline(args.workload).items()
+                                if k2 != "seconds"}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -369,11 +545,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fuse-sweeps", type=int, default=0, choices=[0, 1, 2, 4],
                     help="pressure sweeps per launch: 0 = autotuned, 1, 2 or 4")
+    ap.add_argument("--sweep-kernel", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="single-sweep kernel: 0 = autotuned, 1 = float4, 2 = one node per "
+                         "thread, 3 = staged rows")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
     if args.impl == "reference":
         return run_reference(args)
+    if WORKLOADS[args.workload]["kind"] == "batch":
+        return run_batch(args)
     return run_ours(args)
 
 

@@ -42,7 +42,7 @@
 extern "C" {
 #endif
 
-#define LBM2P_ABI_VERSION 2
+#define LBM2P_ABI_VERSION 3
 /* Sparse wells passed to the sweep kernels as launch arguments (more wells: error). */
 #define LBM2P_MAX_WELLS 16
 
@@ -74,6 +74,15 @@ typedef enum { LBM2P_MOB_QUADRATIC = 0, LBM2P_MOB_DECOUPLED = 1, LBM2P_MOB_RATIO
  *                geometric mean of D_p(K, S0) over the grid at t = 0 (fixed for the run);
  *   PHYSICAL_DT: s = dt / dx^2 (pseudo step equal to the physical step, as in Sec. 4). */
 typedef enum { LBM2P_TAU_REFERENCE = 0, LBM2P_TAU_PHYSICAL_DT = 1 } lbm2p_tau_mode;
+
+/* Single-sweep pressure kernels.  All compute bit for bit the same populations:
+ *   VEC4:   four nodes per thread, 128-bit loads and stores;
+ *   SCALAR: one node per thread;
+ *   ROWS:   a block marches down a strip of rows whose input rows are staged in shared memory
+ *           by bulk asynchronous copies (cp.async.bulk) several rows ahead.
+ * AUTO lets create time them on the lattice and keep the fastest. */
+typedef enum { LBM2P_SWEEP_AUTO = 0, LBM2P_SWEEP_VEC4 = 1, LBM2P_SWEEP_SCALAR = 2,
+               LBM2P_SWEEP_ROWS = 3 } lbm2p_sweep_kernel;
 
 /* Population storage.  FP16_DEV (FP16 deviations from equilibrium) is reserved. */
 typedef enum { LBM2P_STORE_FP32 = 0, LBM2P_STORE_FP16_DEV = 1 } lbm2p_storage;
@@ -108,6 +117,7 @@ typedef struct {
                                    writes the populations once per fused group of sweeps.
                                    Within the choice, create times the candidate kernels and
                                    tile shapes on the lattice and keeps the fastest. */
+    int sweep_kernel;           /* lbm2p_sweep_kernel: the single-sweep kernel (AUTO: timed) */
     void *stream;               /* cudaStream_t the work is enqueued on */
     void *(*alloc)(size_t bytes, void *ctx);            /* optional device allocator */
     void (*release)(void *ptr, size_t bytes, void *ctx); /* its matching free */
@@ -198,13 +208,52 @@ lbm2p_status lbm2p_set_state(lbm2p *h, const float *buf, size_t count, int on_de
 lbm2p_status lbm2p_set_timing(lbm2p *h, int enable);
 
 /* How the pressure sweeps run on this handle, as chosen at create: sweeps fused per launch
-   (1, 2 or 4); the single-sweep kernel (0: four nodes per thread with 128-bit accesses,
-   1: one node per thread); the fused kernel's threads per block and rows per block (0 when
-   not fused). */
+   (1, 2 or 4); the single-sweep kernel (an lbm2p_sweep_kernel value, never AUTO); the tile
+   of the kernel that runs the sweeps: for fused sweeps its threads per block and rows per
+   block, for the ROWS kernel its strip width and rows per block, otherwise 0 and 0. */
 lbm2p_status lbm2p_sweep_config(const lbm2p *h, int *fused, int *kind, int *tile_w, int *tile_h);
 
 /* Running totals since creation: kernels launched by the library, pressure sweeps run. */
 lbm2p_status lbm2p_counters(const lbm2p *h, long long *launches, long long *sweeps);
+
+/* ---- Batched realisations --------------------------------------------------------------
+ * Independent lattices (for instance Monte Carlo realisations of the permeability field,
+ * each with its own size, coefficients and sources) advanced together: one CUDA graph per
+ * physical step runs steps 1-3 above for every member, each kernel covering the tiles of
+ * all members, and the sub-iteration continues while any member is still above its
+ * tolerance (members that met theirs stop sweeping).  The paper solves one realisation at
+ * a time; this is the same per-member computation scheduled so that small lattices fill
+ * the GPU together.
+ *
+ * members: count handles made by lbm2p_create on the current device, all on one stream,
+ * all with one even check_every that divides each member's max_sub_iters; each handle
+ * appears once.  The batch keeps pointers to the members' device memory: destroy the
+ * batch before any member, and while it exists step members only through the batch
+ * (lbm2p_batch_step returns EINVAL if a member was stepped alone).  Between batch steps
+ * a member may be read (fields, velocity, get_state, counters) and its sources, wall
+ * values and state replaced (set_sources, set_dirichlet, set_state).  The batch owns a
+ * little device memory of its own (a descriptor per member, 36 bytes per tile of 256
+ * nodes), allocated with cudaMalloc. */
+typedef struct lbm2p_batch lbm2p_batch;
+lbm2p_status lbm2p_batch_create(lbm2p_batch **out, lbm2p *const *members, int count);
+
+/* Advance every member nsteps physical steps.  Member m's stopping rule is its own tol
+ * and max_sub_iters.  replay: NULL, or nsteps*count sweep counts (step-major: entry
+ * s*count + m), each a multiple of check_every, run exactly.  stats: NULL or nsteps*count
+ * entries in the same order (step_ms is the whole batched step; sweep_ms is -1).  Each
+ * member's state after a step is bit-identical to lbm2p_step on that handle alone with the
+ * same sweep count.  Returns the worst status (ENONFINITE stops at the failing step). */
+lbm2p_status lbm2p_batch_step(lbm2p_batch *b, int nsteps, const int *replay,
+                              lbm2p_step_stats *stats);
+
+/* Kernels launched by the batch so far, and the tiles (256 nodes) of one batched sweep. */
+lbm2p_status lbm2p_batch_counters(const lbm2p_batch *b, long long *launches, int *total_tiles);
+
+/* One-line description of the batch's last error (NULL: that of the last failed create). */
+const char *lbm2p_batch_last_error(const lbm2p_batch *b);
+
+/* Free the batch (not its members; NULL is ignored).  Synchronises the stream first. */
+void lbm2p_batch_destroy(lbm2p_batch *b);
 
 /* ---- Pressure sweep for callers that cannot allocate device memory -------------------
  * The paper has no counterpart of this call: it exists for host programs that must not

@@ -26,6 +26,7 @@ PERIODIC, NOFLUX, DIRICHLET = 0, 1, 2
 MOB_QUADRATIC, MOB_DECOUPLED, MOB_RATIONAL = 0, 1, 2
 TAU_REFERENCE, TAU_PHYSICAL_DT = 0, 1
 STORE_FP32, STORE_FP16_DEV = 0, 1
+SWEEP_AUTO, SWEEP_VEC4, SWEEP_SCALAR, SWEEP_ROWS = 0, 1, 2, 3
 MAX_WELLS = 16
 STATE_PLANES = 20   # n_1..n_8 (f^+ - w_i R), g_0..g_8, 1/tau_f, S, R
 
@@ -44,6 +45,7 @@ class lbm2p_params(C.Structure):
                 ("tau_mode", C.c_int), ("tau_p", C.c_double), ("D_ref", C.c_double),
                 ("tol", C.c_double), ("max_sub_iters", C.c_int), ("check_every", C.c_int),
                 ("bc", C.c_int * 4), ("storage", C.c_int), ("fuse_sweeps", C.c_int),
+                ("sweep_kernel", C.c_int),
                 ("stream", C.c_void_p),
                 ("alloc", ALLOC_FN), ("release", RELEASE_FN), ("alloc_ctx", C.c_void_p)]
 
@@ -106,6 +108,12 @@ def load_library(path: str = LIB_PATH):
                                                    C.POINTER(fp), C.POINTER(fp), fp, fp, fp,
                                                    C.POINTER(fp), fp, C.POINTER(C.c_double),
                                                    C.c_void_p]),
+        "lbm2p_batch_create": (C.c_int, [C.POINTER(H), C.POINTER(H), C.c_int]),
+        "lbm2p_batch_step": (C.c_int, [H, C.c_int, C.POINTER(C.c_int),
+                                       C.POINTER(lbm2p_step_stats)]),
+        "lbm2p_batch_counters": (C.c_int, [H, C.POINTER(C.c_longlong), C.POINTER(C.c_int)]),
+        "lbm2p_batch_last_error": (C.c_char_p, [H]),
+        "lbm2p_batch_destroy": (None, [H]),
         "lbm2p_last_error": (C.c_char_p, [H]),
         "lbm2p_destroy": (None, [H]),
     }
@@ -234,6 +242,48 @@ def lbm2p_destroy(h):
         _lib_or_raise().lbm2p_destroy(h)
 
 
+def lbm2p_batch_last_error(b=None) -> str:
+    s = _lib_or_raise().lbm2p_batch_last_error(b)
+    return s.decode() if s else ""
+
+
+def lbm2p_batch_create(handles):
+    arr = (C.c_void_p * len(handles))(*[h.value if isinstance(h, C.c_void_p) else h
+                                        for h in handles])
+    b = C.c_void_p()
+    st = _lib_or_raise().lbm2p_batch_create(C.byref(b), arr, len(handles))
+    if st != OK:
+        raise LBM2PError(st, lbm2p_batch_last_error(None))
+    return b
+
+
+def lbm2p_batch_step(b, nsteps, count, replay=None, stats=None):
+    """replay: None or nsteps*count sweep counts, step-major."""
+    rp = None
+    if replay is not None:
+        flat = [int(v) for v in np.asarray(replay).reshape(-1)]
+        if len(flat) != nsteps * count:
+            raise ValueError(f"replay needs {nsteps * count} counts")
+        rp = (C.c_int * len(flat))(*flat)
+    st = _lib_or_raise().lbm2p_batch_step(b, nsteps, rp, stats)
+    if st not in (OK, ENOTCONVERGED):
+        raise LBM2PError(st, lbm2p_batch_last_error(b))
+    return st
+
+
+def lbm2p_batch_counters(b):
+    a, t = C.c_longlong(0), C.c_int(0)
+    st = _lib_or_raise().lbm2p_batch_counters(b, C.byref(a), C.byref(t))
+    if st != OK:
+        raise LBM2PError(st, lbm2p_batch_last_error(b))
+    return a.value, t.value
+
+
+def lbm2p_batch_destroy(b):
+    if b:
+        _lib_or_raise().lbm2p_batch_destroy(b)
+
+
 # ------------------------------------------------------------------------------------------
 # marshalling helpers
 # ------------------------------------------------------------------------------------------
@@ -290,7 +340,8 @@ class Solver:
     def __init__(self, *, nx, ny, dx, dt, phi, beta, mobility, mu_w, mu_n, D_s, tau_mode,
                  tau_p, bc, K, S0, P0=None, Fp=None, Fs=None, wells=(), P_b=None, S_b=None,
                  D_ref=0.0, tol=1e-8, max_sub_iters=10_000_000, check_every=8,
-                 init_replay=None, use_torch=True, stream=None, fuse_sweeps=0):
+                 init_replay=None, use_torch=True, stream=None, fuse_sweeps=0,
+                 sweep_kernel=0):
         lib = _lib_or_raise()
         self.nx, self.ny = int(nx), int(ny)
         n = self.nx * self.ny
@@ -302,6 +353,7 @@ class Solver:
         p.tau_mode, p.tau_p, p.D_ref = int(tau_mode), float(tau_p), float(D_ref)
         p.tol, p.max_sub_iters, p.check_every = float(tol), int(max_sub_iters), int(check_every)
         p.fuse_sweeps = int(fuse_sweeps)
+        p.sweep_kernel = int(sweep_kernel)
         for s in range(4):
             p.bc[s] = int(bc[s])
         self._mem = None
@@ -431,3 +483,40 @@ class Solver:
         if buf.size != n:
             raise ValueError(f"state must hold {n} floats")
         lbm2p_set_state(self.h, _fp(buf), n, 0)
+
+
+class Batch:
+    """Steps several Solver objects together (lbm2p_batch_*).  Keep the solvers alive and
+    step them only through the batch while it exists."""
+
+    def __init__(self, solvers):
+        self.solvers = list(solvers)
+        self.b = lbm2p_batch_create([s.h for s in self.solvers])
+
+    def close(self):
+        if getattr(self, "b", None):
+            lbm2p_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def step(self, nsteps=1, replay=None):
+        """Advance every member nsteps; returns (status, stats[nsteps][count])."""
+        n = len(self.solvers)
+        stats = (lbm2p_step_stats * max(1, nsteps * n))()
+        st = lbm2p_batch_step(self.b, nsteps, n, replay, stats)
+        return st, [[stats[s * n + m] for m in range(n)] for s in range(nsteps)]
+
+    def counters(self):
+        """(kernels launched by the batch, tiles of one batched sweep)"""
+        return lbm2p_batch_counters(self.b)

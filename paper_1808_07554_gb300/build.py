@@ -31,7 +31,7 @@ def sources() -> list[str]:
 
 
 def _deps() -> list[str]:
-    out = sources() + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
+    out = sources() + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     out.append(os.path.join(INCLUDE, "lbm2p.h"))
     return out
 

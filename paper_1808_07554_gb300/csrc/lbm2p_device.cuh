@@ -162,6 +162,14 @@ struct RebaseArgs {         // n_i += w_i (R - Pnew); R = Pnew  (node-local)
     Geom g;
 };
 
+struct RebaseMidArgs {      // within a long solve: R += dP of the last sweep (node-local)
+    float *n[8];
+    float *R;
+    const float *Fp;
+    Geom g;
+    Wells w;
+};
+
 struct ResidualOut {        // written by the finalize kernel
     double r;
     double mean_P;
@@ -173,7 +181,7 @@ struct LoopCtl {
     int k;          // sweeps run so far in this solve
     int m;          // sweeps per loop body (= check_every)
     int cap;        // max_sub_iters (a multiple of m)
-    int pad;
+    int every;      // sweeps between mid-solve rebases (a multiple of m)
     double tol;
     double r;       // last residual
 };
@@ -185,7 +193,7 @@ namespace lbm2p_internal {
 lbm2p_status set_global_error(lbm2p_status st, const char *fmt, ...);
 }
 
-// Launchers implemented in kernels.cu (all asynchronous on `stream`).
+// Launchers implemented in kernels.cu and sweep_rows.cu (all asynchronous on `stream`).
 namespace lbm2p_launch {
 using namespace lbm2p_dev;
 // single-sweep kernels: kind 0 = four nodes per thread (float4), kind 1 = one node per thread
@@ -202,6 +210,18 @@ cudaError_t tb_prepare(int T, int W);
 int tb_blocks_per_sm(int T, int W);
 void pressure_sweeps_fused(const PressureArgs &a, int T, int W, int H, bool check, int grid,
                            void *stream);
+// staged-rows single sweep (sweep_rows.cu): bt threads per block (128 or 256), npt nodes
+// per thread (1, or 2 with bt = 256), strips of bt * npt columns, H rows per block
+bool rows_shape_ok(int bt, int npt);
+size_t rows_smem_bytes(int bt, int npt);
+long long rows_grid(int bt, int npt, int H, int nx, int ny);
+cudaError_t rows_prepare(int bt, int npt);
+int rows_blocks_per_sm(int bt, int npt);
+void pressure_sweep_rows(const PressureArgs &a, bool check, bool write_p, int bt, int npt, int H,
+                         int grid, void *stream);
+cudaError_t node_pressure_rows(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
+                               const PressureArgs &a, bool check, bool write_p, int bt, int npt,
+                               int H, int grid);
 void refresh(const RefreshArgs &a, int grid, void *stream);
 void saturation(const SaturationArgs &a, int grid, void *stream);
 void init_g(const InitGArgs &a, int grid, void *stream);
@@ -216,7 +236,11 @@ cudaError_t node_pressure_fused(cudaGraphNode_t *n, cudaGraph_t g, const cudaGra
                                 const PressureArgs &a, int T, int W, int H, bool check, int grid);
 cudaError_t node_finalize_loop(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
                                const double *partials, int nparts, long long nnodes, float *shift,
-                               ResidualOut *out, LoopCtl *ctl, cudaGraphConditionalHandle h);
+                               ResidualOut *out, LoopCtl *ctl, cudaGraphConditionalHandle h,
+                               cudaGraphConditionalHandle h_rebase);
+void rebase_mid(const RebaseMidArgs &a, int grid, void *stream);
+cudaError_t node_rebase_mid(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
+                            const RebaseMidArgs &a, int grid);
 cudaError_t node_loop_reset(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
                             LoopCtl *ctl);
 cudaError_t node_refresh(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,

@@ -13,6 +13,7 @@
 
 #include "lbm2p.h"
 #include "lbm2p_device.cuh"
+#include "lbm2p_handle.h"
 
 using namespace lbm2p_dev;
 
@@ -20,60 +21,107 @@ namespace {
 
 thread_local std::string g_create_error;
 constexpr int kStatePlanes = 20;   // n_1..n_8, g_0..g_8, 1/tau_f, S, R
-
-struct Alloc {
-    void *ptr;
-    size_t bytes;
-};
+using lbm2p_internal::Alloc;
 
 }  // namespace
 
-struct lbm2p {
-    lbm2p_params p{};
-    int nx = 0, ny = 0, pitch = 0;
-    long long plane = 0;       // floats per plane
-    long long nnodes = 0;
-    Geom geom{};
-    Model model{};
-    Wells wells{};
-    double s = 0, tau_g = 0, D_ref = 0;
-    int grid = 0;              // blocks of every grid-stride lattice launch
-    int grid_check = 0;        // blocks of a pressure sweep that accumulates the residual
-    int sweep_kind = 0;        // single-sweep kernel: 0 = four nodes per thread, 1 = one
-    int grid_k[2] = {}, grid_check_k[2] = {};
-    int tb_T = 0, tb_W = 0, tb_H = 0, tb_grid = 0;   // fused sweeps per launch and tile shape
-    int tb_T_graph = 0;        // fused sweeps used inside the graph loop body (0: single sweeps)
-    void *stream = nullptr;
-    std::vector<Alloc> allocs;
-    float *fbuf[2][8] = {};
-    float *gbuf[2][9] = {};
-    float *inv_tau = nullptr, *K = nullptr, *S = nullptr, *Pio = nullptr, *tmp = nullptr;
-    float *R = nullptr;                // reference pressure of the pressure populations
-    float *Fp = nullptr, *Fs = nullptr;
-    float *Pb[4] = {}, *Sb[4] = {};
-    double *partials = nullptr, *mean = nullptr;
-    float *shift = nullptr;
-    ResidualOut *res = nullptr;
-    ResidualOut *res_host = nullptr;   // pinned
-    float *stage = nullptr;            // compact [ny][nx] device staging plane
-    int cur_f = 0, cur_g = 0;          // buffer holding the current post-collision state
-    long long launches = 0, sweeps = 0;
-    bool timing = false;
-    cudaEvent_t ev_step0 = nullptr, ev_step1 = nullptr, ev_sw0 = nullptr, ev_sw1 = nullptr;
-    // graph-resident sub-iteration (free-running solves when check_every is even and
-    // divides max_sub_iters): one graph per f parity for a bare solve, and one per
-    // (f parity, g parity) for a whole physical step
-    bool graph_ok = false;
-    LoopCtl *ctl = nullptr;
-    LoopCtl *ctl_host = nullptr;       // pinned
-    cudaGraph_t solve_g[2] = {};
-    cudaGraphExec_t solve_x[2] = {};
-    cudaGraph_t step_g[2][2] = {};
-    cudaGraphExec_t step_x[2][2] = {};
-    std::string err;
-};
+namespace lbm2p_internal {
+
+// ---- kernel argument blocks for the current ping-pong state -----------------------------
+PressureArgs pressure_args(lbm2p *h, int src)
+{
+    PressureArgs a{};
+    for (int i = 0; i < 8; ++i) {
+        a.fin[i] = h->fbuf[src][i];
+        a.fout[i] = h->fbuf[1 - src][i];
+    }
+    a.R = h->R;
+    a.inv_tau = h->inv_tau;
+    a.Fp = h->Fp;
+    a.Pio = h->Pio;
+    a.partials = h->partials;
+    a.shift = h->shift;
+    for (int s = 0; s < 4; ++s)
+        a.Pb[s] = h->Pb[s];
+    a.g = h->geom;
+    a.w = h->wells;
+    return a;
+}
+
+RefreshArgs refresh_args(lbm2p *h, int pg)
+{
+    RefreshArgs a{};
+    for (int i = 0; i < 9; ++i)
+        a.gin[i] = h->gbuf[pg][i];
+    a.K = h->K;
+    a.Fs = h->Fs;
+    a.inv_tau = h->inv_tau;
+    for (int s = 0; s < 4; ++s)
+        a.Sb[s] = h->Sb[s];
+    a.g = h->geom;
+    a.m = h->model;
+    a.w = h->wells;
+    return a;
+}
+
+SaturationArgs saturation_args(lbm2p *h, int pf, int pg)
+{
+    SaturationArgs a{};
+    for (int i = 0; i < 8; ++i)
+        a.fin[i] = h->fbuf[pf][i];
+    a.R = h->R;
+    a.Pnew = h->Pio;
+    for (int i = 0; i < 9; ++i) {
+        a.gin[i] = h->gbuf[pg][i];
+        a.gout[i] = h->gbuf[1 - pg][i];
+    }
+    a.K = h->K;
+    a.inv_tau = h->inv_tau;
+    a.Fs = h->Fs;
+    a.S = h->S;
+    for (int s = 0; s < 4; ++s) {
+        a.Pb[s] = h->Pb[s];
+        a.Sb[s] = h->Sb[s];
+    }
+    a.g = h->geom;
+    a.m = h->model;
+    a.w = h->wells;
+    return a;
+}
+
+
+RebaseMidArgs rebase_mid_args(lbm2p *h, int pf)
+{
+    RebaseMidArgs a{};
+    for (int i = 0; i < 8; ++i)
+        a.n[i] = h->fbuf[pf][i];
+    a.R = h->R;
+    a.Fp = h->Fp;
+    a.g = h->geom;
+    a.w = h->wells;
+    return a;
+}
+
+RebaseArgs rebase_args(lbm2p *h, int pf)
+{
+    RebaseArgs a{};
+    for (int i = 0; i < 8; ++i)
+        a.n[i] = h->fbuf[pf][i];
+    a.R = h->R;
+    a.Pnew = h->Pio;
+    a.g = h->geom;
+    return a;
+}
+
+}  // namespace lbm2p_internal
 
 namespace {
+
+using lbm2p_internal::pressure_args;
+using lbm2p_internal::refresh_args;
+using lbm2p_internal::saturation_args;
+using lbm2p_internal::rebase_args;
+using lbm2p_internal::rebase_mid_args;
 
 lbm2p_status fail(lbm2p *h, lbm2p_status st, const char *fmt, ...)
 {
@@ -201,78 +249,31 @@ lbm2p_status upload_trace(lbm2p *h, float *dst, const double *src, int n)
     return LBM2P_OK;
 }
 
-// ---- kernel argument blocks for the current ping-pong state -----------------------------
-PressureArgs pressure_args(lbm2p *h, int src)
+// ---- single pressure sweeps with the kernel chosen at create ---------------------------
+void launch_sweep(lbm2p *h, const PressureArgs &a, bool check, bool write_p)
 {
-    PressureArgs a{};
-    for (int i = 0; i < 8; ++i) {
-        a.fin[i] = h->fbuf[src][i];
-        a.fout[i] = h->fbuf[1 - src][i];
-    }
-    a.R = h->R;
-    a.inv_tau = h->inv_tau;
-    a.Fp = h->Fp;
-    a.Pio = h->Pio;
-    a.partials = h->partials;
-    a.shift = h->shift;
-    for (int s = 0; s < 4; ++s)
-        a.Pb[s] = h->Pb[s];
-    a.g = h->geom;
-    a.w = h->wells;
-    return a;
+    if (h->sweep_kind == 2)
+        lbm2p_launch::pressure_sweep_rows(a, check, write_p, h->rows_bt, h->rows_npt, h->rows_H,
+                                          h->rows_grid, h->stream);
+    else
+        lbm2p_launch::pressure_sweep(a, check, write_p, check ? h->grid_check : h->grid, h->stream,
+                                     h->sweep_kind);
 }
 
-RefreshArgs refresh_args(lbm2p *h, int pg)
+cudaError_t add_sweep_node(lbm2p *h, cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
+                           const PressureArgs &a, bool check, bool write_p)
 {
-    RefreshArgs a{};
-    for (int i = 0; i < 9; ++i)
-        a.gin[i] = h->gbuf[pg][i];
-    a.K = h->K;
-    a.Fs = h->Fs;
-    a.inv_tau = h->inv_tau;
-    for (int s = 0; s < 4; ++s)
-        a.Sb[s] = h->Sb[s];
-    a.g = h->geom;
-    a.m = h->model;
-    a.w = h->wells;
-    return a;
+    if (h->sweep_kind == 2)
+        return lbm2p_launch::node_pressure_rows(n, g, dep, a, check, write_p, h->rows_bt,
+                                                h->rows_npt, h->rows_H, h->rows_grid);
+    return lbm2p_launch::node_pressure(n, g, dep, a, check, write_p,
+                                       check ? h->grid_check : h->grid, h->sweep_kind);
 }
 
-SaturationArgs saturation_args(lbm2p *h, int pf, int pg)
+// residual partials written by one checking single sweep
+int sweep_nparts(const lbm2p *h)
 {
-    SaturationArgs a{};
-    for (int i = 0; i < 8; ++i)
-        a.fin[i] = h->fbuf[pf][i];
-    a.R = h->R;
-    a.Pnew = h->Pio;
-    for (int i = 0; i < 9; ++i) {
-        a.gin[i] = h->gbuf[pg][i];
-        a.gout[i] = h->gbuf[1 - pg][i];
-    }
-    a.K = h->K;
-    a.inv_tau = h->inv_tau;
-    a.Fs = h->Fs;
-    a.S = h->S;
-    for (int s = 0; s < 4; ++s) {
-        a.Pb[s] = h->Pb[s];
-        a.Sb[s] = h->Sb[s];
-    }
-    a.g = h->geom;
-    a.m = h->model;
-    a.w = h->wells;
-    return a;
-}
-
-
-RebaseArgs rebase_args(lbm2p *h, int pf)
-{
-    RebaseArgs a{};
-    for (int i = 0; i < 8; ++i)
-        a.n[i] = h->fbuf[pf][i];
-    a.R = h->R;
-    a.Pnew = h->Pio;
-    a.g = h->geom;
-    return a;
+    return h->sweep_kind == 2 ? h->rows_grid : h->grid_check;
 }
 
 // ---- graph-resident sub-iteration ----------------------------------------------------------
@@ -297,7 +298,7 @@ lbm2p_status add_loop(lbm2p *h, cudaGraph_t G, const cudaGraphNode_t *dep, int p
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     cudaGraphNode_t prev = nullptr;
     int src = pf;
-    int nparts = h->grid_check;
+    int nparts = sweep_nparts(h);
     if (h->tb_T_graph > 1) {
         const int T = h->tb_T_graph;
         for (int kk = T; kk <= m; kk += T) {
@@ -313,16 +314,26 @@ lbm2p_status add_loop(lbm2p *h, cudaGraph_t G, const cudaGraphNode_t *dep, int p
         for (int kk = 1; kk <= m; ++kk) {
             cudaGraphNode_t n;
             PressureArgs a = pressure_args(h, src);
-            CUDA_TRY(h, lbm2p_launch::node_pressure(&n, body, prev ? &prev : nullptr, a, kk == m,
-                                                    kk == m - 1, kk == m ? h->grid_check : h->grid,
-                                                    h->sweep_kind));
+            CUDA_TRY(h, add_sweep_node(h, &n, body, prev ? &prev : nullptr, a, kk == m,
+                                       kk == m - 1));
             prev = n;
             src = 1 - src;
         }
     }
-    cudaGraphNode_t fin;
+    // finalize decides whether to continue, and whether R moves to the current P first
+    cudaGraphNode_t fin, ifn, rb;
+    cudaGraphConditionalHandle hr;
+    CUDA_TRY(h, cudaGraphConditionalHandleCreate(&hr, body, 0, 0));
     CUDA_TRY(h, lbm2p_launch::node_finalize_loop(&fin, body, &prev, h->partials, nparts,
-                                                 h->nnodes, h->shift, h->res, h->ctl, hd));
+                                                 h->nnodes, h->shift, h->res, h->ctl, hd, hr));
+    cudaGraphNodeParams ip{};
+    ip.type = cudaGraphNodeTypeConditional;
+    ip.conditional.handle = hr;
+    ip.conditional.type = cudaGraphCondTypeIf;
+    ip.conditional.size = 1;
+    CUDA_TRY(h, cudaGraphAddNode(&ifn, body, &fin, nullptr, 1, &ip));
+    CUDA_TRY(h, lbm2p_launch::node_rebase_mid(&rb, ip.conditional.phGraph_out[0], nullptr,
+                                              rebase_mid_args(h, pf), h->grid));
     CUDA_TRY(h, cudaGraphAddEventRecordNode(&ev1, G, &wn, 1, h->ev_sw1));
     *last = ev1;
     return LBM2P_OK;
@@ -377,7 +388,9 @@ lbm2p_status read_loop(lbm2p *h, int *k, double *r, float *sweep_ms)
     const int m = h->p.check_every;
     const int per_launch = h->tb_T_graph > 1 ? h->tb_T_graph : 1;
     h->sweeps += *k;
-    h->launches += 1 + *k / per_launch + *k / m;   // reset, sweep launches, finalizes
+    // reset, sweep launches, finalizes, mid-solve rebases
+    h->launches += 1 + *k / per_launch + *k / m +
+                   (h->rebase_every > 0 && *k > 0 ? (*k - 1) / h->rebase_every : 0);
     if (sweep_ms) {
         *sweep_ms = -1.0f;
         if (h->timing)
@@ -413,7 +426,7 @@ lbm2p_status pressure_solve(lbm2p *h, int replay, int *k_out, double *r_out, flo
         return (kk % m == 0) || kk >= cap;
     };
     // run sweeps k+1 .. upto; the last one evaluates the residual when asked
-    int last_nparts = h->grid_check;
+    int last_nparts = sweep_nparts(h);
     // run sweeps k+1 .. upto; the last one evaluates the residual when it is a check point.
     // With fused sweeps the batch is a few single sweeps followed by fused launches, the
     // last of which computes the residual from its final two stages.
@@ -430,8 +443,7 @@ lbm2p_status pressure_solve(lbm2p *h, int replay, int *k_out, double *r_out, flo
             const bool check = nf == 0 && is_check(kk) && kk >= 2;
             const bool write_p = nf == 0 && is_check(kk + 1) && kk + 1 >= 2;
             PressureArgs a = pressure_args(h, h->cur_f);
-            lbm2p_launch::pressure_sweep(a, check, write_p, check ? h->grid_check : h->grid,
-                                         h->stream, h->sweep_kind);
+            launch_sweep(h, a, check, write_p);
             LAUNCHED(h, "pressure sweep");
             h->cur_f = 1 - h->cur_f;
             h->sweeps += 1;
@@ -444,7 +456,7 @@ lbm2p_status pressure_solve(lbm2p *h, int replay, int *k_out, double *r_out, flo
             h->cur_f = 1 - h->cur_f;
             h->sweeps += T;
         }
-        last_nparts = nf > 0 ? h->tb_grid : h->grid_check;
+        last_nparts = nf > 0 ? h->tb_grid : sweep_nparts(h);
         if (h->timing)
             CUDA_TRY(h, cudaEventRecord(h->ev_sw1, st));
         k = upto;
@@ -486,12 +498,27 @@ lbm2p_status pressure_solve(lbm2p *h, int replay, int *k_out, double *r_out, flo
             *ms_out = ms;
         return loop_status(h, k, r);
     }
+    // R moves to the current P after sweep k when k is a multiple of rebase_every and the
+    // solve goes on (the graph loop applies the same rule)
+    const int every = h->rebase_every;
+    auto rebase_mid = [&]() -> lbm2p_status {
+        lbm2p_launch::rebase_mid(rebase_mid_args(h, h->cur_f), h->grid, h->stream);
+        LAUNCHED(h, "mid-solve rebase");
+        return LBM2P_OK;
+    };
     if (replay >= 0) {
         if (replay > 0) {
-            if ((e = run_batch(replay)) != LBM2P_OK)
-                return e;
-            if ((e = add_time()) != LBM2P_OK)
-                return e;
+            while (k < replay) {
+                int next = replay;
+                if (every > 0 && (k / every + 1) * every < replay)
+                    next = (k / every + 1) * every;
+                if ((e = run_batch(next)) != LBM2P_OK)
+                    return e;
+                if ((e = add_time()) != LBM2P_OK)
+                    return e;
+                if (k < replay && every > 0 && k % every == 0 && (e = rebase_mid()) != LBM2P_OK)
+                    return e;
+            }
             if (replay >= 2) {
                 if ((e = read_residual()) != LBM2P_OK)
                     return e;
@@ -524,6 +551,8 @@ lbm2p_status pressure_solve(lbm2p *h, int replay, int *k_out, double *r_out, flo
                 status = LBM2P_ENOTCONVERGED;
                 break;
             }
+            if (every > 0 && k % every == 0 && (e = rebase_mid()) != LBM2P_OK)
+                return e;
         }
     }
     if (k_out)
@@ -658,6 +687,8 @@ lbm2p_status check_params(const lbm2p_params *p, const lbm2p_inputs *in)
         return fail(nullptr, LBM2P_EINVAL, "Dirichlet y-sides need ny >= 3");
     if (p->fuse_sweeps != 0 && p->fuse_sweeps != 1 && p->fuse_sweeps != 2 && p->fuse_sweeps != 4)
         return fail(nullptr, LBM2P_EINVAL, "fuse_sweeps must be 0, 1, 2 or 4");
+    if (p->sweep_kernel < LBM2P_SWEEP_AUTO || p->sweep_kernel > LBM2P_SWEEP_ROWS)
+        return fail(nullptr, LBM2P_EINVAL, "sweep_kernel must be an lbm2p_sweep_kernel value");
     if (p->storage == LBM2P_STORE_FP16_DEV)
         return fail(nullptr, LBM2P_ENOTIMPL, "FP16 deviation storage is not available");
     if (p->storage != LBM2P_STORE_FP32)
@@ -683,49 +714,127 @@ lbm2p_status check_params(const lbm2p_params *p, const lbm2p_inputs *in)
     return LBM2P_OK;
 }
 
-// Pick how the pressure sweeps run on this lattice by timing every candidate: one sweep
-// per launch, and (when allowed) T = 2 and 4 fused sweeps over each tile shape (W columns,
-// H rows).  Runs on the zeroed buffers before initialisation; they are zeroed again after.
+// Pick how the pressure sweeps run on this lattice by timing every candidate: the single-
+// sweep kernels (the staged-rows one over strip widths and rows per block), and (when
+// allowed) T = 2 and 4 fused sweeps over each tile shape (W columns, H rows).  A requested
+// single-sweep kernel is the only one timed; requested fused sweeps win over single ones.
+// Each candidate runs once untimed, then the best of two timed groups of reps launches
+// counts.  Runs on the zeroed buffers before initialisation; they are zeroed again after.
 lbm2p_status autotune_sweeps(lbm2p *h)
 {
     cudaStream_t st = (cudaStream_t)h->stream;
     for (auto &a : h->allocs)
         CUDA_TRY(h, cudaMemsetAsync(a.ptr, 0, a.bytes, st));
+    int dev = 0, sms = 0;
+    CUDA_TRY(h, cudaGetDevice(&dev));
+    CUDA_TRY(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     cudaEvent_t e0, e1;
     CUDA_TRY(h, cudaEventCreate(&e0));
     CUDA_TRY(h, cudaEventCreate(&e1));
     lbm2p_status status = LBM2P_OK;
-    auto timed = [&](auto launch, int reps, float *ms) -> bool {
+    const int reps = 6;
+    // per-launch time of a candidate: best of two groups of reps launches after one warm-up
+    auto timed = [&](auto launch, float *ms) -> bool {
         launch(0);
-        cudaEventRecord(e0, st);
-        for (int rep = 0; rep < reps; ++rep)
-            launch(rep + 1);
-        cudaEventRecord(e1, st);
-        cudaError_t le = cudaEventSynchronize(e1);
-        if (le != cudaSuccess) {
-            status = fail(h, LBM2P_ECUDA, "sweep timing failed: %s", cudaGetErrorString(le));
-            return false;
+        float best_ms = 1e30f;
+        for (int trial = 0; trial < 2; ++trial) {
+            cudaEventRecord(e0, st);
+            for (int rep = 0; rep < reps; ++rep)
+                launch(rep + 1);
+            cudaEventRecord(e1, st);
+            cudaError_t le = cudaEventSynchronize(e1);
+            if (le != cudaSuccess) {
+                status = fail(h, LBM2P_ECUDA, "sweep timing failed: %s", cudaGetErrorString(le));
+                return false;
+            }
+            float t = 0.0f;
+            cudaEventElapsedTime(&t, e0, e1);
+            best_ms = t < best_ms ? t : best_ms;
         }
-        cudaEventElapsedTime(ms, e0, e1);
+        *ms = best_ms / reps;
         return true;
     };
-    const int reps = 4;
-    float best = 1e30f;   // per-sweep time
+    const int forced = h->p.sweep_kernel;                  // 0: any single-sweep kernel
+    auto allowed = [&](int kind) { return forced == LBM2P_SWEEP_AUTO || forced == kind + 1; };
+    const bool fused_only = h->p.fuse_sweeps == 2 || h->p.fuse_sweeps == 4;
+    float best = 1e30f;                                    // per-sweep time of the choice
     h->tb_T = 0;
-    if (h->p.fuse_sweeps != 2 && h->p.fuse_sweeps != 4) {
+    h->sweep_kind = forced == LBM2P_SWEEP_AUTO ? 0 : forced - 1;
+    if (!fused_only || forced != LBM2P_SWEEP_AUTO) {
         for (int kind = 0; kind < 2; ++kind) {
+            if (!allowed(kind))
+                continue;
             float ms = 0.0f;
             if (!timed([&](int k) {
                     PressureArgs a = pressure_args(h, k % 2);
                     lbm2p_launch::pressure_sweep(a, false, false, h->grid_k[kind], h->stream, kind);
-                }, reps, &ms))
+                }, &ms))
                 goto done;
-            if (ms / reps < best) {
-                best = ms / reps;
+            if (ms < best) {
+                best = ms;
                 h->sweep_kind = kind;
             }
         }
+        // the staged-rows kernel: strip width, and rows per block giving 1, 2 or 4 blocks
+        // per resident block slot
+        const int shapes[3][2] = {{256, 1}, {128, 1}, {256, 2}};
+        float best_rows = 1e30f;
+        int rows_shape[4] = {0, 0, 0, 0};                  // bt, npt, H, grid
+        for (const auto &sh : shapes) {
+            if (!allowed(2))
+                break;
+            const int bt = sh[0], npt = sh[1];
+            if (lbm2p_launch::rows_prepare(bt, npt) != cudaSuccess) {
+                cudaGetLastError();
+                continue;
+            }
+            const int per_sm = lbm2p_launch::rows_blocks_per_sm(bt, npt);
+            if (per_sm < 1)
+                continue;
+            const int strips = (h->nx + bt * npt - 1) / (bt * npt);
+            int last_H = -1;
+            for (int mult : {1, 2, 4}) {
+                const long long want = (long long)sms * per_sm * mult;
+                long long chunks = (want + strips - 1) / strips;
+                chunks = chunks < 1 ? 1 : chunks;
+                const int H = (int)((h->ny + chunks - 1) / chunks);
+                if (H == last_H)
+                    continue;
+                last_H = H;
+                const int grid = (int)lbm2p_launch::rows_grid(bt, npt, H, h->nx, h->ny);
+                float ms = 0.0f;
+                if (!timed([&](int k) {
+                        PressureArgs a = pressure_args(h, k % 2);
+                        lbm2p_launch::pressure_sweep_rows(a, false, false, bt, npt, H, grid,
+                                                          h->stream);
+                    }, &ms))
+                    goto done;
+                if (ms < best_rows) {
+                    best_rows = ms;
+                    rows_shape[0] = bt;
+                    rows_shape[1] = npt;
+                    rows_shape[2] = H;
+                    rows_shape[3] = grid;
+                }
+            }
+        }
+        if (rows_shape[0] > 0 && (best_rows < best || forced == LBM2P_SWEEP_ROWS)) {
+            best = best_rows;
+            h->sweep_kind = 2;
+        }
+        if (rows_shape[0] > 0) {
+            h->rows_bt = rows_shape[0];
+            h->rows_npt = rows_shape[1];
+            h->rows_H = rows_shape[2];
+            h->rows_grid = rows_shape[3];
+        }
+        if (forced == LBM2P_SWEEP_ROWS && rows_shape[0] == 0) {
+            status = fail(h, LBM2P_ENOTIMPL, "the staged-rows sweep kernel cannot run here");
+            goto done;
+        }
     }
+    if (fused_only)
+        best = 1e30f;
     if (h->p.fuse_sweeps != 1) {
         for (int T : {2, 4}) {
             if (h->p.fuse_sweeps != 0 && h->p.fuse_sweeps != T)
@@ -745,10 +854,10 @@ lbm2p_status autotune_sweeps(lbm2p *h)
                             PressureArgs a = pressure_args(h, k % 2);
                             lbm2p_launch::pressure_sweeps_fused(a, T, W, H, false, (int)blocks,
                                                                 h->stream);
-                        }, reps, &ms))
+                        }, &ms))
                         goto done;
-                    if (ms / (reps * T) < best) {
-                        best = ms / (reps * T);
+                    if (ms / T < best) {
+                        best = ms / T;
                         h->tb_T = T;
                         h->tb_W = W;
                         h->tb_H = H;
@@ -888,10 +997,12 @@ lbm2p_status build(lbm2p *h, const lbm2p_inputs *in, lbm2p_step_stats *init_stat
         if (e != LBM2P_OK)
             return e;
     }
-    h->grid = h->grid_k[h->sweep_kind];
-    h->grid_check = h->grid_check_k[h->sweep_kind];
+    // grid-stride lattice kernels keep the one-node-per-thread capacity when the staged
+    // sweep is chosen
+    h->grid = h->grid_k[h->sweep_kind < 2 ? h->sweep_kind : 1];
+    h->grid_check = h->grid_check_k[h->sweep_kind < 2 ? h->sweep_kind : 1];
     {
-        int np = h->tb_grid;
+        int np = h->tb_grid > h->rows_grid ? h->tb_grid : h->rows_grid;
         for (int kind = 0; kind < 2; ++kind) {
             np = np > h->grid_k[kind] ? np : h->grid_k[kind];
             np = np > h->grid_check_k[kind] ? np : h->grid_check_k[kind];
@@ -914,6 +1025,8 @@ lbm2p_status build(lbm2p *h, const lbm2p_inputs *in, lbm2p_step_stats *init_stat
     cudaStream_t st = (cudaStream_t)h->stream;
     for (auto &a : h->allocs)
         CUDA_TRY(h, cudaMemsetAsync(a.ptr, 0, a.bytes, st));
+    // a long solve moves R to the current P about every 1024 sweeps (at a check point)
+    h->rebase_every = p.check_every * ((1024 + p.check_every - 1) / p.check_every);
     // the loop body holds check_every sweeps and must return to the same f buffer
     h->graph_ok = p.check_every >= 2 && p.check_every % 2 == 0 &&
                   p.max_sub_iters % p.check_every == 0;
@@ -925,6 +1038,7 @@ lbm2p_status build(lbm2p *h, const lbm2p_inputs *in, lbm2p_step_stats *init_stat
         LoopCtl c{};
         c.m = p.check_every;
         c.cap = p.max_sub_iters;
+        c.every = h->rebase_every;
         c.tol = p.tol;
         c.r = 0.0;
         *h->ctl_host = c;
@@ -1039,6 +1153,7 @@ void lbm2p_default_params(lbm2p_params *p)
     p->max_sub_iters = 10000000;
     p->check_every = 8;
     p->fuse_sweeps = 0;
+    p->sweep_kernel = LBM2P_SWEEP_AUTO;
     for (int s = 0; s < 4; ++s)
         p->bc[s] = LBM2P_BC_NOFLUX;
     p->storage = LBM2P_STORE_FP32;
@@ -1263,11 +1378,11 @@ lbm2p_status lbm2p_sweep_config(const lbm2p *h, int *fused, int *kind, int *tile
     if (fused)
         *fused = h->tb_T > 1 ? h->tb_T : 1;
     if (kind)
-        *kind = h->sweep_kind;
+        *kind = h->sweep_kind + 1;        // internal 0, 1, 2 = VEC4, SCALAR, ROWS
     if (tile_w)
-        *tile_w = h->tb_T > 1 ? h->tb_W : 0;
+        *tile_w = h->tb_T > 1 ? h->tb_W : (h->sweep_kind == 2 ? h->rows_bt * h->rows_npt : 0);
     if (tile_h)
-        *tile_h = h->tb_T > 1 ? h->tb_H : 0;
+        *tile_h = h->tb_T > 1 ? h->tb_H : (h->sweep_kind == 2 ? h->rows_H : 0);
     return LBM2P_OK;
 }
 

@@ -1,6 +1,7 @@
 """Pressure sweeps fused in time (several sweeps per kernel launch) against one sweep per
-launch: identical populations bit for bit, on every wall kind and on ragged and tiny
-lattices, and the same residual up to the grouping of its partial sums."""
+launch, and the single-sweep kernels against each other: identical populations bit for bit,
+on every wall kind and on ragged and tiny lattices, and the same residual up to the grouping
+of its partial sums."""
 import numpy as np
 import pytest
 
@@ -47,7 +48,7 @@ def test_fused_equals_single_sweeps(kind, T):
     prob = _problem(kind)
     single = pkg.Solver.from_problem(prob, init_replay=0, fuse_sweeps=1)
     fused = pkg.Solver.from_problem(prob, init_replay=0, fuse_sweeps=T)
-    assert single.sweep_config()[0] == 1 and single.sweep_config()[1] in (0, 1)
+    assert single.sweep_config()[0] == 1 and single.sweep_config()[1] in (1, 2, 3)
     cfg = fused.sweep_config()
     assert cfg[0] == T and cfg[2] in (32, 64, 128) and cfg[3] in (8, 16, 32, 64)
     rng = np.random.default_rng(3)
@@ -71,3 +72,62 @@ def test_fused_equals_single_sweeps(kind, T):
     assert np.array_equal(single.get_state(), fused.get_state())
     single.close()
     fused.close()
+
+
+@pytest.mark.parametrize("kind", ["five_spot_ragged", "wide_ragged", "periodic", "dirichlet",
+                                  "mixed", "tiny", "column", "tall"])
+def test_single_sweep_kernels_agree(kind):
+    """VEC4, SCALAR and ROWS (strips staged in shared memory) give the same populations."""
+    import paper_1808_07554_gb300 as pkg
+    prob = _problem(kind)
+    solvers = [pkg.Solver.from_problem(prob, init_replay=0, fuse_sweeps=1, sweep_kernel=k)
+               for k in (pkg.SWEEP_VEC4, pkg.SWEEP_SCALAR, pkg.SWEEP_ROWS)]
+    for k, s in zip((pkg.SWEEP_VEC4, pkg.SWEEP_SCALAR, pkg.SWEEP_ROWS), solvers):
+        cfg = s.sweep_config()
+        assert cfg[0] == 1 and cfg[1] == k
+        if k == pkg.SWEEP_ROWS:
+            assert cfg[2] in (128, 256, 512) and 1 <= cfg[3] <= prob.ny
+    rng = np.random.default_rng(5)
+    state = solvers[0].get_state()
+    state[:8] = 0.01 * rng.standard_normal(state[:8].shape)
+    state[17] = 1.0 / (0.55 + 2.0 * rng.random(state[17].shape))
+    state[19] = rng.standard_normal(state[19].shape)
+    for s in solvers:
+        s.set_state(state)
+    for n in (1, 2, 7, 8):
+        rs = [s.pressure_sweeps(n) for s in solvers]
+        ref = solvers[0].get_state()
+        for s, r in zip(solvers[1:], rs[1:]):
+            b = s.get_state()
+            assert np.array_equal(ref, b), (kind, n, float(np.max(np.abs(ref - b))))
+            if n >= 2:
+                assert r == pytest.approx(rs[0], rel=1e-3, abs=1e-30)
+    steps = [s.step(2, replay=[16, 8]) for s in solvers]
+    ref = solvers[0].get_state()
+    for s in solvers[1:]:
+        assert np.array_equal(ref, s.get_state())
+    for s in solvers:
+        s.close()
+
+
+def test_rows_kernel_free_running_graph_loop():
+    """The staged-rows kernel inside the graph-resident loop: a free-running step agrees with
+    the scalar kernel's (the same populations when the sweep counts agree; the counts may
+    differ by one loop body when a residual sits on the tolerance)."""
+    import paper_1808_07554_gb300 as pkg
+    prob = W.quarter_five_spot(300, 140, seed=9, corr_len=8.0)
+    a = pkg.Solver.from_problem(prob, init_replay=400, sweep_kernel=pkg.SWEEP_SCALAR,
+                                fuse_sweeps=1)
+    b = pkg.Solver.from_problem(prob, init_replay=400, sweep_kernel=pkg.SWEEP_ROWS,
+                                fuse_sweeps=1)
+    assert np.array_equal(a.get_state(), b.get_state())
+    for _ in range(3):
+        sa, ta = a.step(1)
+        sb, tb = b.step(1)
+        assert sa == pkg.OK and sb == pkg.OK
+        ka, kb = ta[0].sub_iters, tb[0].sub_iters
+        assert abs(ka - kb) <= 8
+        if ka == kb:
+            assert np.array_equal(a.get_state(), b.get_state())
+        else:
+            b.set_state(a.get_state())
