@@ -213,6 +213,13 @@ lbm2p_status lbm2p_set_timing(lbm2p *h, int enable);
    block, for the ROWS kernel its strip width and rows per block, otherwise 0 and 0. */
 lbm2p_status lbm2p_sweep_config(const lbm2p *h, int *fused, int *kind, int *tile_w, int *tile_h);
 
+/* The candidates create timed to choose the sweep kernel, one line each:
+ *   "single_vec4 <grid> 0 0 0 <us>", "single_scalar <grid> 0 0 0 <us>",
+ *   "single_rows <strip width> <ring slots> <rows per block> <grid> <us>",
+ *   "fused <sweeps per launch> <threads per block> <rows per block> <grid> <us>"
+ * with <us> the time per sweep.  Owned by h; valid until the next create-time tuning. */
+const char *lbm2p_autotune_report(const lbm2p *h);
+
 /* Running totals since creation: kernels launched by the library, pressure sweeps run. */
 lbm2p_status lbm2p_counters(const lbm2p *h, long long *launches, long long *sweeps);
 

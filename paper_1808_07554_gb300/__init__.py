@@ -104,6 +104,7 @@ def load_library(path: str = LIB_PATH):
         "lbm2p_set_timing": (C.c_int, [H, C.c_int]),
         "lbm2p_counters": (C.c_int, [H, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
         "lbm2p_sweep_config": (C.c_int, [H] + [C.POINTER(C.c_int)] * 4),
+        "lbm2p_autotune_report": (C.c_char_p, [H]),
         "lbm2p_pressure_sweep_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int),
                                                    C.POINTER(fp), C.POINTER(fp), fp, fp, fp,
                                                    C.POINTER(fp), fp, C.POINTER(C.c_double),
@@ -235,6 +236,11 @@ def lbm2p_sweep_config(h):
     v = [C.c_int(0) for _ in range(4)]
     _check(_lib_or_raise().lbm2p_sweep_config(h, *[C.byref(x) for x in v]), h)
     return tuple(x.value for x in v)
+
+
+def lbm2p_autotune_report(h) -> str:
+    s = _lib_or_raise().lbm2p_autotune_report(h)
+    return s.decode() if s else ""
 
 
 def lbm2p_destroy(h):
@@ -457,6 +463,14 @@ class Solver:
 
     def sweep_config(self):
         return lbm2p_sweep_config(self.h)
+
+    def autotune_report(self):
+        """[(candidate, a1, a2, a3, a4, us per sweep)] as timed at create."""
+        out = []
+        for ln in lbm2p_autotune_report(self.h).splitlines():
+            f = ln.split()
+            out.append((f[0], *[int(v) for v in f[1:5]], float(f[5])))
+        return out
 
     # -- outputs --------------------------------------------------------------------------
     def fields(self, mean_free_P=False):

@@ -92,27 +92,26 @@ __global__ void kb_reset(MemberCtl *ctl, const int *__restrict__ caps,
     }
 }
 
-// sweep number idx (0-based) of a loop body, for every active member
+// Sweep number idx (0-based) of a loop body over the tiles of the still-active members:
+// act[0 .. counts[2]) lists (member, tile of the member), rebuilt after every body.
 template <bool CHECK, bool WRITE_P>
 __global__ void __launch_bounds__(kBlock) kb_sweep(const Member *__restrict__ mem,
-                                                   const int *__restrict__ tile_member,
-                                                   int total, int idx,
-                                                   const MemberCtl *__restrict__ ctl,
+                                                   const int2 *__restrict__ act,
+                                                   const int *__restrict__ counts, int idx,
                                                    double *__restrict__ partials)
 {
     __shared__ double red[kBlock / 32][4];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int total = counts[2];
     for (int t = blockIdx.x; t < total; t += gridDim.x) {
-        const int mi = tile_member[t];
-        if (!ctl[mi].active)
-            continue;                                   // uniform over the block
-        const Member &M = mem[mi];
+        const int2 e = act[t];
+        const Member &M = mem[e.x];
         const PressureArgs &a = M.pa[M.pf ^ (idx & 1)];
         float d = 0.0f, q = 0.0f;
         int x, y;
         const float shift = CHECK ? M.shift[0] : 0.0f;
         const float dshift = CHECK ? M.shift[1] : 0.0f;
-        if (tile_node(M, t - M.tile0, x, y))
+        if (tile_node(M, e.y, x, y))
             sweep_node<CHECK, WRITE_P>(a, x, y, y * a.g.pitch + x, shift, dshift, d, q);
         if (CHECK) {
             const float s0 = warp_sum(d), s1 = warp_sum(d * d), s2 = warp_sum(q), s3 = warp_sum(q * q);
@@ -128,7 +127,7 @@ __global__ void __launch_bounds__(kBlock) kb_sweep(const Member *__restrict__ me
 #pragma unroll
                 for (int w = 0; w < kBlock / 32; ++w)
                     s += red[w][threadIdx.x];
-                partials[4 * (size_t)t + threadIdx.x] = s;
+                partials[4 * (size_t)(M.tile0 + e.y) + threadIdx.x] = s;
             }
             __syncthreads();
         }
@@ -193,13 +192,61 @@ __global__ void __launch_bounds__(256) kb_finalize(const Member *__restrict__ me
     }
 }
 
-__global__ void kb_condition(int *counts, cudaGraphConditionalHandle h_loop,
-                             cudaGraphConditionalHandle h_rebase)
+// One block: (SET) continue the loop while a member is active and rebase when one asks;
+// then the exclusive prefix of the active members' tile counts, counts[2] = their total.
+template <bool SET>
+__global__ void __launch_bounds__(256) kb_prefix(const Member *__restrict__ mem,
+                                                 const MemberCtl *__restrict__ ctl, int count,
+                                                 int *__restrict__ prefix, int *counts,
+                                                 cudaGraphConditionalHandle h_loop,
+                                                 cudaGraphConditionalHandle h_rebase)
 {
-    const int active = counts[0], rebase = counts[1];
-    counts[0] = counts[1] = 0;
-    cudaGraphSetConditional(h_loop, active > 0 ? 1u : 0u);
-    cudaGraphSetConditional(h_rebase, rebase > 0 ? 1u : 0u);
+    __shared__ int scan[256];
+    __shared__ int carry;
+    if (threadIdx.x == 0) {
+        if (SET) {
+            const int active = counts[0], rebase = counts[1];
+            counts[0] = counts[1] = 0;
+            cudaGraphSetConditional(h_loop, active > 0 ? 1u : 0u);
+            cudaGraphSetConditional(h_rebase, rebase > 0 ? 1u : 0u);
+        }
+        carry = 0;
+    }
+    __syncthreads();
+    for (int base = 0; base < count; base += 256) {
+        const int m = base + (int)threadIdx.x;
+        const int v = (m < count && ctl[m].active) ? mem[m].ntiles : 0;
+        scan[threadIdx.x] = v;
+        __syncthreads();
+        for (int off = 1; off < 256; off <<= 1) {        // inclusive scan
+            const int add = (int)threadIdx.x >= off ? scan[threadIdx.x - off] : 0;
+            __syncthreads();
+            scan[threadIdx.x] += add;
+            __syncthreads();
+        }
+        if (m < count)
+            prefix[m] = carry + scan[threadIdx.x] - v;
+        __syncthreads();
+        if (threadIdx.x == 255)
+            carry += scan[255];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        counts[2] = carry;
+}
+
+// one block per member: list the tiles of an active member at its prefix offset
+__global__ void __launch_bounds__(256) kb_scatter(const Member *__restrict__ mem,
+                                                  const MemberCtl *__restrict__ ctl,
+                                                  const int *__restrict__ prefix,
+                                                  int2 *__restrict__ act)
+{
+    const int m = blockIdx.x;
+    if (!ctl[m].active)
+        return;
+    const int base = prefix[m], n = mem[m].ntiles;
+    for (int i = threadIdx.x; i < n; i += 256)
+        act[base + i] = make_int2(m, i);
 }
 
 __global__ void __launch_bounds__(kBlock) kb_rebase_mid(const Member *__restrict__ mem,
@@ -255,7 +302,10 @@ struct lbm2p_batch {
     double *d_tols = nullptr;
     int *h_caps = nullptr;               // pinned
     double *h_tols = nullptr;            // pinned
-    int *d_active = nullptr;             // [0] active members, [1] members to rebase
+    int *d_active = nullptr;             // [0] active members, [1] members to rebase,
+                                         // [2] tiles of the active members
+    int *d_prefix = nullptr;             // first compacted tile of each active member
+    int2 *d_act = nullptr;               // compacted (member, tile) list
     double *d_partials = nullptr;
     cudaGraph_t graph[2] = {};
     cudaGraphExec_t exec[2] = {};
@@ -301,6 +351,8 @@ void batch_free(lbm2p_batch *b)
     cudaFree(b->d_caps);
     cudaFree(b->d_tols);
     cudaFree(b->d_active);
+    cudaFree(b->d_prefix);
+    cudaFree(b->d_act);
     cudaFree(b->d_partials);
     if (b->h_ctl)
         cudaFreeHost(b->h_ctl);
@@ -332,7 +384,8 @@ void *sweep_kernel(bool check, bool write_p)
 }
 
 // the graph of one batched step at step parity q (the g buffers swap every step):
-// refresh -> reset -> WHILE{ body sweeps -> finalize -> condition } -> saturation -> rebase
+// refresh -> reset -> prefix -> scatter -> WHILE{ body sweeps -> finalize -> condition +
+// prefix -> scatter -> IF{ mid-solve rebase } } -> saturation -> rebase
 lbm2p_status build_graph(lbm2p_batch *b, int q)
 {
     cudaGraph_t G;
@@ -348,8 +401,13 @@ lbm2p_status build_graph(lbm2p_batch *b, int q)
     int *act = b->d_active;
     double *partials = b->d_partials;
     const double *cpartials = b->d_partials;
+    int *prefix = b->d_prefix;
+    const int *cprefix = b->d_prefix;
+    int2 *actl = b->d_act;
+    const int2 *cactl = b->d_act;
+    const int *cact = b->d_active;
     int body = b->body;
-    cudaGraphNode_t nr, nreset, nw, nsat, nreb;
+    cudaGraphNode_t nr, nreset, npre, nsc, nw, nsat, nreb;
     {
         void *args[] = {(void *)&mem, (void *)&tm, (void *)&total, (void *)&q};
         BTRY(b, add_k(&nr, G, nullptr, (void *)kb_refresh, b->grid, kBlock, args));
@@ -358,27 +416,36 @@ lbm2p_status build_graph(lbm2p_batch *b, int q)
         void *args[] = {(void *)&ctl, (void *)&caps, (void *)&tols, (void *)&count, (void *)&act};
         BTRY(b, add_k(&nreset, G, &nr, (void *)kb_reset, (count + 255) / 256, 256, args));
     }
-    cudaGraphConditionalHandle hd;
+    cudaGraphConditionalHandle hd, hnone{};
     BTRY(b, cudaGraphConditionalHandleCreate(&hd, G, 1, cudaGraphCondAssignDefault));
+    {
+        void *args[] = {(void *)&mem, (void *)&cctl, (void *)&count, (void *)&prefix,
+                        (void *)&act, (void *)&hnone, (void *)&hnone};
+        BTRY(b, add_k(&npre, G, &nreset, (void *)kb_prefix<false>, 1, 256, args));
+    }
+    {
+        void *args[] = {(void *)&mem, (void *)&cctl, (void *)&cprefix, (void *)&actl};
+        BTRY(b, add_k(&nsc, G, &npre, (void *)kb_scatter, count, 256, args));
+    }
     cudaGraphNodeParams cp{};
     cp.type = cudaGraphNodeTypeConditional;
     cp.conditional.handle = hd;
     cp.conditional.type = cudaGraphCondTypeWhile;
     cp.conditional.size = 1;
-    BTRY(b, cudaGraphAddNode(&nw, G, &nreset, nullptr, 1, &cp));
+    BTRY(b, cudaGraphAddNode(&nw, G, &nsc, nullptr, 1, &cp));
     cudaGraph_t bg = cp.conditional.phGraph_out[0];
     cudaGraphNode_t prev = nullptr;
     for (int kk = 0; kk < body; ++kk) {
         const bool check = kk == body - 1, write_p = kk == body - 2;
         int idx = kk;
-        void *args[] = {(void *)&mem, (void *)&tm, (void *)&total, (void *)&idx, (void *)&cctl,
+        void *args[] = {(void *)&mem, (void *)&cactl, (void *)&cact, (void *)&idx,
                         (void *)&partials};
         cudaGraphNode_t n;
         BTRY(b, add_k(&n, bg, prev ? &prev : nullptr, sweep_kernel(check, write_p),
                       check ? b->grid_check : b->grid, kBlock, args));
         prev = n;
     }
-    cudaGraphNode_t nf, nc, nif, nrm;
+    cudaGraphNode_t nf, nc, nsc2, nif, nrm;
     {
         void *args[] = {(void *)&mem, (void *)&cpartials, (void *)&ctl, (void *)&body, (void *)&act};
         BTRY(b, add_k(&nf, bg, &prev, (void *)kb_finalize, count, 256, args));
@@ -386,15 +453,20 @@ lbm2p_status build_graph(lbm2p_batch *b, int q)
     cudaGraphConditionalHandle hr;
     BTRY(b, cudaGraphConditionalHandleCreate(&hr, bg, 0, 0));
     {
-        void *args[] = {(void *)&act, (void *)&hd, (void *)&hr};
-        BTRY(b, add_k(&nc, bg, &nf, (void *)kb_condition, 1, 1, args));
+        void *args[] = {(void *)&mem, (void *)&cctl, (void *)&count, (void *)&prefix,
+                        (void *)&act, (void *)&hd, (void *)&hr};
+        BTRY(b, add_k(&nc, bg, &nf, (void *)kb_prefix<true>, 1, 256, args));
+    }
+    {
+        void *args[] = {(void *)&mem, (void *)&cctl, (void *)&cprefix, (void *)&actl};
+        BTRY(b, add_k(&nsc2, bg, &nc, (void *)kb_scatter, count, 256, args));
     }
     cudaGraphNodeParams ip{};
     ip.type = cudaGraphNodeTypeConditional;
     ip.conditional.handle = hr;
     ip.conditional.type = cudaGraphCondTypeIf;
     ip.conditional.size = 1;
-    BTRY(b, cudaGraphAddNode(&nif, bg, &nc, nullptr, 1, &ip));
+    BTRY(b, cudaGraphAddNode(&nif, bg, &nsc2, nullptr, 1, &ip));
     {
         void *args[] = {(void *)&mem, (void *)&tm, (void *)&total, (void *)&cctl};
         BTRY(b, add_k(&nrm, ip.conditional.phGraph_out[0], nullptr, (void *)kb_rebase_mid,
@@ -511,7 +583,9 @@ lbm2p_status lbm2p_batch_create(lbm2p_batch **out, lbm2p *const *members, int co
             ok(cudaMalloc(&b->d_ctl, sizeof(MemberCtl) * (size_t)count), "cudaMalloc") &&
             ok(cudaMalloc(&b->d_caps, sizeof(int) * (size_t)count), "cudaMalloc") &&
             ok(cudaMalloc(&b->d_tols, sizeof(double) * (size_t)count), "cudaMalloc") &&
-            ok(cudaMalloc(&b->d_active, 2 * sizeof(int)), "cudaMalloc") &&
+            ok(cudaMalloc(&b->d_active, 4 * sizeof(int)), "cudaMalloc") &&
+            ok(cudaMalloc(&b->d_prefix, sizeof(int) * (size_t)count), "cudaMalloc") &&
+            ok(cudaMalloc(&b->d_act, sizeof(int2) * (size_t)total), "cudaMalloc") &&
             ok(cudaMalloc(&b->d_partials, sizeof(double) * 4 * (size_t)total), "cudaMalloc") &&
             ok(cudaMallocHost(&b->h_ctl, sizeof(MemberCtl) * (size_t)count), "cudaMallocHost") &&
             ok(cudaMallocHost(&b->h_caps, sizeof(int) * (size_t)count), "cudaMallocHost") &&
@@ -526,7 +600,7 @@ lbm2p_status lbm2p_batch_create(lbm2p_batch **out, lbm2p *const *members, int co
             ok(cudaMemcpyAsync(b->d_tile_member, tile_member.data(), sizeof(int) * (size_t)total,
                                cudaMemcpyHostToDevice, cs), "cudaMemcpyAsync") &&
             ok(cudaMemsetAsync(b->d_ctl, 0, sizeof(MemberCtl) * (size_t)count, cs), "cudaMemsetAsync") &&
-            ok(cudaMemsetAsync(b->d_active, 0, 2 * sizeof(int), cs), "cudaMemsetAsync") &&
+            ok(cudaMemsetAsync(b->d_active, 0, 4 * sizeof(int), cs), "cudaMemsetAsync") &&
             ok(cudaStreamSynchronize(cs), "cudaStreamSynchronize");
     }
     for (int q = 0; q < 2 && st == LBM2P_OK; ++q)
@@ -608,11 +682,11 @@ lbm2p_status lbm2p_batch_step(lbm2p_batch *b, int nsteps, const int *replay,
                 o.step_ms = ms;
             }
         }
-        // refresh, reset, saturation, rebase; per loop pass: body sweeps, finalize, condition;
-        // and the mid-solve rebases of the longest solve
+        // refresh, reset, prefix, scatter, saturation, rebase; per loop pass: body sweeps,
+        // finalize, condition + prefix, scatter; and the mid-solve rebases of the longest solve
         const int passes = kmax > 0 ? kmax / b->body : 1;
         const int every = b->body * ((1024 + b->body - 1) / b->body);
-        b->launches += 4 + (long long)passes * (b->body + 2) + (kmax > 0 ? (kmax - 1) / every : 0);
+        b->launches += 6 + (long long)passes * (b->body + 3) + (kmax > 0 ? (kmax - 1) / every : 0);
         if (worst == LBM2P_ENONFINITE)
             return bfail(b, worst, "a member's pressure residual is not finite (step %d)", s);
     }

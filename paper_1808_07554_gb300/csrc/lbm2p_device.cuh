@@ -210,18 +210,20 @@ cudaError_t tb_prepare(int T, int W);
 int tb_blocks_per_sm(int T, int W);
 void pressure_sweeps_fused(const PressureArgs &a, int T, int W, int H, bool check, int grid,
                            void *stream);
-// staged-rows single sweep (sweep_rows.cu): bt threads per block (128 or 256), npt nodes
-// per thread (1, or 2 with bt = 256), strips of bt * npt columns, H rows per block
-bool rows_shape_ok(int bt, int npt);
-size_t rows_smem_bytes(int bt, int npt);
-long long rows_grid(int bt, int npt, int H, int nx, int ny);
-cudaError_t rows_prepare(int bt, int npt);
-int rows_blocks_per_sm(int bt, int npt);
-void pressure_sweep_rows(const PressureArgs &a, bool check, bool write_p, int bt, int npt, int H,
-                         int grid, void *stream);
+// staged-rows single sweep (sweep_rows.cu): strips of `width` columns (128 or 256; one
+// consumer warp per 32 columns plus a producer warp), `slots` ring slots (8; or 6 with width
+// 256), H rows per block
+bool rows_shape_ok(int width, int slots);
+int rows_threads(int width);
+size_t rows_smem_bytes(int width, int slots, bool has_fp);
+long long rows_grid(int width, int H, int nx, int ny);
+cudaError_t rows_prepare(int width, int slots);
+int rows_blocks_per_sm(int width, int slots, bool has_fp);
+void pressure_sweep_rows(const PressureArgs &a, bool check, bool write_p, int width, int slots,
+                         int H, int grid, void *stream);
 cudaError_t node_pressure_rows(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
-                               const PressureArgs &a, bool check, bool write_p, int bt, int npt,
-                               int H, int grid);
+                               const PressureArgs &a, bool check, bool write_p, int width,
+                               int slots, int H, int grid);
 void refresh(const RefreshArgs &a, int grid, void *stream);
 void saturation(const SaturationArgs &a, int grid, void *stream);
 void init_g(const InitGArgs &a, int grid, void *stream);

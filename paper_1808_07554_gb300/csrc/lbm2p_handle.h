@@ -30,7 +30,7 @@ struct lbm2p {
     int sweep_kind = 0;        // single-sweep kernel: 0 = four nodes per thread, 1 = one
                                // node per thread, 2 = staged rows
     int grid_k[2] = {}, grid_check_k[2] = {};
-    int rows_bt = 0, rows_npt = 0, rows_H = 0, rows_grid = 0;   // staged-rows kernel shape
+    int rows_w = 0, rows_slots = 0, rows_H = 0, rows_grid = 0;   // staged-rows kernel shape
     int tb_T = 0, tb_W = 0, tb_H = 0, tb_grid = 0;   // fused sweeps per launch and tile shape
     int tb_T_graph = 0;        // fused sweeps used inside the graph loop body (0: single sweeps)
     int rebase_every = 0;      // a long solve moves R to the current P after every this many
@@ -62,6 +62,7 @@ struct lbm2p {
     cudaGraphExec_t solve_x[2] = {};
     cudaGraph_t step_g[2][2] = {};
     cudaGraphExec_t step_x[2][2] = {};
+    std::string autotune_log;          // one line per candidate timed at create
     std::string err;
 };
 

@@ -253,7 +253,7 @@ lbm2p_status upload_trace(lbm2p *h, float *dst, const double *src, int n)
 void launch_sweep(lbm2p *h, const PressureArgs &a, bool check, bool write_p)
 {
     if (h->sweep_kind == 2)
-        lbm2p_launch::pressure_sweep_rows(a, check, write_p, h->rows_bt, h->rows_npt, h->rows_H,
+        lbm2p_launch::pressure_sweep_rows(a, check, write_p, h->rows_w, h->rows_slots, h->rows_H,
                                           h->rows_grid, h->stream);
     else
         lbm2p_launch::pressure_sweep(a, check, write_p, check ? h->grid_check : h->grid, h->stream,
@@ -264,8 +264,8 @@ cudaError_t add_sweep_node(lbm2p *h, cudaGraphNode_t *n, cudaGraph_t g, const cu
                            const PressureArgs &a, bool check, bool write_p)
 {
     if (h->sweep_kind == 2)
-        return lbm2p_launch::node_pressure_rows(n, g, dep, a, check, write_p, h->rows_bt,
-                                                h->rows_npt, h->rows_H, h->rows_grid);
+        return lbm2p_launch::node_pressure_rows(n, g, dep, a, check, write_p, h->rows_w,
+                                                h->rows_slots, h->rows_H, h->rows_grid);
     return lbm2p_launch::node_pressure(n, g, dep, a, check, write_p,
                                        check ? h->grid_check : h->grid, h->sweep_kind);
 }
@@ -758,6 +758,12 @@ lbm2p_status autotune_sweeps(lbm2p *h)
     auto allowed = [&](int kind) { return forced == LBM2P_SWEEP_AUTO || forced == kind + 1; };
     const bool fused_only = h->p.fuse_sweeps == 2 || h->p.fuse_sweeps == 4;
     float best = 1e30f;                                    // per-sweep time of the choice
+    h->autotune_log.clear();
+    auto note = [&](const char *what, int a1, int a2, int a3, int a4, float us) {
+        char line[160];
+        snprintf(line, sizeof line, "%s %d %d %d %d %.3f\n", what, a1, a2, a3, a4, us);
+        h->autotune_log += line;
+    };
     h->tb_T = 0;
     h->sweep_kind = forced == LBM2P_SWEEP_AUTO ? 0 : forced - 1;
     if (!fused_only || forced != LBM2P_SWEEP_AUTO) {
@@ -770,30 +776,31 @@ lbm2p_status autotune_sweeps(lbm2p *h)
                     lbm2p_launch::pressure_sweep(a, false, false, h->grid_k[kind], h->stream, kind);
                 }, &ms))
                 goto done;
+            note(kind == 0 ? "single_vec4" : "single_scalar", h->grid_k[kind], 0, 0, 0, ms * 1e3f);
             if (ms < best) {
                 best = ms;
                 h->sweep_kind = kind;
             }
         }
-        // the staged-rows kernel: strip width, and rows per block giving 1, 2 or 4 blocks
-        // per resident block slot
-        const int shapes[3][2] = {{256, 1}, {128, 1}, {256, 2}};
+        // the staged-rows kernel: strip width, ring slots, and rows per block giving 1 to 16
+        // blocks per resident block slot
+        const int shapes[3][2] = {{128, 8}, {256, 6}, {256, 8}};
         float best_rows = 1e30f;
-        int rows_shape[4] = {0, 0, 0, 0};                  // bt, npt, H, grid
+        int rows_shape[4] = {0, 0, 0, 0};                  // width, slots, H, grid
         for (const auto &sh : shapes) {
             if (!allowed(2))
                 break;
-            const int bt = sh[0], npt = sh[1];
-            if (lbm2p_launch::rows_prepare(bt, npt) != cudaSuccess) {
+            const int width = sh[0], slots = sh[1];
+            if (lbm2p_launch::rows_prepare(width, slots) != cudaSuccess) {
                 cudaGetLastError();
                 continue;
             }
-            const int per_sm = lbm2p_launch::rows_blocks_per_sm(bt, npt);
+            const int per_sm = lbm2p_launch::rows_blocks_per_sm(width, slots, h->Fp != nullptr);
             if (per_sm < 1)
                 continue;
-            const int strips = (h->nx + bt * npt - 1) / (bt * npt);
+            const int strips = (h->nx + width - 1) / width;
             int last_H = -1;
-            for (int mult : {1, 2, 4}) {
+            for (int mult : {1, 2, 4, 8, 16}) {
                 const long long want = (long long)sms * per_sm * mult;
                 long long chunks = (want + strips - 1) / strips;
                 chunks = chunks < 1 ? 1 : chunks;
@@ -801,18 +808,19 @@ lbm2p_status autotune_sweeps(lbm2p *h)
                 if (H == last_H)
                     continue;
                 last_H = H;
-                const int grid = (int)lbm2p_launch::rows_grid(bt, npt, H, h->nx, h->ny);
+                const int grid = (int)lbm2p_launch::rows_grid(width, H, h->nx, h->ny);
                 float ms = 0.0f;
                 if (!timed([&](int k) {
                         PressureArgs a = pressure_args(h, k % 2);
-                        lbm2p_launch::pressure_sweep_rows(a, false, false, bt, npt, H, grid,
+                        lbm2p_launch::pressure_sweep_rows(a, false, false, width, slots, H, grid,
                                                           h->stream);
                     }, &ms))
                     goto done;
+                note("single_rows", width, slots, H, grid, ms * 1e3f);
                 if (ms < best_rows) {
                     best_rows = ms;
-                    rows_shape[0] = bt;
-                    rows_shape[1] = npt;
+                    rows_shape[0] = width;
+                    rows_shape[1] = slots;
                     rows_shape[2] = H;
                     rows_shape[3] = grid;
                 }
@@ -823,8 +831,8 @@ lbm2p_status autotune_sweeps(lbm2p *h)
             h->sweep_kind = 2;
         }
         if (rows_shape[0] > 0) {
-            h->rows_bt = rows_shape[0];
-            h->rows_npt = rows_shape[1];
+            h->rows_w = rows_shape[0];
+            h->rows_slots = rows_shape[1];
             h->rows_H = rows_shape[2];
             h->rows_grid = rows_shape[3];
         }
@@ -856,6 +864,7 @@ lbm2p_status autotune_sweeps(lbm2p *h)
                                                                 h->stream);
                         }, &ms))
                         goto done;
+                    note("fused", T, W, H, (int)blocks, ms / T * 1e3f);
                     if (ms / T < best) {
                         best = ms / T;
                         h->tb_T = T;
@@ -1380,10 +1389,15 @@ lbm2p_status lbm2p_sweep_config(const lbm2p *h, int *fused, int *kind, int *tile
     if (kind)
         *kind = h->sweep_kind + 1;        // internal 0, 1, 2 = VEC4, SCALAR, ROWS
     if (tile_w)
-        *tile_w = h->tb_T > 1 ? h->tb_W : (h->sweep_kind == 2 ? h->rows_bt * h->rows_npt : 0);
+        *tile_w = h->tb_T > 1 ? h->tb_W : (h->sweep_kind == 2 ? h->rows_w : 0);
     if (tile_h)
         *tile_h = h->tb_T > 1 ? h->tb_H : (h->sweep_kind == 2 ? h->rows_H : 0);
     return LBM2P_OK;
+}
+
+const char *lbm2p_autotune_report(const lbm2p *h)
+{
+    return h ? h->autotune_log.c_str() : "";
 }
 
 lbm2p_status lbm2p_counters(const lbm2p *h, long long *launches, long long *sweeps)
