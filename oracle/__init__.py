@@ -99,11 +99,13 @@ class Oracle:
         self.nx, self.ny = prob.nx, prob.ny
         self.prob = prob
         shape = (prob.ny, prob.nx)
-        ip = (C.c_int * 11)(prob.nx, prob.ny, prob.mobility, prob.tau_mode, int(max_sub_iters),
+        ip = (C.c_int * 12)(prob.nx, prob.ny, prob.mobility, prob.tau_mode, int(max_sub_iters),
                             int(check_every), *[int(b) for b in prob.bc],
-                            -1 if init_replay is None else int(init_replay))
-        dpar = (C.c_double * 10)(prob.dx, prob.dt, prob.phi, prob.beta, prob.mu_w, prob.mu_n,
-                                 prob.D_s, prob.tau_p, prob.D_ref, tol)
+                            -1 if init_replay is None else int(init_replay),
+                            int(getattr(prob, "sat_lattice", 9)))
+        dpar = (C.c_double * 11)(prob.dx, prob.dt, prob.phi, prob.beta, prob.mu_w, prob.mu_n,
+                                 prob.D_s, prob.tau_p, prob.D_ref, tol,
+                                 float(getattr(prob, "D_c", 0.0)))
         self._keep = []
         K = _f64(prob.K, shape)
         S0 = _f64(prob.S0, shape)
@@ -231,9 +233,10 @@ class Oracle:
                     last_k=int(out[5]))
 
     def constants(self):
-        out = np.zeros(54)
+        out = np.zeros(64)
         self.lib.orc_constants(self.h, _dptr(out))
-        return dict(w=out[0:9], wbar=out[9:18], Gamma=out[18:27], ex=out[27:36].astype(int),
+        return dict(w=out[0:9], wbar=out[9:18], Gamma=out[18:27], wg=out[54:63], qs=int(out[63]),
+                    ex=out[27:36].astype(int),
                     ey=out[36:45].astype(int), opp=out[45:54].astype(int))
 
     def sums(self):

@@ -31,6 +31,13 @@
  *    saturation source uses the water fraction at S* = sum_i g_i / phi.
  *  - the initial saturation gradient (Eq. gneq) is a second-order central difference
  *    (mirror at no-flux walls, wrap when periodic, one-sided at Dirichlet walls).
+ *  - D2Q5 saturation lattice (Remark V, Eq. 3-4b): weights omega_0 = 1/3, omega_1..4 =
+ *    1/6 (c_s^2 = 1/3, the paper gives none); the collision, the walls and Eq. gneq keep
+ *    their D2Q9 form with these weights and Gamma_i.
+ *  - saturation-dependent D_s (Remark IV): with a linear capillary pressure
+ *    P_c = p_e (1 - S), Eq. 2-16 gives D_s = K lambda_n f_w p_e = p_e K lambda_w lambda_n /
+ *    lambda_t; the model uses D_s(x, S) = D_s + D_c K lambda_w lambda_n / lambda_t
+ *    (D_c = p_e; D_c = 0 is the constant case), so tau_g varies per node (Eq. 3-11b).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -63,6 +70,9 @@ typedef struct orc {
     int max_sub, check_every;
     int bc[4];
     double w[9], wbar[9], Gam[9];      /* Eq. 3-5, 3-5a; Gamma_i = g_i^eq / S (Sec. 4) */
+    int qs;                            /* saturation lattice: 9 (D2Q9) or 5 (D2Q5) */
+    double wg[9];                      /* weights of the saturation lattice */
+    double D_c;                        /* capillary part of D_s (Remark IV) */
     double *K;
     double *f[9], *fpre[9];            /* post-collision f_i^+, pulled (pre-collision) f_i */
     double *g[9], *gpre[9];
@@ -94,6 +104,15 @@ static void set_constants(orc *o)
         /* Eq. 3-4: g_i^eq = omega_i S [phi + C:(c_i c_i - cs2 I)/(2 cs2)], C = (beta - phi) I,
            and C:(c_i c_i - cs2 I) = (beta - phi)(|c_i|^2 - 2 cs2) in two dimensions. */
         o->Gam[i] = o->w[i] * (o->phi + (o->beta - o->phi) * ((double)e2 - 2.0 * cs2) / (2.0 * cs2));
+        o->wg[i] = o->w[i];
+    }
+    if (o->qs == 5) {
+        /* D2Q5 (Remark V): omega_0 = 1/3, omega_1..4 = 1/6; Eq. 3-4b:
+           g_0^eq = [(omega_0 - 1) beta + phi] S, g_i^eq = omega_i beta S */
+        for (int i = 0; i < 9; ++i) {
+            o->wg[i] = i == 0 ? 1.0 / 3.0 : (i < 5 ? 1.0 / 6.0 : 0.0);
+            o->Gam[i] = i == 0 ? (o->wg[0] - 1.0) * o->beta + o->phi : o->wg[i] * o->beta;
+        }
     }
 }
 
@@ -121,6 +140,18 @@ static double frac_w(const orc *o, double S)
     double lw, lt;
     mobility(o, S, &lw, &lt);
     return lt != 0.0 ? lw / lt : 0.0;
+}
+
+/* Eq. 3-11b: D_s = beta c_s^2 (tau_g - 1/2) dt, c_s^2 = (dx/dt)^2 / 3, with
+   D_s(x, S) = D_s + D_c K lambda_w lambda_n / lambda_t and lambda_n = lambda_t - lambda_w */
+static double tau_g_at(const orc *o, size_t a, double S)
+{
+    if (o->D_c == 0.0)
+        return o->tau_g;
+    double lw, lt;
+    mobility(o, S, &lw, &lt);
+    double Ds = o->D_s + (lt != 0.0 ? o->D_c * o->K[a] * lw * (lt - lw) / lt : 0.0);
+    return 0.5 + 3.0 * Ds * o->dt / (o->beta * o->dx * o->dx);
 }
 
 /* ------------------------------------------------------------------------------------ */
@@ -167,12 +198,13 @@ static double pull(const orc *o, double *const *post, int i, int x, int y, int i
 static void stream(orc *o, double *const *post, double **pre, int is_g)
 {
     const int nx = o->nx, ny = o->ny;
+    const int q = is_g ? o->qs : 9;
 #pragma omp parallel for schedule(static)
     for (int y = 0; y < ny; ++y) {
         for (int x = 0; x < nx; ++x) {
             size_t a = (size_t)y * nx + x;
             int inner = x >= 1 && x <= nx - 2 && y >= 1 && y <= ny - 2;
-            for (int i = 0; i < 9; ++i) {
+            for (int i = 0; i < q; ++i) {
                 if (inner)
                     pre[i][a] = post[i][(size_t)(y - EY[i]) * nx + (x - EX[i])];
                 else
@@ -244,14 +276,14 @@ static void saturation_from_gpre(orc *o)
     double *Sstar = o->S;   /* S* = sum_i g_i / phi, overwritten below */
     for (size_t a = 0; a < o->n; ++a) {
         double s = 0.0;
-        for (int i = 0; i < 9; ++i)
+        for (int i = 0; i < o->qs; ++i)
             s += o->gpre[i][a];
         Sstar[a] = s / o->phi;
     }
     saturation_source(o, Sstar);
     for (size_t a = 0; a < o->n; ++a) {
         double s = 0.0;
-        for (int i = 0; i < 9; ++i)
+        for (int i = 0; i < o->qs; ++i)
             s += o->gpre[i][a];
         o->S[a] = (s + 0.5 * o->Fs_t[a]) / o->phi;
     }
@@ -305,18 +337,18 @@ static void collide_f(orc *o, const double *P, const double *Fp_t)
    gamma_t = -3 lambda_w K dt / dx^2. */
 static void collide_g(orc *o)
 {
-    const double tg = o->tau_g;
 #pragma omp parallel for schedule(static)
     for (size_t a = 0; a < o->n; ++a) {
+        const double tg = tau_g_at(o, a, o->S[a]);
         double lw, lt;
         mobility(o, o->S[a], &lw, &lt);
         double gam_t = -3.0 * lw * o->K[a] * o->dt / (o->dx * o->dx);
-        for (int i = 0; i < 9; ++i) {
+        for (int i = 0; i < o->qs; ++i) {
             double geq = o->Gam[i] * o->S[a];
             double gi = o->gpre[i][a];
             double cgrad = EX[i] * o->gxX[a] + EY[i] * o->gyX[a];
-            o->g[i][a] = gi - (gi - geq) / tg + o->w[i] * (1.0 - 1.0 / (2.0 * tg)) * o->Fs_t[a]
-                         + gam_t * o->w[i] * cgrad / tg;
+            o->g[i][a] = gi - (gi - geq) / tg + o->wg[i] * (1.0 - 1.0 / (2.0 * tg)) * o->Fs_t[a]
+                         + gam_t * o->wg[i] * cgrad / tg;
         }
     }
 }
@@ -540,21 +572,21 @@ static int initialise(orc *o, const double *P0, const double *S0, int init_repla
     gradient_from_fpre(o);
     /* dt F_s at t = 0, with S* = S_0 at the producer */
     saturation_source(o, S0);
-    const double tg = o->tau_g;
     for (int y = 0; y < o->ny; ++y) {
         for (int x = 0; x < o->nx; ++x) {
             size_t a = (size_t)y * o->nx + x;
+            const double tg = tau_g_at(o, a, S0[a]);
             double sxX = fd_axis(o, S0, x, y, 0);
             double syX = fd_axis(o, S0, x, y, 1);
             double lw, lt;
             mobility(o, S0[a], &lw, &lt);
             double gam_t = -3.0 * lw * o->K[a] * o->dt / (o->dx * o->dx);
-            for (int i = 0; i < 9; ++i) {
+            for (int i = 0; i < o->qs; ++i) {
                 double cS = EX[i] * sxX + EY[i] * syX;
                 double cP = EX[i] * o->gxX[a] + EY[i] * o->gyX[a];
                 /* Eq. gneq in lattice units */
-                double neq = -tg * ((o->Gam[i] / o->phi - o->w[i] * (1.0 - 1.0 / (2.0 * tg))) * o->Fs_t[a]
-                                    + o->Gam[i] * cS - gam_t * o->w[i] * cP / tg);
+                double neq = -tg * ((o->Gam[i] / o->phi - o->wg[i] * (1.0 - 1.0 / (2.0 * tg))) * o->Fs_t[a]
+                                    + o->Gam[i] * cS - gam_t * o->wg[i] * cP / tg);
                 o->gpre[i][a] = o->Gam[i] * S0[a] + neq;   /* Eq. gini */
             }
         }
@@ -562,7 +594,7 @@ static int initialise(orc *o, const double *P0, const double *S0, int init_repla
     /* S at t = 0 from the initial g (Eq. 3-9b), then the t = 0 collision */
     for (size_t a = 0; a < o->n; ++a) {
         double s = 0.0;
-        for (int i = 0; i < 9; ++i)
+        for (int i = 0; i < o->qs; ++i)
             s += o->gpre[i][a];
         o->S[a] = (s + 0.5 * o->Fs_t[a]) / o->phi;
     }
@@ -572,8 +604,9 @@ static int initialise(orc *o, const double *P0, const double *S0, int init_repla
 }
 
 /* Create the oracle and run the t = 0 initialisation.
-   iparams: nx, ny, mobility, tau_mode, max_sub, check_every, bc[4], init_replay (11 ints)
-   dparams: dx, dt, phi, beta, mu_w, mu_n, D_s, tau_p, D_ref, tol (10 doubles)
+   iparams: nx, ny, mobility, tau_mode, max_sub, check_every, bc[4], init_replay,
+            saturation lattice (9 or 5) (12 ints)
+   dparams: dx, dt, phi, beta, mu_w, mu_n, D_s, tau_p, D_ref, tol, D_c (11 doubles)
    wells:   nw entries of (i, j, is_producer) in wint and q in wq. */
 orc *orc_create(const int *iparams, const double *dparams, const double *K, const double *S0,
                 const double *P0, const double *Fp, const double *Fs, int nw, const int *wint,
@@ -599,6 +632,7 @@ orc *orc_create(const int *iparams, const double *dparams, const double *K, cons
     for (int s = 0; s < 4; ++s)
         o->bc[s] = iparams[6 + s];
     int init_replay = iparams[10];
+    o->qs = iparams[11];
     o->dx = dparams[0];
     o->dt = dparams[1];
     o->phi = dparams[2];
@@ -609,7 +643,8 @@ orc *orc_create(const int *iparams, const double *dparams, const double *K, cons
     o->tau_p = dparams[7];
     o->D_ref = dparams[8];
     o->tol = dparams[9];
-    if (o->check_every < 1 || o->max_sub < 1 || (o->bc[0] == PERIODIC) != (o->bc[1] == PERIODIC) ||
+    o->D_c = dparams[10];
+    if ((o->qs != 9 && o->qs != 5) || o->check_every < 1 || o->max_sub < 1 || (o->bc[0] == PERIODIC) != (o->bc[1] == PERIODIC) ||
         (o->bc[2] == PERIODIC) != (o->bc[3] == PERIODIC)) {
         free(o);
         return NULL;
@@ -780,7 +815,7 @@ void orc_set_prev_pressure(orc *o, const double *P)
     memcpy(o->Pprev, P, o->n * sizeof(double));
 }
 
-/* Scalars: [s, tau_g, D_ref, step, last_r, last_k] */
+/* Scalars: [s, tau_g (of the constant D_s), D_ref, step, last_r, last_k] */
 void orc_scalars(const orc *o, double *out)
 {
     out[0] = o->s;
@@ -791,7 +826,8 @@ void orc_scalars(const orc *o, double *out)
     out[5] = (double)o->last_k;
 }
 
-/* Lattice constants: w[9], wbar[9], Gamma[9], ex[9], ey[9], opp[9] (as doubles). */
+/* Lattice constants: w[9], wbar[9], Gamma[9], ex[9], ey[9], opp[9], then the saturation
+   lattice's weights wg[9] and its size (as doubles). */
 void orc_constants(const orc *o, double *out)
 {
     for (int i = 0; i < 9; ++i) {
@@ -801,7 +837,9 @@ void orc_constants(const orc *o, double *out)
         out[27 + i] = EX[i];
         out[36 + i] = EY[i];
         out[45 + i] = OPP[i];
+        out[54 + i] = o->wg[i];
     }
+    out[63] = (double)o->qs;
 }
 
 /* sums over all nodes of sum_i f_i^+ and sum_i g_i^+ (conservation checks) */

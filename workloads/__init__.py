@@ -59,6 +59,8 @@ class Problem:
     P_b: list = field(default_factory=lambda: [None] * 4)
     S_b: list = field(default_factory=lambda: [None] * 4)
     D_ref: float = 0.0                          # <= 0: geometric mean of D_p at t = 0
+    sat_lattice: int = 9                        # saturation lattice: 9 (D2Q9) or 5 (D2Q5)
+    D_c: float = 0.0                            # D_s(S) = D_s + D_c K lambda_w lambda_n / lambda_t
     # callables t -> arrays, for problems whose sources / wall values depend on time
     sources_at: object = None                   # t -> (Fp, Fs)
     walls_at: object = None                     # t -> (P_b list, S_b list)
@@ -114,12 +116,13 @@ def grf_lnK(nx: int, ny: int, sigma: float, corr_len: float, seed: int) -> np.nd
 # --------------------------------------------------------------------------------------
 # Manufactured periodic problem: 64^2 unit square, quadratic relative permeabilities
 # --------------------------------------------------------------------------------------
-def manufactured_fields(x, y, t, mu_w=1.0, mu_n=2.0, phi=0.2, D_s=0.01, p_amp=1.0):
+def manufactured_fields(x, y, t, mu_w=1.0, mu_n=2.0, phi=0.2, D_s=0.01, p_amp=1.0, D_c=0.0):
     """Closed-form p, S, K on the periodic unit square and the sources that make them exact.
 
     p = A sin(2 pi x) cos(2 pi y) e^-t,  S = 1/2 + 1/4 sin(2 pi x) sin(2 pi y) e^-t,
     K = 1 + 1/2 sin(2 pi x) sin(2 pi y),  lambda_w = S^2/mu_w, lambda_n = (1-S)^2/mu_n.
-    F_p = -div(K lambda_t grad p),  F_s = phi dS/dt - D_s lap S - div(lambda_w K grad p),
+    F_p = -div(K lambda_t grad p),  F_s = phi dS/dt - div(D grad S) - div(lambda_w K grad p)
+    with D = D_s + D_c K h(S), h = lambda_w lambda_n / lambda_t (D_c = 0: constant D_s),
     expanded by the product rule with hand-derived first and second derivatives.
     The pressure amplitude A (p_amp) is 1 for the parity workload; smaller values lower the
     Darcy velocity, hence the advective Courant number on coarse grids.
@@ -150,42 +153,53 @@ def manufactured_fields(x, y, t, mu_w=1.0, mu_n=2.0, phi=0.2, D_s=0.01, p_amp=1.
     div_Klt_gradp = lt * gradK_gradp + K * dlt * gradS_gradp + K * lt * lap_p
     div_Klw_gradp = lw * gradK_gradp + K * dlw * gradS_gradp + K * lw * lap_p
     Fp = -div_Klt_gradp
-    Fs = phi * dS_dt - D_s * lap_S - div_Klw_gradp
+    # div(D grad S) = D lap S + grad D . grad S, grad D = D_c (h grad K + K h'(S) grad S)
+    dln = -2.0 * (1.0 - S) / mu_n
+    h = lw * ln / lt
+    dh = (dlw * ln + lw * dln) / lt - lw * ln * dlt / (lt * lt)
+    D = D_s + D_c * K * h
+    gradS2 = Sx * Sx + Sy * Sy
+    gradK_gradS = Kx * Sx + Ky * Sy
+    div_D_gradS = D * lap_S + D_c * (h * gradK_gradS + K * dh * gradS2)
+    Fs = phi * dS_dt - div_D_gradS - div_Klw_gradp
     u_x = -K * lt * px
     u_y = -K * lt * py
     return dict(K=K, P=p, S=S, Fp=Fp, Fs=Fs, ux=u_x, uy=u_y, gradPx=px, gradPy=py)
 
 
 def manufactured_periodic(n: int = 64, steps: int = 500, tau_p: float = 1.0,
-                          p_amp: float = 1.0) -> Problem:
+                          p_amp: float = 1.0, D_c: float = 0.0, sat_lattice: int = 9,
+                          beta: float = 0.4) -> Problem:
     """64x64 periodic unit square with the manufactured p and S (closed-form sources).
 
     phi = 0.2, beta = 0.4 (the largest admissible value not above 1 for phi = 0.2),
     mu_w = 1, mu_n = 2, D_s = 0.01, tau_p = 1.0, tau_s = 0.8; dt = 4 dx^2 is the step
     at which the saturation relaxation time equals 0.8 for these beta and D_s.
     The discrete mean of F_p is removed at every time: on a periodic domain the pressure
-    equation is solvable only for a zero-mean source.
+    equation is solvable only for a zero-mean source.  Variants: D_c > 0 makes D_s depend
+    on S and K (D_s + D_c K lambda_w lambda_n / lambda_t); sat_lattice = 5 carries S on
+    D2Q5 (which needs beta <= 1.5 phi, e.g. beta = 0.3).
     """
     dx = 1.0 / n
     dt = 4.0 * dx * dx
     X, Y = node_coords(n, n, dx)
-    f0 = manufactured_fields(X, Y, 0.0, p_amp=p_amp)
+    f0 = manufactured_fields(X, Y, 0.0, p_amp=p_amp, D_c=D_c)
 
     def sources_at(t):
-        m = manufactured_fields(X, Y, t, p_amp=p_amp)
+        m = manufactured_fields(X, Y, t, p_amp=p_amp, D_c=D_c)
         Fp = m["Fp"] - m["Fp"].mean()
         return Fp, m["Fs"]
 
     def exact_at(t):
-        m = manufactured_fields(X, Y, t, p_amp=p_amp)
+        m = manufactured_fields(X, Y, t, p_amp=p_amp, D_c=D_c)
         return dict(P=m["P"], S=m["S"], ux=m["ux"], uy=m["uy"])
 
     Fp0, Fs0 = sources_at(0.0)
     return Problem(name=f"manufactured_periodic_{n}", nx=n, ny=n, dx=dx, dt=dt, phi=0.2,
-                   beta=0.4, mobility=MOB_QUADRATIC, mu_w=1.0, mu_n=2.0, D_s=0.01,
+                   beta=beta, mobility=MOB_QUADRATIC, mu_w=1.0, mu_n=2.0, D_s=0.01,
                    tau_mode=TAU_REFERENCE, tau_p=tau_p, bc=(PERIODIC,) * 4, K=f0["K"],
                    S0=f0["S"], P0=f0["P"], Fp=Fp0, Fs=Fs0, sources_at=sources_at,
-                   exact_at=exact_at, steps=steps)
+                   exact_at=exact_at, steps=steps, sat_lattice=sat_lattice, D_c=D_c)
 
 
 # --------------------------------------------------------------------------------------
