@@ -42,6 +42,8 @@ import workloads as W  # noqa: E402
 # (stored as FP32 deviations) + the reference pressure + 1/tau_f; a launch that fuses T
 # sweeps moves the same bytes once for T sweeps
 BYTES_PER_SWEEP_NODE = 72
+# with FP16 storage: 8 populations x (2 + 2) B + the node pressure read and written + 1/tau_f
+BYTES_PER_SWEEP_NODE_FP16 = 44
 WORKLOADS = {
     "five_spot_1024": dict(kind="five_spot", n=1024),
     "five_spot_4096": dict(kind="five_spot", n=4096),
@@ -264,9 +266,10 @@ def run_ours(args):
         P0 = coarse_initial_pressure(prob, pkg, log=coarse_log)
         if P0 is not None:
             prob.P0 = P0
-    solver = pkg.Solver.from_problem(prob, tol=1e-8, check_every=args.check_every,
+    solver = pkg.Solver.from_problem(prob, tol=args.tol, check_every=args.check_every,
                                      max_sub_iters=args.max_sub_iters, fuse_sweeps=args.fuse_sweeps,
-                                     sweep_kernel=args.sweep_kernel)
+                                     sweep_kernel=args.sweep_kernel,
+                                     storage=1 if args.storage == "fp16" else 0)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t_setup
     init_sweeps = solver.init_stats.sub_iters
@@ -343,14 +346,17 @@ def run_ours(args):
     avg_sweep_s = float(np.sum(sweep_ms)) / 1e3 / max(1, sweeps_timed)
     fused = sweep_cfg[0]
     avg_launch_s = avg_sweep_s * fused
-    achieved = BYTES_PER_SWEEP_NODE * nodes / avg_launch_s / 1e9
+    bpn = BYTES_PER_SWEEP_NODE_FP16 if args.storage == "fp16" else BYTES_PER_SWEEP_NODE
+    achieved = bpn * nodes / avg_launch_s / 1e9
     traffic = NCU_TRAFFIC_PER_SWEEP.get(args.workload)
     line = {
         "metric": "MLUPS", "value": updates_all / time_max / 1e6, "unit": "MLUPS",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": args.workload, "nx": prob.nx, "ny": prob.ny, "tol": 1e-8,
+        "vs_baseline": None, "dtype": "f32" if args.storage == "fp32" else "f16 storage, f32 arithmetic",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "nx": prob.nx, "ny": prob.ny, "tol": args.tol,
+                   "storage": args.storage,
                    "check_every": args.check_every, "fuse_sweeps": args.fuse_sweeps,
                    "sweep_kernel": sweep_cfg[1], "sweep_tile": [sweep_cfg[2], sweep_cfg[3]],
                    "l2": "flushed before every timed step",
@@ -364,10 +370,11 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": ("pressure sweep (fused stream + collide, Eq. 3-1), "
-                                + (f"{fused} sweeps per launch" if fused > 1 else
-                                   SWEEP_KERNEL_NAMES.get(sweep_cfg[1], "?"))
-                                + (", autotuned" if args.sweep_kernel == 0 else "")),
-                     "bytes_per_launch": BYTES_PER_SWEEP_NODE * nodes,
+                                + ("FP16 populations, one node per thread" if args.storage == "fp16"
+                                   else (f"{fused} sweeps per launch" if fused > 1 else
+                                         SWEEP_KERNEL_NAMES.get(sweep_cfg[1], "?"))
+                                   + (", autotuned" if args.sweep_kernel == 0 else ""))),
+                     "bytes_per_launch": bpn * nodes,
                      "avg_launch_us": avg_launch_s * 1e6,
                      "launch_time_includes": "the residual finalize kernel of every 8th sweep",
                      "peak_kind": peak_kind},
@@ -545,6 +552,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fuse-sweeps", type=int, default=0, choices=[0, 1, 2, 4],
                     help="pressure sweeps per launch: 0 = autotuned, 1, 2 or 4")
+    ap.add_argument("--storage", choices=["fp32", "fp16"], default="fp32",
+                    help="pressure populations during the sub-iteration: FP32 or FP16 deviations")
+    ap.add_argument("--tol", type=float, default=1e-8,
+                    help="relative increment that ends a pressure solve")
     ap.add_argument("--sweep-kernel", type=int, default=0, choices=[0, 1, 2, 3],
                     help="single-sweep kernel: 0 = autotuned, 1 = float4, 2 = one node per "
                          "thread, 3 = staged rows")

@@ -42,7 +42,7 @@
 extern "C" {
 #endif
 
-#define LBM2P_ABI_VERSION 3
+#define LBM2P_ABI_VERSION 4
 /* Sparse wells passed to the sweep kernels as launch arguments (more wells: error). */
 #define LBM2P_MAX_WELLS 16
 
@@ -84,7 +84,17 @@ typedef enum { LBM2P_TAU_REFERENCE = 0, LBM2P_TAU_PHYSICAL_DT = 1 } lbm2p_tau_mo
 typedef enum { LBM2P_SWEEP_AUTO = 0, LBM2P_SWEEP_VEC4 = 1, LBM2P_SWEEP_SCALAR = 2,
                LBM2P_SWEEP_ROWS = 3 } lbm2p_sweep_kernel;
 
-/* Population storage.  FP16_DEV (FP16 deviations from equilibrium) is reserved. */
+/* Population storage during the pressure sub-iteration.
+ *   FP32:     the FP32 deviations n_i = f_i^+ - w_i R (see lbm2p_state_count), 72 B per node
+ *             and sweep.
+ *   FP16_DEV: each solve narrows them to FP16 scaled by a power of two chosen from max |n_i|,
+ *             sweeps with R moved to the node's new pressure after every sweep (so the
+ *             stored values are the post-collision non-equilibrium parts f_i^+ - w_i P), and
+ *             widens the result back; arithmetic FP32, residual FP64; 44 B per node and
+ *             sweep.  The state between steps stays FP32.  FP16 rounding puts a floor under
+ *             the relative increment r: use a tolerance above it or replayed sweep counts.  Sweeps are launched from the host (no graph), by
+ *             one one-node-per-thread kernel (lbm2p_sweep_config reports SCALAR); not
+ *             available in batches. */
 typedef enum { LBM2P_STORE_FP32 = 0, LBM2P_STORE_FP16_DEV = 1 } lbm2p_storage;
 
 /* A point well at node (i, j) with total rate q >= 0 (per unit depth): the node's cell
@@ -118,6 +128,12 @@ typedef struct {
                                    Within the choice, create times the candidate kernels and
                                    tile shapes on the lattice and keeps the fastest. */
     int sweep_kernel;           /* lbm2p_sweep_kernel: the single-sweep kernel (AUTO: timed) */
+    int sat_lattice;            /* saturation lattice: 9 (D2Q9, Eq. 3-4) or 5 (D2Q5, Remark V,
+                                   Eq. 3-4b, weights 1/3 and 1/6; needs beta <= 1.5 phi) */
+    double D_c;                 /* saturation-dependent diffusivity (Remark IV):
+                                   D_s(x, S) = D_s + D_c K lambda_w lambda_n / lambda_t, the
+                                   D_s of Eq. 2-16 with a linear capillary pressure of scale
+                                   D_c; tau_g then varies per node (Eq. 3-11b).  0: constant */
     void *stream;               /* cudaStream_t the work is enqueued on */
     void *(*alloc)(size_t bytes, void *ctx);            /* optional device allocator */
     void (*release)(void *ptr, size_t bytes, void *ctx); /* its matching free */

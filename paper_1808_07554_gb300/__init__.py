@@ -45,7 +45,7 @@ class lbm2p_params(C.Structure):
                 ("tau_mode", C.c_int), ("tau_p", C.c_double), ("D_ref", C.c_double),
                 ("tol", C.c_double), ("max_sub_iters", C.c_int), ("check_every", C.c_int),
                 ("bc", C.c_int * 4), ("storage", C.c_int), ("fuse_sweeps", C.c_int),
-                ("sweep_kernel", C.c_int),
+                ("sweep_kernel", C.c_int), ("sat_lattice", C.c_int), ("D_c", C.c_double),
                 ("stream", C.c_void_p),
                 ("alloc", ALLOC_FN), ("release", RELEASE_FN), ("alloc_ctx", C.c_void_p)]
 
@@ -347,7 +347,7 @@ class Solver:
                  tau_p, bc, K, S0, P0=None, Fp=None, Fs=None, wells=(), P_b=None, S_b=None,
                  D_ref=0.0, tol=1e-8, max_sub_iters=10_000_000, check_every=8,
                  init_replay=None, use_torch=True, stream=None, fuse_sweeps=0,
-                 sweep_kernel=0):
+                 sweep_kernel=0, sat_lattice=9, D_c=0.0, storage=0):
         lib = _lib_or_raise()
         self.nx, self.ny = int(nx), int(ny)
         n = self.nx * self.ny
@@ -360,6 +360,9 @@ class Solver:
         p.tol, p.max_sub_iters, p.check_every = float(tol), int(max_sub_iters), int(check_every)
         p.fuse_sweeps = int(fuse_sweeps)
         p.sweep_kernel = int(sweep_kernel)
+        p.sat_lattice = int(sat_lattice)
+        p.storage = int(storage)
+        p.D_c = float(D_c)
         for s in range(4):
             p.bc[s] = int(bc[s])
         self._mem = None
@@ -417,7 +420,9 @@ class Solver:
                    mobility=prob.mobility, mu_w=prob.mu_w, mu_n=prob.mu_n, D_s=prob.D_s,
                    tau_mode=prob.tau_mode, tau_p=prob.tau_p, bc=prob.bc, K=prob.K, S0=prob.S0,
                    P0=prob.P0, Fp=prob.Fp, Fs=prob.Fs, wells=prob.wells, P_b=prob.P_b,
-                   S_b=prob.S_b, D_ref=prob.D_ref, **kw)
+                   S_b=prob.S_b, D_ref=prob.D_ref,
+                   sat_lattice=getattr(prob, "sat_lattice", 9), D_c=getattr(prob, "D_c", 0.0),
+                   **kw)
 
     # -- lifecycle ----------------------------------------------------------------------
     def close(self):

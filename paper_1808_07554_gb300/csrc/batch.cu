@@ -508,6 +508,8 @@ lbm2p_status lbm2p_batch_create(lbm2p_batch **out, lbm2p *const *members, int co
             return bfail(nullptr, LBM2P_EINVAL,
                          "members need one even check_every (member %d has %d, member 0 %d)", i,
                          h->p.check_every, m0->p.check_every);
+        if (h->fp16)
+            return bfail(nullptr, LBM2P_EINVAL, "member %d uses FP16 storage (not batched)", i);
         if (h->p.max_sub_iters % h->p.check_every)
             return bfail(nullptr, LBM2P_EINVAL,
                          "member %d: max_sub_iters %d is not a multiple of check_every %d", i,

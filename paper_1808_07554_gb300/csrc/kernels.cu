@@ -690,7 +690,6 @@ __global__ void __launch_bounds__(kBlock) k_init_g(const __grid_constant__ InitG
 {
     const Geom &g = a.g;
     const Model &m = a.m;
-    const float tg = 1.0f / m.inv_tau_g;
     for (int t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
         const int y = t / g.tiles_x;
         const int x = (t - y * g.tiles_x) * kBlock + threadIdx.x;
@@ -707,30 +706,41 @@ __global__ void __launch_bounds__(kBlock) k_init_g(const __grid_constant__ InitG
         const float it = a.inv_tau[o];
         const float gx = -3.0f * mx * it, gy = -3.0f * my * it;
         const float Fs = saturation_source(m, a.w, a.Fs, o, S0);   // S* = S0 at t = 0
+        const float K = a.K[o];
         float lw, lt;
         mobility(m, S0, lw, lt);
-        const float gam0 = -m.gam_c * lw * a.K[o];
+        float inv_tg0, src_g0;
+        tau_g_node(m, K, lw, lt, inv_tg0, src_g0);
+        const float tg = 1.0f / inv_tg0;
+        const float gam0 = -m.gam_c * lw * K;
         float q[9];
         float sum = 0.0f;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            const float wi = wgt(i);
+            q[i] = 0.0f;
+            if (i >= m.qs)
+                continue;
+            const float wi = m.wg[i];
             const float cS = (float)cx(i) * sx + (float)cy(i) * sy;
             const float cP = (float)cx(i) * gx + (float)cy(i) * gy;
-            const float neq = -tg * ((m.Gam[i] * m.inv_phi - wi * m.src_g) * Fs + m.Gam[i] * cS
-                                     - gam0 * wi * cP * m.inv_tau_g);
+            const float neq = -tg * ((m.Gam[i] * m.inv_phi - wi * src_g0) * Fs + m.Gam[i] * cS
+                                     - gam0 * wi * cP * inv_tg0);
             q[i] = m.Gam[i] * S0 + neq;
             sum += q[i];
         }
         const float S = (sum + 0.5f * Fs) * m.inv_phi;
         mobility(m, S, lw, lt);
-        const float gam = -m.gam_c * lw * a.K[o] * m.inv_tau_g;
-        const float src = m.src_g * Fs;
+        float inv_tg, src_g;
+        tau_g_node(m, K, lw, lt, inv_tg, src_g);
+        const float gam = -m.gam_c * lw * K * inv_tg;
+        const float src = src_g * Fs;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            const float wi = wgt(i);
+            if (i >= m.qs)
+                break;
+            const float wi = m.wg[i];
             const float cg = (float)cx(i) * gx + (float)cy(i) * gy;
-            a.gout[i][o] = fmaf(m.Gam[i] * S - q[i], m.inv_tau_g, q[i]) + wi * src + gam * wi * cg;
+            a.gout[i][o] = fmaf(m.Gam[i] * S - q[i], inv_tg, q[i]) + wi * src + gam * wi * cg;
         }
         a.S[o] = S;
     }

@@ -18,6 +18,7 @@
 //   g: 9 planes, g_0 .. g_8, plain post-collision values.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -72,7 +73,11 @@ struct Model {
     float src_g;         // 1 - 1/(2 tau_g)
     float gam_c;         // gamma~ = -gam_c * lambda_w K   (3 dt / dx^2)
     float inv_dx;
-    float Gam[9];        // g_i^eq / S (Eq. 3-4)
+    float Gam[9];        // g_i^eq / S (Eq. 3-4, or Eq. 3-4b on D2Q5)
+    int qs;              // saturation lattice: 9 or 5 populations
+    float wg[9];         // weights of the saturation lattice (D2Q5: 1/3, 1/6)
+    int var_ds;          // tau_g per node: 1/2 + ds_a0 + ds_a1 K lambda_w lambda_n / lambda_t
+    float ds_a0, ds_a1;  // 3 D_s dt / (beta dx^2), 3 D_c dt / (beta dx^2)
 };
 
 // Sparse point wells, rates already divided by dx^2.
@@ -170,6 +175,33 @@ struct RebaseMidArgs {      // within a long solve: R += dP of the last sweep (n
     Wells w;
 };
 
+// FP16 storage inside a sub-iteration (fp16.cu)
+struct HalfConvertArgs {
+    const float *n32[8];     // narrow: FP32 deviations read
+    float *n32w[8];          // widen: FP32 deviations written (the same planes)
+    __half *n16[8];          // FP16 populations, scaled by scale[0]
+    float *R;                // narrow reads it, widen writes it
+    float *Rh;               // narrow writes it, widen reads it
+    float *scale;            // [0] s, [1] 1/s, [2] max |n_i| (as float bits, for the next s)
+    Geom g;
+};
+
+struct HalfSweepArgs {
+    const __half *nin[8];
+    __half *nout[8];
+    const float *Rin;        // node pressures of the previous sweep
+    float *Rout;             // Rin + dP
+    const float *inv_tau;
+    const float *Fp;
+    double *partials;
+    const float *shift;
+    const float *scale;      // [0] s, [1] 1/s
+    float *scale_out;        // the same array: check sweeps raise [3] to max |stored value|
+    const float *Pb[4];
+    Geom g;
+    Wells w;
+};
+
 struct ResidualOut {        // written by the finalize kernel
     double r;
     double mean_P;
@@ -224,6 +256,12 @@ void pressure_sweep_rows(const PressureArgs &a, bool check, bool write_p, int wi
 cudaError_t node_pressure_rows(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
                                const PressureArgs &a, bool check, bool write_p, int width,
                                int slots, int H, int grid);
+// FP16 storage (fp16.cu): narrow = max |n| -> scale -> convert; one sweep; widen
+int max_blocks_per_sm_pressure_h();
+void half_narrow(const HalfConvertArgs &a, int grid, void *stream);
+void half_widen(const HalfConvertArgs &a, int grid, void *stream);
+void half_rescale(const HalfConvertArgs &a, float factor, int grid, void *stream);
+void pressure_sweep_h(const HalfSweepArgs &a, bool check, int grid, void *stream);
 void refresh(const RefreshArgs &a, int grid, void *stream);
 void saturation(const SaturationArgs &a, int grid, void *stream);
 void init_g(const InitGArgs &a, int grid, void *stream);

@@ -33,6 +33,14 @@ struct lbm2p {
     int rows_w = 0, rows_slots = 0, rows_H = 0, rows_grid = 0;   // staged-rows kernel shape
     int tb_T = 0, tb_W = 0, tb_H = 0, tb_grid = 0;   // fused sweeps per launch and tile shape
     int tb_T_graph = 0;        // fused sweeps used inside the graph loop body (0: single sweeps)
+    bool fp16 = false;         // storage FP16_DEV: sweeps run on FP16 copies inside a solve
+    __half *hbuf[2][8] = {};
+    float *Rh[2] = {};
+    float *hscale = nullptr;   // [0] s, [1] 1/s, [2] max |n| of the last narrow,
+                               // [3] max |stored value| seen by the check sweeps
+    float *hscale_host = nullptr;   // pinned copy
+    int hcur = 0;
+    int grid_h = 0;
     int rebase_every = 0;      // a long solve moves R to the current P after every this many
                                // sweeps (a multiple of check_every)
     void *stream = nullptr;

@@ -132,27 +132,49 @@ __device__ __forceinline__ void gather_g(const float *const *gin, const Geom &g,
                                          const float *const *Sb, int x, int y, int o,
                                          float (&q)[9])
 {
+    // D2Q5 (m.qs == 5) carries populations 0..4 only; the diagonal slots read as zero
     q[0] = gin[0][o];
+    q[5] = q[6] = q[7] = q[8] = 0.0f;
     if (interior(g, x, y)) {
         const int p = g.pitch;
         q[1] = gin[1][o - 1];
         q[2] = gin[2][o - p];
         q[3] = gin[3][o + 1];
         q[4] = gin[4][o + p];
-        q[5] = gin[5][o - p - 1];
-        q[6] = gin[6][o - p + 1];
-        q[7] = gin[7][o + p + 1];
-        q[8] = gin[8][o + p - 1];
+        if (m.qs == 9) {
+            q[5] = gin[5][o - p - 1];
+            q[6] = gin[6][o - p + 1];
+            q[7] = gin[7][o + p + 1];
+            q[8] = gin[8][o + p - 1];
+        }
     } else {
         q[1] = pull_edge<1>(gin[1], gin[opp(1)], g, Sb, m.Gam[opp(1)], x, y);
         q[2] = pull_edge<2>(gin[2], gin[opp(2)], g, Sb, m.Gam[opp(2)], x, y);
         q[3] = pull_edge<3>(gin[3], gin[opp(3)], g, Sb, m.Gam[opp(3)], x, y);
         q[4] = pull_edge<4>(gin[4], gin[opp(4)], g, Sb, m.Gam[opp(4)], x, y);
-        q[5] = pull_edge<5>(gin[5], gin[opp(5)], g, Sb, m.Gam[opp(5)], x, y);
-        q[6] = pull_edge<6>(gin[6], gin[opp(6)], g, Sb, m.Gam[opp(6)], x, y);
-        q[7] = pull_edge<7>(gin[7], gin[opp(7)], g, Sb, m.Gam[opp(7)], x, y);
-        q[8] = pull_edge<8>(gin[8], gin[opp(8)], g, Sb, m.Gam[opp(8)], x, y);
+        if (m.qs == 9) {
+            q[5] = pull_edge<5>(gin[5], gin[opp(5)], g, Sb, m.Gam[opp(5)], x, y);
+            q[6] = pull_edge<6>(gin[6], gin[opp(6)], g, Sb, m.Gam[opp(6)], x, y);
+            q[7] = pull_edge<7>(gin[7], gin[opp(7)], g, Sb, m.Gam[opp(7)], x, y);
+            q[8] = pull_edge<8>(gin[8], gin[opp(8)], g, Sb, m.Gam[opp(8)], x, y);
+        }
     }
+}
+
+// 1/tau_g and 1 - 1/(2 tau_g) at a node: constants when D_s is constant, otherwise
+// tau_g = 1/2 + 3 D_s(x, S) dt / (beta dx^2) with D_s = D_s + D_c K lambda_w lambda_n /
+// lambda_t (Eq. 3-11b with the diffusivity of Eq. 2-16 for a linear capillary pressure)
+__device__ __forceinline__ void tau_g_node(const Model &m, float K, float lw, float lt,
+                                           float &inv_tg, float &src)
+{
+    if (!m.var_ds) {
+        inv_tg = m.inv_tau_g;
+        src = m.src_g;
+        return;
+    }
+    const float h = lt != 0.0f ? lw * (lt - lw) / lt : 0.0f;
+    inv_tg = 1.0f / (0.5f + m.ds_a0 + m.ds_a1 * K * h);
+    src = 1.0f - 0.5f * inv_tg;
 }
 
 // Eq. 3-9a: P = sum_{i=1..8} f_i / (1 - w_0) = (9/5) sum
@@ -247,15 +269,20 @@ __device__ __forceinline__ void saturation_node(const SaturationArgs &a, int x, 
     const float gx = -3.0f * mx * it, gy = -3.0f * my * it;
     float lw, lt;
     mobility(m, S, lw, lt);
+    const float K = a.K[o];
+    float inv_tg, src_g;
+    tau_g_node(m, K, lw, lt, inv_tg, src_g);
     // gamma~ = -3 lambda_w K dt / dx^2 (Eq. 3-8 in lattice units), pre-divided by tau_g
-    const float gam = -m.gam_c * lw * a.K[o] * m.inv_tau_g;
-    const float src = m.src_g * Fs;
+    const float gam = -m.gam_c * lw * K * inv_tg;
+    const float src = src_g * Fs;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        const float wi = wgt(i);
+        if (i >= m.qs)
+            break;
+        const float wi = m.wg[i];
         const float cg = (float)cx(i) * gx + (float)cy(i) * gy;
         const float eq = m.Gam[i] * S;
-        a.gout[i][o] = fmaf(eq - q[i], m.inv_tau_g, q[i]) + wi * src + gam * wi * cg;
+        a.gout[i][o] = fmaf(eq - q[i], inv_tg, q[i]) + wi * src + gam * wi * cg;
     }
     a.S[o] = S;
 }

@@ -205,6 +205,9 @@ void free_all(lbm2p *h)
     if (h->ctl_host)
         cudaFreeHost(h->ctl_host);
     h->ctl_host = nullptr;
+    if (h->hscale_host)
+        cudaFreeHost(h->hscale_host);
+    h->hscale_host = nullptr;
     for (cudaEvent_t *e : {&h->ev_step0, &h->ev_step1, &h->ev_sw0, &h->ev_sw1})
         if (*e) {
             cudaEventDestroy(*e);
@@ -411,8 +414,169 @@ lbm2p_status loop_status(lbm2p *h, int k, double r)
 
 // ---- the pressure sub-iteration (Sec. 3) ------------------------------------------------
 // replay >= 0: exactly that many sweeps; replay < 0: until r <= tol at a check or the cap.
+lbm2p_status pressure_solve_h(lbm2p *h, int replay, int *k_out, double *r_out, float *ms_out);
+
+// The sub-iteration with FP16 storage (fp16.cu): narrow the FP32 state, sweep on FP16 with
+// the same stopping rule and replay semantics as pressure_solve, widen the result.
+lbm2p_status pressure_solve_h(lbm2p *h, int replay, int *k_out, double *r_out, float *ms_out)
+{
+    cudaStream_t st = (cudaStream_t)h->stream;
+    const int m = h->p.check_every;
+    const int cap = h->p.max_sub_iters;
+    auto convert_args = [&](int hb) {
+        HalfConvertArgs a{};
+        for (int i = 0; i < 8; ++i) {
+            a.n32[i] = h->fbuf[h->cur_f][i];
+            a.n32w[i] = h->fbuf[h->cur_f][i];
+            a.n16[i] = h->hbuf[hb][i];
+        }
+        a.R = h->R;
+        a.Rh = h->Rh[hb];
+        a.scale = h->hscale;
+        a.g = h->geom;
+        return a;
+    };
+    lbm2p_launch::half_narrow(convert_args(0), h->grid, h->stream);
+    LAUNCHED(h, "FP16 narrow");
+    h->hcur = 0;
+    int k = 0;
+    double r = std::nan("");
+    float ms_total = 0.0f;
+    lbm2p_status status = LBM2P_OK;
+    auto sweeps = [&](int upto, bool final_check) -> lbm2p_status {
+        if (h->timing)
+            CUDA_TRY(h, cudaEventRecord(h->ev_sw0, st));
+        for (int kk = k + 1; kk <= upto; ++kk) {
+            HalfSweepArgs a{};
+            for (int i = 0; i < 8; ++i) {
+                a.nin[i] = h->hbuf[h->hcur][i];
+                a.nout[i] = h->hbuf[1 - h->hcur][i];
+            }
+            a.Rin = h->Rh[h->hcur];
+            a.Rout = h->Rh[1 - h->hcur];
+            a.inv_tau = h->inv_tau;
+            a.Fp = h->Fp;
+            a.partials = h->partials;
+            a.shift = h->shift;
+            a.scale = h->hscale;
+            a.scale_out = h->hscale;
+            for (int s = 0; s < 4; ++s)
+                a.Pb[s] = h->Pb[s];
+            a.g = h->geom;
+            a.w = h->wells;
+            lbm2p_launch::pressure_sweep_h(a, final_check && kk == upto, h->grid_h, h->stream);
+            LAUNCHED(h, "FP16 pressure sweep");
+            h->hcur = 1 - h->hcur;
+            h->sweeps += 1;
+        }
+        k = upto;
+        if (h->timing) {
+            float ms = 0.0f;
+            CUDA_TRY(h, cudaEventRecord(h->ev_sw1, st));
+            CUDA_TRY(h, cudaEventSynchronize(h->ev_sw1));
+            CUDA_TRY(h, cudaEventElapsedTime(&ms, h->ev_sw0, h->ev_sw1));
+            ms_total += ms;
+        }
+        return LBM2P_OK;
+    };
+    auto read_residual = [&]() -> lbm2p_status {
+        lbm2p_launch::residual_finalize(h->partials, h->grid_h, h->nnodes, h->shift, h->res,
+                                        h->stream);
+        LAUNCHED(h, "residual finalize");
+        CUDA_TRY(h, cudaMemcpyAsync(h->res_host, h->res, sizeof(ResidualOut),
+                                    cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(h, cudaStreamSynchronize(st));
+        r = h->res_host->r;
+        return LBM2P_OK;
+    };
+    // keep the largest stored magnitude, as seen by the last check sweep, within [2^9, 2^14]
+    // of FP16's 2^16: otherwise multiply every stored value by a power of two (exact)
+    auto rescale = [&]() -> lbm2p_status {
+        CUDA_TRY(h, cudaMemcpyAsync(h->hscale_host, h->hscale, 4 * sizeof(float),
+                                    cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(h, cudaStreamSynchronize(st));
+        const float s = h->hscale_host[0], M = h->hscale_host[3];
+        CUDA_TRY(h, cudaMemsetAsync(h->hscale + 3, 0, sizeof(float), st));
+        if (!(M > 0.0f) || !std::isfinite(M) || (M >= 512.0f && M <= 16384.0f))
+            return LBM2P_OK;
+        int ex = 0;
+        std::frexp(M, &ex);
+        const float factor = std::ldexp(1.0f, 12 - ex);
+        const float sn = s * factor;
+        if (!(sn > 0.0f) || !std::isfinite(sn))
+            return LBM2P_OK;
+        lbm2p_launch::half_rescale(convert_args(h->hcur), factor, h->grid, h->stream);
+        LAUNCHED(h, "FP16 rescale");
+        h->hscale_host[0] = sn;
+        h->hscale_host[1] = 1.0f / sn;
+        CUDA_TRY(h, cudaMemcpyAsync(h->hscale, h->hscale_host, 2 * sizeof(float),
+                                    cudaMemcpyHostToDevice, st));
+        CUDA_TRY(h, cudaStreamSynchronize(st));
+        return LBM2P_OK;
+    };
+    lbm2p_status e;
+    if (replay >= 0) {
+        // long replays are cut into chunks of 256 sweeps ending in a check sweep, for the
+        // rescale (the residual of intermediate chunks is not read)
+        while (k + 256 < replay) {
+            if ((e = sweeps(k + 256, true)) != LBM2P_OK)
+                return e;
+            if ((e = rescale()) != LBM2P_OK)
+                return e;
+        }
+        if ((e = sweeps(replay, replay >= 2)) != LBM2P_OK)
+            return e;
+        if (replay >= 2) {
+            if ((e = read_residual()) != LBM2P_OK)
+                return e;
+            if (std::isnan(r))
+                status = LBM2P_ENONFINITE;
+        }
+    } else {
+        for (;;) {
+            int next = (k / m + 1) * m;
+            next = next > cap ? cap : next;
+            next = next < 1 ? 1 : next;
+            if ((e = sweeps(next, next >= 2)) != LBM2P_OK)
+                return e;
+            if (k >= 2) {
+                if ((e = read_residual()) != LBM2P_OK)
+                    return e;
+                if (std::isnan(r)) {
+                    status = LBM2P_ENONFINITE;
+                    break;
+                }
+                if (r <= h->p.tol)
+                    break;
+            }
+            if (k >= cap) {
+                status = LBM2P_ENOTCONVERGED;
+                break;
+            }
+            if (k >= 2 && (e = rescale()) != LBM2P_OK)
+                return e;
+        }
+    }
+    lbm2p_launch::half_widen(convert_args(h->hcur), h->grid, h->stream);
+    LAUNCHED(h, "FP16 widen");
+    if (k_out)
+        *k_out = k;
+    if (r_out)
+        *r_out = r;
+    if (ms_out)
+        *ms_out = h->timing ? ms_total : -1.0f;
+    if (status == LBM2P_ENONFINITE)
+        return fail(h, status, "pressure residual is not finite after %d sweeps", k);
+    if (status == LBM2P_ENOTCONVERGED)
+        return fail(h, status, "pressure residual %.3e above tol %.3e after %d sweeps", r,
+                    h->p.tol, k);
+    return LBM2P_OK;
+}
+
 lbm2p_status pressure_solve(lbm2p *h, int replay, int *k_out, double *r_out, float *ms_out)
 {
+    if (h->fp16)
+        return pressure_solve_h(h, replay, k_out, r_out, ms_out);
     cudaStream_t st = (cudaStream_t)h->stream;
     const int m = h->p.check_every;
     const int cap = h->p.max_sub_iters;
@@ -658,6 +822,10 @@ lbm2p_status check_params(const lbm2p_params *p, const lbm2p_inputs *in)
         return fail(nullptr, LBM2P_EINVAL, "phi and beta must be positive");
     if (!(p->D_s > 0))
         return fail(nullptr, LBM2P_EINVAL, "D_s must be positive (tau_g > 1/2)");
+    if (p->sat_lattice != 9 && p->sat_lattice != 5)
+        return fail(nullptr, LBM2P_EINVAL, "sat_lattice must be 9 or 5 (got %d)", p->sat_lattice);
+    if (!(p->D_c >= 0) || !std::isfinite(p->D_c))
+        return fail(nullptr, LBM2P_EINVAL, "D_c must be finite and >= 0");
     if (p->mobility == LBM2P_MOB_QUADRATIC) {
         if (!(p->mu_w > 0) || !(p->mu_n > 0))
             return fail(nullptr, LBM2P_EINVAL, "quadratic mobility needs mu_w, mu_n > 0");
@@ -689,9 +857,7 @@ lbm2p_status check_params(const lbm2p_params *p, const lbm2p_inputs *in)
         return fail(nullptr, LBM2P_EINVAL, "fuse_sweeps must be 0, 1, 2 or 4");
     if (p->sweep_kernel < LBM2P_SWEEP_AUTO || p->sweep_kernel > LBM2P_SWEEP_ROWS)
         return fail(nullptr, LBM2P_EINVAL, "sweep_kernel must be an lbm2p_sweep_kernel value");
-    if (p->storage == LBM2P_STORE_FP16_DEV)
-        return fail(nullptr, LBM2P_ENOTIMPL, "FP16 deviation storage is not available");
-    if (p->storage != LBM2P_STORE_FP32)
+    if (p->storage != LBM2P_STORE_FP32 && p->storage != LBM2P_STORE_FP16_DEV)
         return fail(nullptr, LBM2P_EINVAL, "unknown storage %d", p->storage);
     if (!in->K || !in->S0)
         return fail(nullptr, LBM2P_EINVAL, "K and S0 are required");
@@ -936,11 +1102,25 @@ lbm2p_status build(lbm2p *h, const lbm2p_inputs *in, lbm2p_step_stats *init_stat
     m.gam_c = (float)(3.0 * p.dt / (p.dx * p.dx));
     m.inv_dx = (float)(1.0 / p.dx);
     // Eq. 3-4: g_i^eq / S = w_i [phi + (beta - phi)(|c_i|^2 - 2 c_s^2) / (2 c_s^2)], c_s^2 = 1/3
+    m.qs = p.sat_lattice;
     for (int i = 0; i < 9; ++i) {
         const double w = i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
         const double c2 = (double)(cx(i) * cx(i) + cy(i) * cy(i));
         m.Gam[i] = (float)(w * (p.phi + (p.beta - p.phi) * (c2 - 2.0 / 3.0) / (2.0 / 3.0)));
+        m.wg[i] = (float)w;
     }
+    if (p.sat_lattice == 5) {
+        // D2Q5 (Remark V): weights 1/3 and 1/6; Eq. 3-4b: g_0^eq / S = (w_0 - 1) beta + phi,
+        // g_i^eq / S = w_i beta
+        for (int i = 0; i < 9; ++i) {
+            const double w = i == 0 ? 1.0 / 3.0 : (i <= 4 ? 1.0 / 6.0 : 0.0);
+            m.wg[i] = (float)w;
+            m.Gam[i] = (float)(i == 0 ? (w - 1.0) * p.beta + p.phi : w * p.beta);
+        }
+    }
+    m.var_ds = p.D_c != 0.0 ? 1 : 0;
+    m.ds_a0 = (float)(3.0 * p.D_s * p.dt / (p.beta * p.dx * p.dx));
+    m.ds_a1 = (float)(3.0 * p.D_c * p.dt / (p.beta * p.dx * p.dx));
     Wells &w = h->wells;
     w.n = in->n_wells;
     for (int k = 0; k < in->n_wells; ++k) {
@@ -996,15 +1176,33 @@ lbm2p_status build(lbm2p *h, const lbm2p_inputs *in, lbm2p_step_stats *init_stat
             ok = ok && h->Pb[s] && h->Sb[s];
         }
     }
+    h->fp16 = p.storage == LBM2P_STORE_FP16_DEV;
+    if (h->fp16) {
+        // FP16 copies of the populations and the per-sweep node pressures of a solve
+        for (int b = 0; b < 2; ++b) {
+            for (int i = 0; i < 8; ++i) {
+                h->hbuf[b][i] = (__half *)dev_alloc(h, (size_t)h->plane * sizeof(__half));
+                ok = ok && h->hbuf[b][i];
+            }
+            ok = ok && plane_alloc(&h->Rh[b]);
+        }
+        h->hscale = (float *)dev_alloc(h, 64);
+        ok = ok && h->hscale;
+        CUDA_TRY(h, cudaMallocHost((void **)&h->hscale_host, 4 * sizeof(float)));
+        h->grid_h = cap_grid((long long)sms * lbm2p_launch::max_blocks_per_sm_pressure_h());
+    }
     if (!ok)
         return fail(h, LBM2P_ENOMEM, "device allocation of %.1f MiB failed",
                     (double)pb * 45 / (1 << 20));
     // which single-sweep kernel, single or fused sweeps, and the fused tile shape: timed
-    // on this lattice (within what fuse_sweeps allows)
-    {
+    // on this lattice (within what fuse_sweeps allows); FP16 storage has one sweep kernel
+    if (!h->fp16) {
         lbm2p_status e = autotune_sweeps(h);
         if (e != LBM2P_OK)
             return e;
+    } else {
+        h->sweep_kind = 1;
+        h->tb_T = 0;
     }
     // grid-stride lattice kernels keep the one-node-per-thread capacity when the staged
     // sweep is chosen
@@ -1012,6 +1210,7 @@ lbm2p_status build(lbm2p *h, const lbm2p_inputs *in, lbm2p_step_stats *init_stat
     h->grid_check = h->grid_check_k[h->sweep_kind < 2 ? h->sweep_kind : 1];
     {
         int np = h->tb_grid > h->rows_grid ? h->tb_grid : h->rows_grid;
+        np = np > h->grid_h ? np : h->grid_h;
         for (int kind = 0; kind < 2; ++kind) {
             np = np > h->grid_k[kind] ? np : h->grid_k[kind];
             np = np > h->grid_check_k[kind] ? np : h->grid_check_k[kind];
@@ -1034,10 +1233,11 @@ lbm2p_status build(lbm2p *h, const lbm2p_inputs *in, lbm2p_step_stats *init_stat
     cudaStream_t st = (cudaStream_t)h->stream;
     for (auto &a : h->allocs)
         CUDA_TRY(h, cudaMemsetAsync(a.ptr, 0, a.bytes, st));
-    // a long solve moves R to the current P about every 1024 sweeps (at a check point)
-    h->rebase_every = p.check_every * ((1024 + p.check_every - 1) / p.check_every);
+    // a long solve moves R to the current P about every 1024 sweeps (at a check point);
+    // FP16 sweeps move it every sweep
+    h->rebase_every = h->fp16 ? 0 : p.check_every * ((1024 + p.check_every - 1) / p.check_every);
     // the loop body holds check_every sweeps and must return to the same f buffer
-    h->graph_ok = p.check_every >= 2 && p.check_every % 2 == 0 &&
+    h->graph_ok = !h->fp16 && p.check_every >= 2 && p.check_every % 2 == 0 &&
                   p.max_sub_iters % p.check_every == 0;
     if (h->tb_T > 1 && p.check_every % (2 * h->tb_T) != 0)
         h->tb_T_graph = 0;
@@ -1163,6 +1363,8 @@ void lbm2p_default_params(lbm2p_params *p)
     p->check_every = 8;
     p->fuse_sweeps = 0;
     p->sweep_kernel = LBM2P_SWEEP_AUTO;
+    p->sat_lattice = 9;
+    p->D_c = 0.0;
     for (int s = 0; s < 4; ++s)
         p->bc[s] = LBM2P_BC_NOFLUX;
     p->storage = LBM2P_STORE_FP32;

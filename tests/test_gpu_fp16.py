@@ -1,0 +1,98 @@
+"""FP16 storage of the pressure populations inside each sub-iteration (storage FP16_DEV)
+against the FP64 oracle: the oracle decides the sweep counts, the GPU replays them, every
+field within relative L2 2e-3 (the FP16 bar); on the five-spot (wells, no-flux walls),
+Example 2 (Dirichlet walls, moving sources) and the periodic manufactured problem."""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from test_gpu_parity import compare, run_pair
+
+pytestmark = pytest.mark.gpu
+
+TOL16 = 2e-3
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1808_07554_gb300 import build
+    build.build()
+    import paper_1808_07554_gb300 as pkg
+    pkg.load_library()
+
+
+def _run_pair16(prob, nsteps):
+    """run_pair with the GPU solver in FP16 storage: the oracle's counts replayed."""
+    import paper_1808_07554_gb300 as pkg
+    orc = O.Oracle(prob, tol=1e-8, check_every=8)
+    gpu = pkg.Solver.from_problem(prob, tol=1e-8, check_every=8, init_replay=orc.init_sub_iters,
+                                  storage=pkg.STORE_FP16_DEV)
+    for n in range(1, nsteps + 1):
+        t = n * prob.dt
+        if prob.sources_at is not None:
+            Fp, Fs = prob.sources_at(t)
+            orc.set_sources(Fp, Fs)
+            gpu.set_sources(Fp, Fs)
+        if prob.walls_at is not None:
+            Pb, Sb = prob.walls_at(t)
+            for s in range(4):
+                if prob.bc[s] == W.DIRICHLET:
+                    orc.set_dirichlet(s, Pb[s], Sb[s])
+                    gpu.set_dirichlet(s, Pb[s], Sb[s])
+        st, k, r = orc.step(1)
+        assert st == O.OK
+        gst, stats = gpu.step(1, replay=[int(k[0])])
+        assert stats[0].sub_iters == int(k[0])
+    return orc, gpu
+
+
+@pytest.mark.parametrize("name", ["five_spot_96", "example2_48", "manufactured_32"])
+def test_fp16_storage_matches_oracle(name):
+    prob = {"five_spot_96": lambda: W.quarter_five_spot(96, seed=8, corr_len=8.0),
+            "example2_48": lambda: W.example2(48),
+            "manufactured_32": lambda: W.manufactured_periodic(32, p_amp=0.2)}[name]()
+    orc, gpu = _run_pair16(prob, 8)
+    err = compare(orc, gpu, gauge_free=W.DIRICHLET not in prob.bc)
+    orc.close()
+    gpu.close()
+    assert all(v <= TOL16 for v in err.values()), err
+    print(name, err)
+
+
+def test_fp16_and_fp32_storage_agree_on_the_same_counts():
+    import paper_1808_07554_gb300 as pkg
+    prob = W.quarter_five_spot(128, seed=9, corr_len=12.0)
+    a = pkg.Solver.from_problem(prob, init_replay=3000)
+    b = pkg.Solver.from_problem(prob, init_replay=3000, storage=pkg.STORE_FP16_DEV)
+    counts = [512, 256, 256, 256]
+    a.step(len(counts), replay=counts)
+    b.step(len(counts), replay=counts)
+    Pa, Sa = a.fields(mean_free_P=True)
+    Pb, Sb = b.fields(mean_free_P=True)
+    assert W.rel_l2(Pb, Pa) <= TOL16 and W.rel_l2(Sb, Sa) <= TOL16
+
+
+def test_fp16_free_running_meets_a_loose_tolerance():
+    """Free-running with FP16 storage stops on the same stopping rule; FP16 rounding floors r
+    well above the FP32 1e-8, so a looser tolerance is used."""
+    import paper_1808_07554_gb300 as pkg
+    prob = W.quarter_five_spot(64, seed=10, corr_len=8.0)
+    s = pkg.Solver.from_problem(prob, tol=1e-5, check_every=8, max_sub_iters=400_000,
+                                storage=pkg.STORE_FP16_DEV)
+    st, stats = s.step(3)
+    assert st == pkg.OK
+    assert all(x.residual <= 1e-5 for x in stats)
+
+
+def test_fp16_member_is_refused_by_a_batch():
+    import paper_1808_07554_gb300 as pkg
+    prob = W.quarter_five_spot(32, seed=11)
+    a = pkg.Solver.from_problem(prob, init_replay=16)
+    b = pkg.Solver.from_problem(prob, init_replay=16, storage=pkg.STORE_FP16_DEV)
+    with pytest.raises(pkg.LBM2PError) as e:
+        pkg.Batch([a, b])
+    assert e.value.status == pkg.EINVAL
