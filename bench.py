@@ -55,7 +55,9 @@ SWEEP_KERNEL_NAMES = {1: "four nodes per thread (128-bit accesses)", 2: "one nod
                       3: "rows staged in shared memory by bulk async copies"}
 # DRAM bytes per pressure-sweep launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum),
 # keyed by workload; None until captured for the current kernel.
-NCU_TRAFFIC_PER_SWEEP = {"five_spot_1024": None, "five_spot_4096": None, "manufactured_64": None,
+# five_spot_1024: k_pressure_scalar<0,0> (the kernel the autotuner picks there), 42.0 MB read +
+# 0.9 MB written per launch, L2 flushed by ncu before the launch (profiles/).
+NCU_TRAFFIC_PER_SWEEP = {"five_spot_1024": 42.87e6, "five_spot_4096": None, "manufactured_64": None,
                          "batch_five_spot_64": None}
 
 
@@ -348,7 +350,10 @@ def run_ours(args):
     avg_launch_s = avg_sweep_s * fused
     bpn = BYTES_PER_SWEEP_NODE_FP16 if args.storage == "fp16" else BYTES_PER_SWEEP_NODE
     achieved = bpn * nodes / avg_launch_s / 1e9
-    traffic = NCU_TRAFFIC_PER_SWEEP.get(args.workload)
+    # the captured traffic belongs to the one-node-per-thread FP32 sweep; any other choice
+    # of the autotuner has no capture here
+    traffic = (NCU_TRAFFIC_PER_SWEEP.get(args.workload)
+               if args.storage == "fp32" and sweep_cfg[0] == 1 and sweep_cfg[1] == 2 else None)
     line = {
         "metric": "MLUPS", "value": updates_all / time_max / 1e6, "unit": "MLUPS",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -370,7 +375,8 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": ("pressure sweep (fused stream + collide, Eq. 3-1), "
-                                + ("FP16 populations, one node per thread" if args.storage == "fp16"
+                                + (("FP16 populations, " + SWEEP_KERNEL_NAMES.get(sweep_cfg[1], "?"))
+                                   if args.storage == "fp16"
                                    else (f"{fused} sweeps per launch" if fused > 1 else
                                          SWEEP_KERNEL_NAMES.get(sweep_cfg[1], "?"))
                                    + (", autotuned" if args.sweep_kernel == 0 else ""))),

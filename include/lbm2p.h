@@ -92,9 +92,11 @@ typedef enum { LBM2P_SWEEP_AUTO = 0, LBM2P_SWEEP_VEC4 = 1, LBM2P_SWEEP_SCALAR = 
  *             stored values are the post-collision non-equilibrium parts f_i^+ - w_i P), and
  *             widens the result back; arithmetic FP32, residual FP64; 44 B per node and
  *             sweep.  The state between steps stays FP32.  FP16 rounding puts a floor under
- *             the relative increment r: use a tolerance above it or replayed sweep counts.  Sweeps are launched from the host (no graph), by
- *             one one-node-per-thread kernel (lbm2p_sweep_config reports SCALAR); not
- *             available in batches. */
+ *             the relative increment r: use a tolerance above it or replayed sweep counts.
+ *             Sweeps are launched from the host (no graph) by an FP16 one-node-per-thread
+ *             kernel or an FP16 staged-rows kernel, timed at create (sweep_kernel SCALAR or
+ *             ROWS pins one; lbm2p_autotune_report lists "fp16_scalar" and "fp16_rows"
+ *             lines); not available in batches. */
 typedef enum { LBM2P_STORE_FP32 = 0, LBM2P_STORE_FP16_DEV = 1 } lbm2p_storage;
 
 /* A point well at node (i, j) with total rate q >= 0 (per unit depth): the node's cell

@@ -262,6 +262,12 @@ void half_narrow(const HalfConvertArgs &a, int grid, void *stream);
 void half_widen(const HalfConvertArgs &a, int grid, void *stream);
 void half_rescale(const HalfConvertArgs &a, float factor, int grid, void *stream);
 void pressure_sweep_h(const HalfSweepArgs &a, bool check, int grid, void *stream);
+// the FP16 staged-rows sweep (fp16.cu): shapes as for rows_* (width 128 or 256, slots 6 or 8)
+size_t rows_h_smem_bytes(int width, int slots, bool has_fp);
+cudaError_t rows_h_prepare(int width, int slots);
+int rows_h_blocks_per_sm(int width, int slots, bool has_fp);
+void pressure_sweep_rows_h(const HalfSweepArgs &a, bool check, int width, int slots, int H,
+                           int grid, void *stream);
 void refresh(const RefreshArgs &a, int grid, void *stream);
 void saturation(const SaturationArgs &a, int grid, void *stream);
 void init_g(const InitGArgs &a, int grid, void *stream);

@@ -40,7 +40,9 @@ struct lbm2p {
                                // [3] max |stored value| seen by the check sweeps
     float *hscale_host = nullptr;   // pinned copy
     int hcur = 0;
-    int grid_h = 0;
+    int grid_h = 0;            // one-node-per-thread FP16 sweep
+    int h16_kind = 0;          // FP16 sweep kernel: 0 one node per thread, 1 staged rows
+    int h16_w = 0, h16_slots = 0, h16_H = 0, h16_grid = 0;
     int rebase_every = 0;      // a long solve moves R to the current P after every this many
                                // sweeps (a multiple of check_every)
     void *stream = nullptr;

@@ -464,7 +464,12 @@ lbm2p_status pressure_solve_h(lbm2p *h, int replay, int *k_out, double *r_out, f
                 a.Pb[s] = h->Pb[s];
             a.g = h->geom;
             a.w = h->wells;
-            lbm2p_launch::pressure_sweep_h(a, final_check && kk == upto, h->grid_h, h->stream);
+            const bool check = final_check && kk == upto;
+            if (h->h16_kind == 1)
+                lbm2p_launch::pressure_sweep_rows_h(a, check, h->h16_w, h->h16_slots, h->h16_H,
+                                                    h->h16_grid, h->stream);
+            else
+                lbm2p_launch::pressure_sweep_h(a, check, h->grid_h, h->stream);
             LAUNCHED(h, "FP16 pressure sweep");
             h->hcur = 1 - h->hcur;
             h->sweeps += 1;
@@ -480,8 +485,8 @@ lbm2p_status pressure_solve_h(lbm2p *h, int replay, int *k_out, double *r_out, f
         return LBM2P_OK;
     };
     auto read_residual = [&]() -> lbm2p_status {
-        lbm2p_launch::residual_finalize(h->partials, h->grid_h, h->nnodes, h->shift, h->res,
-                                        h->stream);
+        lbm2p_launch::residual_finalize(h->partials, h->h16_kind == 1 ? h->h16_grid : h->grid_h,
+                                        h->nnodes, h->shift, h->res, h->stream);
         LAUNCHED(h, "residual finalize");
         CUDA_TRY(h, cudaMemcpyAsync(h->res_host, h->res, sizeof(ResidualOut),
                                     cudaMemcpyDeviceToHost, st));
@@ -1054,6 +1059,123 @@ done:
     return LBM2P_OK;
 }
 
+// FP16 storage: time the one-node-per-thread FP16 sweep and the FP16 staged-rows sweep over
+// its shapes on this lattice (zeroed buffers) and keep the fastest
+lbm2p_status autotune_h(lbm2p *h, int sms)
+{
+    cudaStream_t st = (cudaStream_t)h->stream;
+    cudaEvent_t e0, e1;
+    CUDA_TRY(h, cudaEventCreate(&e0));
+    CUDA_TRY(h, cudaEventCreate(&e1));
+    auto args = [&](int k) {
+        HalfSweepArgs a{};
+        for (int i = 0; i < 8; ++i) {
+            a.nin[i] = h->hbuf[k & 1][i];
+            a.nout[i] = h->hbuf[1 - (k & 1)][i];
+        }
+        a.Rin = h->Rh[k & 1];
+        a.Rout = h->Rh[1 - (k & 1)];
+        a.inv_tau = h->inv_tau;
+        a.Fp = h->Fp;
+        a.partials = h->partials;
+        a.shift = h->shift;
+        a.scale = h->hscale;
+        a.scale_out = h->hscale;
+        for (int s = 0; s < 4; ++s)
+            a.Pb[s] = h->Pb[s];
+        a.g = h->geom;
+        a.w = h->wells;
+        return a;
+    };
+    lbm2p_status status = LBM2P_OK;
+    const int reps = 6;
+    auto timed = [&](auto launch, float *ms) -> bool {
+        launch(0);
+        float best_ms = 1e30f;
+        for (int trial = 0; trial < 2; ++trial) {
+            cudaEventRecord(e0, st);
+            for (int rep = 0; rep < reps; ++rep)
+                launch(rep + 1);
+            cudaEventRecord(e1, st);
+            cudaError_t le = cudaEventSynchronize(e1);
+            if (le != cudaSuccess) {
+                status = fail(h, LBM2P_ECUDA, "FP16 sweep timing failed: %s", cudaGetErrorString(le));
+                return false;
+            }
+            float t = 0.0f;
+            cudaEventElapsedTime(&t, e0, e1);
+            best_ms = t < best_ms ? t : best_ms;
+        }
+        *ms = best_ms / reps;
+        return true;
+    };
+    char line[160];
+    float best = 1e30f;
+    const bool rows_only = h->p.sweep_kernel == LBM2P_SWEEP_ROWS;
+    const bool no_rows = h->p.sweep_kernel == LBM2P_SWEEP_SCALAR || h->p.sweep_kernel == LBM2P_SWEEP_VEC4;
+    h->h16_kind = 0;
+    {
+        float ms = 0.0f;
+        if (!timed([&](int k) { lbm2p_launch::pressure_sweep_h(args(k), false, h->grid_h, h->stream); },
+                   &ms))
+            goto done;
+        snprintf(line, sizeof line, "fp16_scalar %d 0 0 0 %.3f\n", h->grid_h, ms * 1e3f);
+        h->autotune_log += line;
+        best = rows_only ? 1e30f : ms;
+    }
+    if (!no_rows) {
+        const int shapes[3][2] = {{128, 8}, {256, 6}, {256, 8}};
+        for (const auto &sh : shapes) {
+            const int width = sh[0], slots = sh[1];
+            if (lbm2p_launch::rows_h_prepare(width, slots) != cudaSuccess) {
+                cudaGetLastError();
+                continue;
+            }
+            const int per_sm = lbm2p_launch::rows_h_blocks_per_sm(width, slots, h->Fp != nullptr);
+            if (per_sm < 1)
+                continue;
+            const int strips = (h->nx + width - 1) / width;
+            int last_H = -1;
+            for (int mult : {1, 2, 4, 8, 16}) {
+                long long chunks = ((long long)sms * per_sm * mult + strips - 1) / strips;
+                chunks = chunks < 1 ? 1 : chunks;
+                const int H = (int)((h->ny + chunks - 1) / chunks);
+                if (H == last_H)
+                    continue;
+                last_H = H;
+                const int grid = (int)lbm2p_launch::rows_grid(width, H, h->nx, h->ny);
+                float ms = 0.0f;
+                if (!timed([&](int k) {
+                        lbm2p_launch::pressure_sweep_rows_h(args(k), false, width, slots, H, grid,
+                                                            h->stream);
+                    }, &ms))
+                    goto done;
+                snprintf(line, sizeof line, "fp16_rows %d %d %d %d %.3f\n", width, slots, H, grid,
+                         ms * 1e3f);
+                h->autotune_log += line;
+                if (ms < best) {
+                    best = ms;
+                    h->h16_kind = 1;
+                    h->h16_w = width;
+                    h->h16_slots = slots;
+                    h->h16_H = H;
+                    h->h16_grid = grid;
+                }
+            }
+        }
+    }
+done:
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (status != LBM2P_OK)
+        return status;
+    CUDA_TRY(h, cudaGetLastError());
+    for (auto &a : h->allocs)
+        CUDA_TRY(h, cudaMemsetAsync(a.ptr, 0, a.bytes, st));
+    CUDA_TRY(h, cudaStreamSynchronize(st));
+    return LBM2P_OK;
+}
+
 lbm2p_status build(lbm2p *h, const lbm2p_inputs *in, lbm2p_step_stats *init_stats)
 {
     const lbm2p_params &p = h->p;
@@ -1203,6 +1325,9 @@ lbm2p_status build(lbm2p *h, const lbm2p_inputs *in, lbm2p_step_stats *init_stat
     } else {
         h->sweep_kind = 1;
         h->tb_T = 0;
+        lbm2p_status e = autotune_h(h, sms);
+        if (e != LBM2P_OK)
+            return e;
     }
     // grid-stride lattice kernels keep the one-node-per-thread capacity when the staged
     // sweep is chosen
@@ -1211,6 +1336,7 @@ lbm2p_status build(lbm2p *h, const lbm2p_inputs *in, lbm2p_step_stats *init_stat
     {
         int np = h->tb_grid > h->rows_grid ? h->tb_grid : h->rows_grid;
         np = np > h->grid_h ? np : h->grid_h;
+        np = np > h->h16_grid ? np : h->h16_grid;
         for (int kind = 0; kind < 2; ++kind) {
             np = np > h->grid_k[kind] ? np : h->grid_k[kind];
             np = np > h->grid_check_k[kind] ? np : h->grid_check_k[kind];
@@ -1588,6 +1714,15 @@ lbm2p_status lbm2p_sweep_config(const lbm2p *h, int *fused, int *kind, int *tile
         return fail(nullptr, LBM2P_EINVAL, "NULL handle");
     if (fused)
         *fused = h->tb_T > 1 ? h->tb_T : 1;
+    if (h->fp16) {                       // the FP16 sweep kernels
+        if (kind)
+            *kind = h->h16_kind == 1 ? LBM2P_SWEEP_ROWS : LBM2P_SWEEP_SCALAR;
+        if (tile_w)
+            *tile_w = h->h16_kind == 1 ? h->h16_w : 0;
+        if (tile_h)
+            *tile_h = h->h16_kind == 1 ? h->h16_H : 0;
+        return LBM2P_OK;
+    }
     if (kind)
         *kind = h->sweep_kind + 1;        // internal 0, 1, 2 = VEC4, SCALAR, ROWS
     if (tile_w)

@@ -18,6 +18,7 @@
 
 #include <cstdint>
 
+#include "lbm2p_async.cuh"
 #include "lbm2p_device.cuh"
 #include "lbm2p_node.cuh"
 
@@ -27,60 +28,6 @@ namespace {
 constexpr int kRowsMaxPlanes = 11;            // n_1..n_8, R, 1/tau_f, F~_p (when present)
 constexpr int kRowsHalo = 4;                  // floats staged on each side of the strip
 constexpr int kRowsBarBytes = 128;            // mbarriers at the start of shared memory
-constexpr unsigned kWaitLimit = 1u << 22;     // try_wait polls before a block gives up
-
-__device__ __forceinline__ unsigned smem_u32(const void *ptr)
-{
-    return (unsigned)__cvta_generic_to_shared(ptr);
-}
-
-__device__ __forceinline__ void bar_init(uint64_t *bar, unsigned count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
-                 : "memory");
-}
-
-__device__ __forceinline__ void bar_arrive(uint64_t *bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ void bar_arrive_tx(uint64_t *bar, unsigned bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool bar_try_wait(uint64_t *bar, unsigned parity)
-{
-    unsigned ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ bool bar_wait_bounded(uint64_t *bar, unsigned parity)
-{
-    for (unsigned it = 0; it < kWaitLimit; ++it)
-        if (bar_try_wait(bar, parity))
-            return true;
-    return false;
-}
-
-__device__ __forceinline__ void bulk_g2s(float *dst, const float *src, unsigned bytes,
-                                         uint64_t *bar)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-        ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
 
 // Warp-specialised pipeline.  Warp CW is the producer: its lane 0 copies input row t into
 // slot t % S once the consumers have released the row that used it before (row t - S).

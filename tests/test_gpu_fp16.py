@@ -25,12 +25,12 @@ def gpu():
     pkg.load_library()
 
 
-def _run_pair16(prob, nsteps):
+def _run_pair16(prob, nsteps, kernel=0):
     """run_pair with the GPU solver in FP16 storage: the oracle's counts replayed."""
     import paper_1808_07554_gb300 as pkg
     orc = O.Oracle(prob, tol=1e-8, check_every=8)
     gpu = pkg.Solver.from_problem(prob, tol=1e-8, check_every=8, init_replay=orc.init_sub_iters,
-                                  storage=pkg.STORE_FP16_DEV)
+                                  storage=pkg.STORE_FP16_DEV, sweep_kernel=kernel)
     for n in range(1, nsteps + 1):
         t = n * prob.dt
         if prob.sources_at is not None:
@@ -50,17 +50,42 @@ def _run_pair16(prob, nsteps):
     return orc, gpu
 
 
+@pytest.mark.parametrize("kernel", [2, 3], ids=["scalar", "rows"])
 @pytest.mark.parametrize("name", ["five_spot_96", "example2_48", "manufactured_32"])
-def test_fp16_storage_matches_oracle(name):
+def test_fp16_storage_matches_oracle(name, kernel):
     prob = {"five_spot_96": lambda: W.quarter_five_spot(96, seed=8, corr_len=8.0),
             "example2_48": lambda: W.example2(48),
             "manufactured_32": lambda: W.manufactured_periodic(32, p_amp=0.2)}[name]()
-    orc, gpu = _run_pair16(prob, 8)
+    orc, gpu = _run_pair16(prob, 8, kernel)
     err = compare(orc, gpu, gauge_free=W.DIRICHLET not in prob.bc)
     orc.close()
     gpu.close()
     assert all(v <= TOL16 for v in err.values()), err
     print(name, err)
+
+
+@pytest.mark.parametrize("name", ["five_spot_300x140", "example2_40", "tiny_5x3"])
+def test_fp16_kernels_agree_bit_for_bit(name):
+    """The FP16 one-node-per-thread and staged-rows sweeps compute the same stored values."""
+    import paper_1808_07554_gb300 as pkg
+    from _problems import uniform
+    rng = np.random.default_rng(12)
+    prob = {"five_spot_300x140": lambda: W.quarter_five_spot(300, 140, seed=12, corr_len=6.0),
+            "example2_40": lambda: W.example2(40),
+            "tiny_5x3": lambda: uniform(5, 3, bc=(1, 1, 0, 0), Fp=rng.standard_normal((3, 5)),
+                                        K=np.exp(rng.standard_normal((3, 5))))}[name]()
+    a = pkg.Solver.from_problem(prob, init_replay=40, storage=pkg.STORE_FP16_DEV,
+                                sweep_kernel=pkg.SWEEP_SCALAR)
+    b = pkg.Solver.from_problem(prob, init_replay=40, storage=pkg.STORE_FP16_DEV,
+                                sweep_kernel=pkg.SWEEP_ROWS)
+    assert any(r[0] == "fp16_rows" for r in b.autotune_report())
+    assert np.array_equal(a.get_state(), b.get_state())
+    for n in (1, 7, 300):
+        ra = a.pressure_sweeps(n)
+        rb = b.pressure_sweeps(n)
+        assert np.array_equal(a.get_state(), b.get_state()), (name, n)
+        if n >= 2:
+            assert rb == pytest.approx(ra, rel=1e-3, abs=1e-30)
 
 
 def test_fp16_and_fp32_storage_agree_on_the_same_counts():
