@@ -93,16 +93,16 @@ class Oracle:
     """FP64 reference solver.  Arrays are [ny, nx] float64, row-major."""
 
     def __init__(self, prob, tol=1e-8, max_sub_iters=10_000_000, check_every=8,
-                 init_replay=None):
+                 init_replay=None, warm_start=0):
         lib = _load()
         self.lib = lib
         self.nx, self.ny = prob.nx, prob.ny
         self.prob = prob
         shape = (prob.ny, prob.nx)
-        ip = (C.c_int * 12)(prob.nx, prob.ny, prob.mobility, prob.tau_mode, int(max_sub_iters),
+        ip = (C.c_int * 13)(prob.nx, prob.ny, prob.mobility, prob.tau_mode, int(max_sub_iters),
                             int(check_every), *[int(b) for b in prob.bc],
                             -1 if init_replay is None else int(init_replay),
-                            int(getattr(prob, "sat_lattice", 9)))
+                            int(getattr(prob, "sat_lattice", 9)), int(warm_start))
         dpar = (C.c_double * 11)(prob.dx, prob.dt, prob.phi, prob.beta, prob.mu_w, prob.mu_n,
                                  prob.D_s, prob.tau_p, prob.D_ref, tol,
                                  float(getattr(prob, "D_c", 0.0)))
@@ -251,11 +251,11 @@ class Oracle:
 
 
 def run_problem(prob, nsteps=None, tol=1e-8, check_every=8, max_sub_iters=10_000_000,
-                replay=None, init_replay=None):
+                replay=None, init_replay=None, warm_start=0):
     """Run a workloads.Problem through the oracle, updating time-dependent sources and
     wall values before each step.  Returns (oracle, sub_iters log [init, step1, ...])."""
     o = Oracle(prob, tol=tol, check_every=check_every, max_sub_iters=max_sub_iters,
-               init_replay=init_replay)
+               init_replay=init_replay, warm_start=warm_start)
     nsteps = prob.steps if nsteps is None else nsteps
     log = [o.init_sub_iters]
     for n in range(1, nsteps + 1):

@@ -38,6 +38,11 @@
  *    P_c = p_e (1 - S), Eq. 2-16 gives D_s = K lambda_n f_w p_e = p_e K lambda_w lambda_n /
  *    lambda_t; the model uses D_s(x, S) = D_s + D_c K lambda_w lambda_n / lambda_t
  *    (D_c = p_e; D_c = 0 is the constant case), so tau_g varies per node (Eq. 3-11b).
+ *  - warm start (optional): before a step's pressure solve the equilibrium part of f moves
+ *    by f^eq(P^n - P^{n-1}) (Eq. 3-3), i.e. the iteration starts from the pressure
+ *    extrapolated linearly in time, 2 P^n - P^{n-1}, with the previous non-equilibrium part
+ *    kept; P^n is the pressure of the last pull of step n.  The fixed point of every solve
+ *    is unchanged; only the starting iterate moves.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -80,6 +85,8 @@ typedef struct orc {
     double *Fp, *Fs;                   /* dense physical sources (may be all zero) */
     double *Fs_t;                      /* dt * F_s at the current step, wells included */
     double *S, *P, *Pprev, *gxX, *gyX; /* S^n, P from the last pull, previous-sweep P, lattice grad P */
+    int warm_start;                    /* 1: start each solve from the extrapolated pressure */
+    double *Pstep;                     /* P of the last pull of the previous step */
     double *Pb[4], *Sb[4];             /* Dirichlet wall traces, 2n+1 half-spaced values */
     int nw;
     int *wi, *wj, *wprod;
@@ -494,6 +501,7 @@ void orc_destroy(orc *o)
     free(o->S);
     free(o->P);
     free(o->Pprev);
+    free(o->Pstep);
     free(o->gxX);
     free(o->gyX);
     for (int s = 0; s < 4; ++s) {
@@ -599,13 +607,26 @@ static int initialise(orc *o, const double *P0, const double *S0, int init_repla
         o->S[a] = (s + 0.5 * o->Fs_t[a]) / o->phi;
     }
     collide_g(o);
+    memcpy(o->Pstep, o->P, o->n * sizeof(double));
     o->step = 0;
     return st;
 }
 
+/* Warm start of a solve: f_i^+ += f_i^eq(P^n - P^{n-1}) (Eq. 3-3: (omega_0 - 1) dP for
+   i = 0, omega_i dP otherwise), then remember P^n. */
+static void extrapolate_start(orc *o)
+{
+    for (size_t a = 0; a < o->n; ++a) {
+        double dP = o->P[a] - o->Pstep[a];
+        for (int i = 0; i < 9; ++i)
+            o->f[i][a] += (i == 0 ? o->w[0] - 1.0 : o->w[i]) * dP;
+        o->Pstep[a] = o->P[a];
+    }
+}
+
 /* Create the oracle and run the t = 0 initialisation.
    iparams: nx, ny, mobility, tau_mode, max_sub, check_every, bc[4], init_replay,
-            saturation lattice (9 or 5) (12 ints)
+            saturation lattice (9 or 5), warm start (0 or 1) (13 ints)
    dparams: dx, dt, phi, beta, mu_w, mu_n, D_s, tau_p, D_ref, tol, D_c (11 doubles)
    wells:   nw entries of (i, j, is_producer) in wint and q in wq. */
 orc *orc_create(const int *iparams, const double *dparams, const double *K, const double *S0,
@@ -633,6 +654,7 @@ orc *orc_create(const int *iparams, const double *dparams, const double *K, cons
         o->bc[s] = iparams[6 + s];
     int init_replay = iparams[10];
     o->qs = iparams[11];
+    o->warm_start = iparams[12];
     o->dx = dparams[0];
     o->dt = dparams[1];
     o->phi = dparams[2];
@@ -669,6 +691,7 @@ orc *orc_create(const int *iparams, const double *dparams, const double *K, cons
     ALLOC(o->S);
     ALLOC(o->P);
     ALLOC(o->Pprev);
+    ALLOC(o->Pstep);
     ALLOC(o->gxX);
     ALLOC(o->gyX);
 #undef ALLOC
@@ -744,6 +767,8 @@ int orc_step(orc *o, int nsteps, const int *replay, int *k_out, double *r_out)
     int worst = ORC_OK;
     for (int s = 0; s < nsteps; ++s) {
         orc_refresh(o);
+        if (o->warm_start)
+            extrapolate_start(o);
         int k;
         double r;
         int st = pressure_solve(o, replay ? replay[s] : -1, &k, &r);
