@@ -271,7 +271,8 @@ def run_ours(args):
     solver = pkg.Solver.from_problem(prob, tol=args.tol, check_every=args.check_every,
                                      max_sub_iters=args.max_sub_iters, fuse_sweeps=args.fuse_sweeps,
                                      sweep_kernel=args.sweep_kernel,
-                                     storage=1 if args.storage == "fp16" else 0)
+                                     storage=1 if args.storage == "fp16" else 0,
+                                     warm_start=1 if args.warm_start == "extrapolate" else 0)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t_setup
     init_sweeps = solver.init_stats.sub_iters
@@ -361,7 +362,7 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32" if args.storage == "fp32" else "f16 storage, f32 arithmetic",
         "data": "synthetic",
         "config": {"workload": args.workload, "nx": prob.nx, "ny": prob.ny, "tol": args.tol,
-                   "storage": args.storage,
+                   "storage": args.storage, "warm_start": args.warm_start,
                    "check_every": args.check_every, "fuse_sweeps": args.fuse_sweeps,
                    "sweep_kernel": sweep_cfg[1], "sweep_tile": [sweep_cfg[2], sweep_cfg[3]],
                    "l2": "flushed before every timed step",
@@ -436,7 +437,8 @@ def run_batch(args):
                 p.P0 = P0
         s = pkg.Solver.from_problem(p, tol=1e-8, check_every=args.check_every,
                                     max_sub_iters=args.max_sub_iters,
-                                    sweep_kernel=args.sweep_kernel)
+                                    sweep_kernel=args.sweep_kernel,
+                                    warm_start=1 if args.warm_start == "extrapolate" else 0)
         init_sweeps += s.init_stats.sub_iters
         solvers.append(s)
     torch.cuda.synchronize()
@@ -516,6 +518,7 @@ def run_batch(args):
         "config": {"workload": args.workload, "members": len(probs),
                    "sizes": {f"{n}x{n}": c for n, c in sizes.items()},
                    "nodes": int(nodes.sum()), "tol": 1e-8, "check_every": args.check_every,
+                   "warm_start": args.warm_start,
                    "l2": "flushed before every timed step",
                    "sub_iters_max_per_step": [int(x) for x in k.max(axis=1)],
                    "sub_iters_mean_per_step": [round(float(x), 1) for x in k.mean(axis=1)],
@@ -558,6 +561,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fuse-sweeps", type=int, default=0, choices=[0, 1, 2, 4],
                     help="pressure sweeps per launch: 0 = autotuned, 1, 2 or 4")
+    ap.add_argument("--warm-start", choices=["none", "extrapolate"], default="none",
+                    help="start of each pressure solve: the previous step's populations (none) "
+                         "or their equilibrium part moved to 2 P^n - P^(n-1) (extrapolate)")
     ap.add_argument("--storage", choices=["fp32", "fp16"], default="fp32",
                     help="pressure populations during the sub-iteration: FP32 or FP16 deviations")
     ap.add_argument("--tol", type=float, default=1e-8,

@@ -42,7 +42,7 @@
 extern "C" {
 #endif
 
-#define LBM2P_ABI_VERSION 4
+#define LBM2P_ABI_VERSION 5
 /* Sparse wells passed to the sweep kernels as launch arguments (more wells: error). */
 #define LBM2P_MAX_WELLS 16
 
@@ -136,6 +136,13 @@ typedef struct {
                                    D_s(x, S) = D_s + D_c K lambda_w lambda_n / lambda_t, the
                                    D_s of Eq. 2-16 with a linear capillary pressure of scale
                                    D_c; tau_g then varies per node (Eq. 3-11b).  0: constant */
+    int warm_start;             /* start of each step's pressure solve.  0: the previous
+                                   step's populations as they are (continuation, the paper's
+                                   pseudo-time reading).  1: their equilibrium part moved to the
+                                   pressure extrapolated linearly in time, 2 P^n - P^{n-1}
+                                   (f_i += f_i^eq(P^n - P^{n-1}), Eq. 3-3), the non-equilibrium
+                                   part kept.  Each solve still runs to the same stopping rule;
+                                   only its starting iterate changes (far fewer sweeps). */
     void *stream;               /* cudaStream_t the work is enqueued on */
     void *(*alloc)(size_t bytes, void *ctx);            /* optional device allocator */
     void (*release)(void *ptr, size_t bytes, void *ctx); /* its matching free */
@@ -221,6 +228,14 @@ size_t lbm2p_state_count(const lbm2p *h);
 /* Copy the state out / in (checkpoint and restart; count must equal lbm2p_state_count). */
 lbm2p_status lbm2p_get_state(lbm2p *h, float *buf, size_t count, int on_device);
 lbm2p_status lbm2p_set_state(lbm2p *h, const float *buf, size_t count, int on_device);
+
+/* Warm start of the next pressure solve from a caller's pressure field (for instance a learned
+   predictor's): P_guess, ny*nx floats (device pointer if on_device, else host), becomes the
+   equilibrium part of the pressure populations (their non-equilibrium part is kept), exactly
+   as warm_start = 1 does with its extrapolated field.  The solve's stopping rule is unchanged.
+   A constant offset in P_guess is harmless where P is defined up to a constant (no Dirichlet
+   side).  Combined with warm_start = 1, the extrapolation is applied on top at the next step. */
+lbm2p_status lbm2p_warm_start(lbm2p *h, const float *P_guess, int on_device);
 
 /* Record CUDA events around each step and its sweeps (fills sweep_ms / step_ms). */
 lbm2p_status lbm2p_set_timing(lbm2p *h, int enable);

@@ -46,6 +46,7 @@ class lbm2p_params(C.Structure):
                 ("tol", C.c_double), ("max_sub_iters", C.c_int), ("check_every", C.c_int),
                 ("bc", C.c_int * 4), ("storage", C.c_int), ("fuse_sweeps", C.c_int),
                 ("sweep_kernel", C.c_int), ("sat_lattice", C.c_int), ("D_c", C.c_double),
+                ("warm_start", C.c_int),
                 ("stream", C.c_void_p),
                 ("alloc", ALLOC_FN), ("release", RELEASE_FN), ("alloc_ctx", C.c_void_p)]
 
@@ -105,6 +106,7 @@ def load_library(path: str = LIB_PATH):
         "lbm2p_counters": (C.c_int, [H, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
         "lbm2p_sweep_config": (C.c_int, [H] + [C.POINTER(C.c_int)] * 4),
         "lbm2p_autotune_report": (C.c_char_p, [H]),
+        "lbm2p_warm_start": (C.c_int, [H, fp, C.c_int]),
         "lbm2p_pressure_sweep_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int),
                                                    C.POINTER(fp), C.POINTER(fp), fp, fp, fp,
                                                    C.POINTER(fp), fp, C.POINTER(C.c_double),
@@ -347,7 +349,7 @@ class Solver:
                  tau_p, bc, K, S0, P0=None, Fp=None, Fs=None, wells=(), P_b=None, S_b=None,
                  D_ref=0.0, tol=1e-8, max_sub_iters=10_000_000, check_every=8,
                  init_replay=None, use_torch=True, stream=None, fuse_sweeps=0,
-                 sweep_kernel=0, sat_lattice=9, D_c=0.0, storage=0):
+                 sweep_kernel=0, sat_lattice=9, D_c=0.0, storage=0, warm_start=0):
         lib = _lib_or_raise()
         self.nx, self.ny = int(nx), int(ny)
         n = self.nx * self.ny
@@ -362,6 +364,7 @@ class Solver:
         p.sweep_kernel = int(sweep_kernel)
         p.sat_lattice = int(sat_lattice)
         p.storage = int(storage)
+        p.warm_start = int(warm_start)
         p.D_c = float(D_c)
         for s in range(4):
             p.bc[s] = int(bc[s])
@@ -446,6 +449,11 @@ class Solver:
     def set_sources(self, Fp=None, Fs=None):
         n = self.nx * self.ny
         lbm2p_set_sources(self.h, _f64(Fp, n), _f64(Fs, n))
+
+    def warm_start(self, P_guess):
+        """Start the next pressure solve from the pressure field P_guess ([ny, nx])."""
+        buf = np.ascontiguousarray(P_guess, dtype=np.float32).reshape(self.ny, self.nx)
+        _check(_lib_or_raise().lbm2p_warm_start(self.h, _fp(buf), 0), self.h)
 
     def set_dirichlet(self, side, P_b=None, S_b=None):
         lbm2p_set_dirichlet(self.h, side, P_b, S_b)

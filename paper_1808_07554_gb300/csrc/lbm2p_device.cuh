@@ -285,6 +285,10 @@ cudaError_t node_finalize_loop(cudaGraphNode_t *n, cudaGraph_t g, const cudaGrap
                                ResidualOut *out, LoopCtl *ctl, cudaGraphConditionalHandle h,
                                cudaGraphConditionalHandle h_rebase);
 void rebase_mid(const RebaseMidArgs &a, int grid, void *stream);
+// warm start: R <- 2 R - Pstep, Pstep <- R (node-local)
+void extrapolate(float *R, float *Pstep, Geom g, int grid, void *stream);
+cudaError_t node_extrapolate(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
+                             float *R, float *Pstep, Geom geom, int grid);
 cudaError_t node_rebase_mid(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
                             const RebaseMidArgs &a, int grid);
 cudaError_t node_loop_reset(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,

@@ -51,6 +51,7 @@ struct lbm2p {
     float *gbuf[2][9] = {};
     float *inv_tau = nullptr, *K = nullptr, *S = nullptr, *Pio = nullptr, *tmp = nullptr;
     float *R = nullptr;                // reference pressure of the pressure populations
+    float *Pstep = nullptr;            // warm start: the node pressure of the previous step
     float *Fp = nullptr, *Fs = nullptr;
     float *Pb[4] = {}, *Sb[4] = {};
     double *partials = nullptr, *mean = nullptr;

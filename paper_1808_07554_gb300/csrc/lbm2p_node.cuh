@@ -320,6 +320,15 @@ __device__ __forceinline__ void rebase_mid_node(const RebaseMidArgs &a, int o)
     a.R[o] = a.R[o] + dP;
 }
 
+// Warm start of a solve: the equilibrium part of f_i = n_i + w_i R moves with R to the
+// pressure extrapolated in time, R' = R + (R - P^{n-1}); n_i (the rest) is kept.
+__device__ __forceinline__ void extrapolate_node(float *R, float *Pstep, int o)
+{
+    const float r = R[o];
+    R[o] = r + (r - Pstep[o]);
+    Pstep[o] = r;
+}
+
 // a2: one node of a pressure sweep with scalar gathers; (d, q) feed the residual partials
 template <bool CHECK, bool WRITE_P>
 __device__ __forceinline__ void sweep_node(const PressureArgs &a, int x, int y, int o,

@@ -367,6 +367,12 @@ lbm2p_status step_graph(lbm2p *h, int pf, int pg, cudaGraphExec_t *out)
         h->step_g[pf][pg] = G;
         cudaGraphNode_t nr, last, ns;
         CUDA_TRY(h, lbm2p_launch::node_refresh(&nr, G, nullptr, refresh_args(h, pg), h->grid));
+        if (h->p.warm_start) {
+            cudaGraphNode_t nx;
+            CUDA_TRY(h, lbm2p_launch::node_extrapolate(&nx, G, &nr, h->R, h->Pstep, h->geom,
+                                                       h->grid));
+            nr = nx;
+        }
         lbm2p_status e = add_loop(h, G, &nr, pf, &last);
         if (e != LBM2P_OK)
             return e;
@@ -756,7 +762,7 @@ lbm2p_status one_step(lbm2p *h, int replay, lbm2p_step_stats *stats)
         float sw_ms = -1.0f, step_ms = -1.0f;
         if ((e = read_loop(h, &k, &r, &sw_ms)) != LBM2P_OK)
             return e;
-        h->launches += 3;                 // refresh, saturation, rebase
+        h->launches += 3 + (h->p.warm_start ? 1 : 0);   // refresh, (warm start,) saturation, rebase
         h->cur_g = 1 - h->cur_g;
         if (h->timing)
             CUDA_TRY(h, cudaEventElapsedTime(&step_ms, h->ev_step0, h->ev_step1));
@@ -775,6 +781,10 @@ lbm2p_status one_step(lbm2p *h, int replay, lbm2p_step_stats *stats)
     // a1: stream g, S^n, tau_f
     lbm2p_launch::refresh(refresh_args(h, h->cur_g), h->grid, h->stream);
     LAUNCHED(h, "refresh");
+    if (h->p.warm_start) {
+        lbm2p_launch::extrapolate(h->R, h->Pstep, h->geom, h->grid, h->stream);
+        LAUNCHED(h, "warm start");
+    }
     // a2/a3: pressure sub-iteration
     int k = 0;
     double r = std::nan("");
@@ -827,6 +837,8 @@ lbm2p_status check_params(const lbm2p_params *p, const lbm2p_inputs *in)
         return fail(nullptr, LBM2P_EINVAL, "phi and beta must be positive");
     if (!(p->D_s > 0))
         return fail(nullptr, LBM2P_EINVAL, "D_s must be positive (tau_g > 1/2)");
+    if (p->warm_start != 0 && p->warm_start != 1)
+        return fail(nullptr, LBM2P_EINVAL, "warm_start must be 0 or 1");
     if (p->sat_lattice != 9 && p->sat_lattice != 5)
         return fail(nullptr, LBM2P_EINVAL, "sat_lattice must be 9 or 5 (got %d)", p->sat_lattice);
     if (!(p->D_c >= 0) || !std::isfinite(p->D_c))
@@ -1287,6 +1299,8 @@ lbm2p_status build(lbm2p *h, const lbm2p_inputs *in, lbm2p_step_stats *init_stat
     }
     ok = ok && plane_alloc(&h->inv_tau) && plane_alloc(&h->K) && plane_alloc(&h->S) &&
          plane_alloc(&h->Pio) && plane_alloc(&h->tmp) && plane_alloc(&h->R);
+    if (p.warm_start)
+        ok = ok && plane_alloc(&h->Pstep);
     if (in->Fp)
         ok = ok && plane_alloc(&h->Fp);
     if (in->Fs)
@@ -1443,6 +1457,9 @@ lbm2p_status build(lbm2p *h, const lbm2p_inputs *in, lbm2p_step_stats *init_stat
     LAUNCHED(h, "init g");
     lbm2p_launch::rebase(rebase_args(h, h->cur_f), h->grid, h->stream);
     LAUNCHED(h, "rebase");
+    if (h->Pstep)                      // no history yet: the first step extrapolates nothing
+        CUDA_TRY(h, cudaMemcpyAsync(h->Pstep, h->R, (size_t)h->plane * sizeof(float),
+                                    cudaMemcpyDeviceToDevice, st));
     h->cur_g = 0;
     CUDA_TRY(h, cudaStreamSynchronize(st));
     return ps;
@@ -1490,6 +1507,7 @@ void lbm2p_default_params(lbm2p_params *p)
     p->fuse_sweeps = 0;
     p->sweep_kernel = LBM2P_SWEEP_AUTO;
     p->sat_lattice = 9;
+    p->warm_start = 0;
     p->D_c = 0.0;
     for (int s = 0; s < 4; ++s)
         p->bc[s] = LBM2P_BC_NOFLUX;
@@ -1686,6 +1704,25 @@ static lbm2p_status state_copy(lbm2p *h, float *buf, size_t count, int on_device
         else
             CUDA_TRY(h, cudaMemcpy2DAsync(planes[c], dpitch, hb, row, row, (size_t)h->ny, kind, st));
     }
+    if (!out && h->Pstep)              // a new state has no history: no extrapolation next step
+        CUDA_TRY(h, cudaMemcpyAsync(h->Pstep, h->R, (size_t)h->plane * sizeof(float),
+                                    cudaMemcpyDeviceToDevice, st));
+    CUDA_TRY(h, cudaStreamSynchronize(st));
+    return LBM2P_OK;
+}
+
+lbm2p_status lbm2p_warm_start(lbm2p *h, const float *P_guess, int on_device)
+{
+    if (!h)
+        return fail(nullptr, LBM2P_EINVAL, "NULL handle");
+    if (!P_guess)
+        return fail(h, LBM2P_EINVAL, "P_guess must not be NULL");
+    cudaStream_t st = (cudaStream_t)h->stream;
+    const size_t row = (size_t)h->nx * sizeof(float);
+    CUDA_TRY(h, cudaMemcpy2DAsync(h->R, (size_t)h->pitch * sizeof(float), P_guess, row, row,
+                                  (size_t)h->ny,
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                  st));
     CUDA_TRY(h, cudaStreamSynchronize(st));
     return LBM2P_OK;
 }

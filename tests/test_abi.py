@@ -37,11 +37,12 @@ def test_every_declared_function_is_exported(lib):
 
 def test_abi_version_and_defaults(lib):
     import paper_1808_07554_gb300 as pkg
-    assert pkg.lbm2p_abi_version() == 4
+    assert pkg.lbm2p_abi_version() == 5
     p = pkg.lbm2p_default_params()
     assert (p.phi, p.beta, p.mu_w, p.mu_n, p.D_s, p.tau_p, p.tol) == (0.2, 0.4, 1.0, 2.0, 0.01, 1.0, 1e-8)
     assert p.check_every == 8 and list(p.bc) == [1, 1, 1, 1] and p.fuse_sweeps == 0
     assert p.sweep_kernel == pkg.SWEEP_AUTO and p.sat_lattice == 9 and p.D_c == 0.0
+    assert p.warm_start == 0
 
 
 def _inputs(pkg, n, K=None, S0=None):
@@ -57,7 +58,7 @@ def _inputs(pkg, n, K=None, S0=None):
     ("nx", 0, 1), ("dx", -1.0, 1), ("phi", 0.0, 1), ("D_s", 0.0, 1), ("tau_p", 0.5, 1),
     ("check_every", 0, 1), ("max_sub_iters", 0, 1), ("storage", 2, 1), ("mobility", 9, 1),
     ("tol", -1.0, 1), ("fuse_sweeps", 3, 1), ("sweep_kernel", 4, 1), ("sweep_kernel", -1, 1), ("sat_lattice", 7, 1),
-    ("D_c", -1.0, 1)])
+    ("D_c", -1.0, 1), ("warm_start", 2, 1)])
 def test_bad_parameters_are_rejected_without_a_device(lib, field, value, status):
     import paper_1808_07554_gb300 as pkg
     p = pkg.lbm2p_default_params()
