@@ -36,7 +36,6 @@ struct Member {
     SaturationArgs sa[2];
     RebaseArgs rb;
     RebaseMidArgs rm;            // mid-solve rebase of the f buffer holding the state
-    float *Pstep;                // warm start: previous step's node pressure (NULL: none)
     float *shift;                // the handle's residual conditioning constants
     long long nnodes;
     int nx, ny;
@@ -250,21 +249,6 @@ __global__ void __launch_bounds__(256) kb_scatter(const Member *__restrict__ mem
         act[base + i] = make_int2(m, i);
 }
 
-// warm start of the members that ask for it: R <- 2 R - Pstep, Pstep <- R
-__global__ void __launch_bounds__(kBlock) kb_extrapolate(const Member *__restrict__ mem,
-                                                         const int *__restrict__ tile_member,
-                                                         int total)
-{
-    for (int t = blockIdx.x; t < total; t += gridDim.x) {
-        const Member &M = mem[tile_member[t]];
-        if (!M.Pstep)
-            continue;                                   // uniform over the block
-        int x, y;
-        if (tile_node(M, t - M.tile0, x, y))
-            extrapolate_node(M.rb.R, M.Pstep, y * M.rb.g.pitch + x);
-    }
-}
-
 __global__ void __launch_bounds__(kBlock) kb_rebase_mid(const Member *__restrict__ mem,
                                                         const int *__restrict__ tile_member,
                                                         int total, const MemberCtl *__restrict__ ctl)
@@ -306,7 +290,6 @@ __global__ void __launch_bounds__(kBlock) kb_rebase(const Member *__restrict__ m
 }  // namespace
 
 struct lbm2p_batch {
-    bool any_warm = false;               // a member warm-starts its solves
     std::vector<lbm2p *> members;
     std::vector<int> pf, pg0;            // buffer parities the graphs were built for
     int count = 0, total = 0, body = 0, grid = 0, grid_check = 0;
@@ -428,12 +411,6 @@ lbm2p_status build_graph(lbm2p_batch *b, int q)
     {
         void *args[] = {(void *)&mem, (void *)&tm, (void *)&total, (void *)&q};
         BTRY(b, add_k(&nr, G, nullptr, (void *)kb_refresh, b->grid, kBlock, args));
-    }
-    if (b->any_warm) {
-        cudaGraphNode_t nx;
-        void *args[] = {(void *)&mem, (void *)&tm, (void *)&total};
-        BTRY(b, add_k(&nx, G, &nr, (void *)kb_extrapolate, b->grid, kBlock, args));
-        nr = nx;
     }
     {
         void *args[] = {(void *)&ctl, (void *)&caps, (void *)&tols, (void *)&count, (void *)&act};
@@ -562,8 +539,6 @@ lbm2p_status lbm2p_batch_create(lbm2p_batch **out, lbm2p *const *members, int co
         }
         M.rb = lbm2p_internal::rebase_args(h, h->cur_f);
         M.rm = lbm2p_internal::rebase_mid_args(h, h->cur_f);
-        M.Pstep = h->p.warm_start ? h->Pstep : nullptr;
-        b->any_warm = b->any_warm || h->p.warm_start;
         M.every = h->rebase_every;
         M.shift = h->shift;
         M.nnodes = h->nnodes;
@@ -713,8 +688,7 @@ lbm2p_status lbm2p_batch_step(lbm2p_batch *b, int nsteps, const int *replay,
         // finalize, condition + prefix, scatter; and the mid-solve rebases of the longest solve
         const int passes = kmax > 0 ? kmax / b->body : 1;
         const int every = b->body * ((1024 + b->body - 1) / b->body);
-        b->launches += 6 + (b->any_warm ? 1 : 0) + (long long)passes * (b->body + 3) +
-                       (kmax > 0 ? (kmax - 1) / every : 0);
+        b->launches += 6 + (long long)passes * (b->body + 3) + (kmax > 0 ? (kmax - 1) / every : 0);
         if (worst == LBM2P_ENONFINITE)
             return bfail(b, worst, "a member's pressure residual is not finite (step %d)", s);
     }

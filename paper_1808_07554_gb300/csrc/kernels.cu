@@ -768,16 +768,6 @@ __global__ void __launch_bounds__(kBlock) k_rebase_mid(const __grid_constant__ R
     }
 }
 
-__global__ void __launch_bounds__(kBlock) k_extrapolate(float *R, float *Pstep, Geom g)
-{
-    for (int t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
-        const int y = t / g.tiles_x;
-        const int x = (t - y * g.tiles_x) * kBlock + threadIdx.x;
-        if (x < g.nx)
-            extrapolate_node(R, Pstep, y * g.pitch + x);
-    }
-}
-
 __global__ void __launch_bounds__(kBlock) k_tau_from_S(float *inv_tau, const float *S,
                                                        const float *K, Geom g, Model m)
 {
@@ -974,11 +964,6 @@ void rebase(const RebaseArgs &a, int grid, void *stream)
     k_rebase<<<grid, kBlock, 0, S(stream)>>>(a);
 }
 
-void extrapolate(float *R, float *Pstep, Geom g, int grid, void *stream)
-{
-    k_extrapolate<<<grid, kBlock, 0, S(stream)>>>(R, Pstep, g);
-}
-
 void rebase_mid(const RebaseMidArgs &a, int grid, void *stream)
 {
     k_rebase_mid<<<grid, kBlock, 0, S(stream)>>>(a);
@@ -1087,13 +1072,6 @@ cudaError_t node_rebase(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t
 {
     void *args[] = {(void *)&a};
     return add_kernel(n, g, dep, (void *)k_rebase, grid, kBlock, args);
-}
-
-cudaError_t node_extrapolate(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
-                             float *R, float *Pstep, Geom geom, int grid)
-{
-    void *args[] = {(void *)&R, (void *)&Pstep, (void *)&geom};
-    return add_kernel(n, g, dep, (void *)k_extrapolate, grid, kBlock, args);
 }
 
 }  // namespace lbm2p_launch

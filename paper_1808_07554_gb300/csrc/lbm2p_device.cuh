@@ -103,8 +103,10 @@ struct PressureArgs {
     Wells w;
 };
 
-struct RefreshArgs {        // stream g, S^n, 1/tau_f
+struct RefreshArgs {        // stream g, S^n, 1/tau_f (and the warm start of the next solve)
     const float *gin[9];
+    float *R;                // warm start: R <- 2 R - Pstep, Pstep <- R  (Pstep NULL: none)
+    float *Pstep;
     const float *K;
     const float *Fs;         // dense F~_s plane or nullptr
     float *inv_tau;
@@ -285,10 +287,6 @@ cudaError_t node_finalize_loop(cudaGraphNode_t *n, cudaGraph_t g, const cudaGrap
                                ResidualOut *out, LoopCtl *ctl, cudaGraphConditionalHandle h,
                                cudaGraphConditionalHandle h_rebase);
 void rebase_mid(const RebaseMidArgs &a, int grid, void *stream);
-// warm start: R <- 2 R - Pstep, Pstep <- R (node-local)
-void extrapolate(float *R, float *Pstep, Geom g, int grid, void *stream);
-cudaError_t node_extrapolate(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
-                             float *R, float *Pstep, Geom geom, int grid);
 cudaError_t node_rebase_mid(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
                             const RebaseMidArgs &a, int grid);
 cudaError_t node_loop_reset(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,

@@ -236,7 +236,17 @@ __device__ __forceinline__ float warp_sum(float v)
 // --------------------------------------------------------------------------------------
 // per-node bodies shared by the single-lattice kernels and the batched kernels
 // --------------------------------------------------------------------------------------
-// a1: S^n (Eq. 3-9b) from the pulled g and 1/tau_f (Eq. 3-11a with D_p = K lambda_t(S))
+// Warm start of a solve: the equilibrium part of f_i = n_i + w_i R moves with R to the
+// pressure extrapolated in time, R' = R + (R - P^{n-1}); n_i (the rest) is kept.
+__device__ __forceinline__ void extrapolate_node(float *R, float *Pstep, int o)
+{
+    const float r = R[o];
+    R[o] = r + (r - Pstep[o]);
+    Pstep[o] = r;
+}
+
+// a1: S^n (Eq. 3-9b) from the pulled g and 1/tau_f (Eq. 3-11a with D_p = K lambda_t(S)); with
+// a warm start also the extrapolation of the node's reference pressure for the coming solve
 __device__ __forceinline__ void refresh_node(const RefreshArgs &a, int x, int y, int o)
 {
     float q[9];
@@ -247,6 +257,8 @@ __device__ __forceinline__ void refresh_node(const RefreshArgs &a, int x, int y,
     float lw, lt;
     mobility(a.m, S, lw, lt);
     a.inv_tau[o] = 1.0f / (0.5f + a.m.s3 * a.K[o] * lt);
+    if (a.Pstep)
+        extrapolate_node(a.R, a.Pstep, o);
 }
 
 // a4 + a5: local grad P (Eq. 3-10a), then the saturation collision (Eq. 3-2); also stores
@@ -318,15 +330,6 @@ __device__ __forceinline__ void rebase_mid_node(const RebaseMidArgs &a, int o)
     for (int i = 0; i < 8; ++i)
         a.n[i][o] = fmaf(-wgt(i + 1), dP, n[i]);
     a.R[o] = a.R[o] + dP;
-}
-
-// Warm start of a solve: the equilibrium part of f_i = n_i + w_i R moves with R to the
-// pressure extrapolated in time, R' = R + (R - P^{n-1}); n_i (the rest) is kept.
-__device__ __forceinline__ void extrapolate_node(float *R, float *Pstep, int o)
-{
-    const float r = R[o];
-    R[o] = r + (r - Pstep[o]);
-    Pstep[o] = r;
 }
 
 // a2: one node of a pressure sweep with scalar gathers; (d, q) feed the residual partials

@@ -53,6 +53,8 @@ RefreshArgs refresh_args(lbm2p *h, int pg)
     RefreshArgs a{};
     for (int i = 0; i < 9; ++i)
         a.gin[i] = h->gbuf[pg][i];
+    a.R = h->R;
+    a.Pstep = h->p.warm_start ? h->Pstep : nullptr;
     a.K = h->K;
     a.Fs = h->Fs;
     a.inv_tau = h->inv_tau;
@@ -367,12 +369,6 @@ lbm2p_status step_graph(lbm2p *h, int pf, int pg, cudaGraphExec_t *out)
         h->step_g[pf][pg] = G;
         cudaGraphNode_t nr, last, ns;
         CUDA_TRY(h, lbm2p_launch::node_refresh(&nr, G, nullptr, refresh_args(h, pg), h->grid));
-        if (h->p.warm_start) {
-            cudaGraphNode_t nx;
-            CUDA_TRY(h, lbm2p_launch::node_extrapolate(&nx, G, &nr, h->R, h->Pstep, h->geom,
-                                                       h->grid));
-            nr = nx;
-        }
         lbm2p_status e = add_loop(h, G, &nr, pf, &last);
         if (e != LBM2P_OK)
             return e;
@@ -762,7 +758,7 @@ lbm2p_status one_step(lbm2p *h, int replay, lbm2p_step_stats *stats)
         float sw_ms = -1.0f, step_ms = -1.0f;
         if ((e = read_loop(h, &k, &r, &sw_ms)) != LBM2P_OK)
             return e;
-        h->launches += 3 + (h->p.warm_start ? 1 : 0);   // refresh, (warm start,) saturation, rebase
+        h->launches += 3;                 // refresh (with the warm start), saturation, rebase
         h->cur_g = 1 - h->cur_g;
         if (h->timing)
             CUDA_TRY(h, cudaEventElapsedTime(&step_ms, h->ev_step0, h->ev_step1));
@@ -781,10 +777,6 @@ lbm2p_status one_step(lbm2p *h, int replay, lbm2p_step_stats *stats)
     // a1: stream g, S^n, tau_f
     lbm2p_launch::refresh(refresh_args(h, h->cur_g), h->grid, h->stream);
     LAUNCHED(h, "refresh");
-    if (h->p.warm_start) {
-        lbm2p_launch::extrapolate(h->R, h->Pstep, h->geom, h->grid, h->stream);
-        LAUNCHED(h, "warm start");
-    }
     // a2/a3: pressure sub-iteration
     int k = 0;
     double r = std::nan("");
