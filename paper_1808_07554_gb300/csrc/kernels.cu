@@ -746,14 +746,53 @@ __global__ void __launch_bounds__(kBlock) k_init_g(const __grid_constant__ InitG
     }
 }
 
+// Four nodes per thread with 128-bit accesses (rows are padded to 32 floats, so a quad never
+// crosses a row); per node the arithmetic of rebase_node.  Padding lanes are written back
+// unchanged.
 __global__ void __launch_bounds__(kBlock) k_rebase(const __grid_constant__ RebaseArgs a)
 {
     const Geom &g = a.g;
-    for (int t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
-        const int y = t / g.tiles_x;
-        const int x = (t - y * g.tiles_x) * kBlock + threadIdx.x;
-        if (x < g.nx)
-            rebase_node(a, y * g.pitch + x);
+    const int qx = (g.nx + 3) / 4;
+    const long long nq = (long long)qx * g.ny;
+    for (long long q = (long long)blockIdx.x * kBlock + threadIdx.x; q < nq;
+         q += (long long)gridDim.x * kBlock) {
+        const int y = (int)(q / qx);
+        const int x = (int)(q - (long long)y * qx) * 4;
+        const int o = y * g.pitch + x;
+        const float4 r = *reinterpret_cast<const float4 *>(a.R + o);
+        const float4 pn = *reinterpret_cast<const float4 *>(a.Pnew + o);
+        const bool in1 = x + 1 < g.nx, in2 = x + 2 < g.nx, in3 = x + 3 < g.nx;
+        float4 d;
+        d.x = r.x - pn.x;
+        d.y = in1 ? r.y - pn.y : 0.0f;
+        d.z = in2 ? r.z - pn.z : 0.0f;
+        d.w = in3 ? r.w - pn.w : 0.0f;
+        float4 n[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            n[i] = *reinterpret_cast<const float4 *>(a.n[i] + o);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const float w = wgt(i + 1);
+            float4 v = n[i];
+            v.x = fmaf(w, d.x, v.x);
+            if (in1)
+                v.y = fmaf(w, d.y, v.y);
+            if (in2)
+                v.z = fmaf(w, d.z, v.z);
+            if (in3)
+                v.w = fmaf(w, d.w, v.w);
+            *reinterpret_cast<float4 *>(a.n[i] + o) = v;
+        }
+        float4 rn = r;
+        rn.x = pn.x;
+        if (in1)
+            rn.y = pn.y;
+        if (in2)
+            rn.z = pn.z;
+        if (in3)
+            rn.w = pn.w;
+        *reinterpret_cast<float4 *>(a.R + o) = rn;
     }
 }
 

@@ -306,7 +306,7 @@ __device__ __forceinline__ void rebase_node(const RebaseArgs &a, int o)
     const float d = a.R[o] - pn;
 #pragma unroll
     for (int i = 0; i < 8; ++i)
-        a.n[i][o] += wgt(i + 1) * d;
+        a.n[i][o] = fmaf(wgt(i + 1), d, a.n[i][o]);
     a.R[o] = pn;
 }
 
