@@ -515,7 +515,9 @@ __global__ void __launch_bounds__(kBlock) k_pressure_scalar(const __grid_constan
 {
     const Geom &g = a.g;
     const int lane = threadIdx.x & 31;
-    double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
+    // residual sums: per thread over its nodes (FP32, the values are shifted to be centred),
+    // then per warp (FP32 shuffles) and per block (FP64) once, after the sweep
+    float acc0 = 0.0f, acc1 = 0.0f, acc2 = 0.0f, acc3 = 0.0f;
     const float shift = CHECK ? a.shift[0] : 0.0f;
     const float dshift = CHECK ? a.shift[1] : 0.0f;
     for (int t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
@@ -525,23 +527,21 @@ __global__ void __launch_bounds__(kBlock) k_pressure_scalar(const __grid_constan
         if (x < g.nx)
             sweep_node<CHECK, WRITE_P>(a, x, y, y * g.pitch + x, shift, dshift, d, q);
         if (CHECK) {
-            const float s0 = warp_sum(d), s1 = warp_sum(d * d), s2 = warp_sum(q), s3 = warp_sum(q * q);
-            if (lane == 0) {
-                acc0 += s0;
-                acc1 += s1;
-                acc2 += s2;
-                acc3 += s3;
-            }
+            acc0 += d;
+            acc1 = fmaf(d, d, acc1);
+            acc2 += q;
+            acc3 = fmaf(q, q, acc3);
         }
     }
     if (CHECK) {
         __shared__ double red[kBlock / 32][4];
         const int warp = threadIdx.x >> 5;
+        const float s0 = warp_sum(acc0), s1 = warp_sum(acc1), s2 = warp_sum(acc2), s3 = warp_sum(acc3);
         if (lane == 0) {
-            red[warp][0] = acc0;
-            red[warp][1] = acc1;
-            red[warp][2] = acc2;
-            red[warp][3] = acc3;
+            red[warp][0] = s0;
+            red[warp][1] = s1;
+            red[warp][2] = s2;
+            red[warp][3] = s3;
         }
         __syncthreads();
         if (threadIdx.x < 4) {
