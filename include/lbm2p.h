@@ -250,7 +250,8 @@ lbm2p_status lbm2p_sweep_config(const lbm2p *h, int *fused, int *kind, int *tile
  *   "single_vec4 <grid> 0 0 0 <us>", "single_scalar <grid> 0 0 0 <us>",
  *   "single_rows <strip width> <ring slots> <rows per block> <grid> <us>",
  *   "fused <sweeps per launch> <threads per block> <rows per block> <grid> <us>"
- * with <us> the time per sweep.  Owned by h; valid until the next create-time tuning. */
+ * with <us> the time per sweep (the first two kinds once per grid tried: the resident-block
+ * capacity of the GPU down to half of it).  Owned by h; valid until the next create-time tuning. */
 const char *lbm2p_autotune_report(const lbm2p *h);
 
 /* Running totals since creation: kernels launched by the library, pressure sweeps run. */

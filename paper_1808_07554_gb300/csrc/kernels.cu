@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(kBlock, LBM2P_SWEEP_MINB) k_pressure(const __g
     const Geom &g = a.g;
     const int lane = threadIdx.x & 31;
     const int p = g.pitch;
-    double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
+    ResAcc racc;                                      // residual sums of this thread
     const float shift = CHECK ? a.shift[0] : 0.0f;    // constant subtracted from P
     const float dshift = CHECK ? a.shift[1] : 0.0f;   // constant subtracted from dP - dP_prev
     const int tiles_x = (g.nx + 4 * kBlock - 1) / (4 * kBlock);
@@ -103,7 +103,6 @@ __global__ void __launch_bounds__(kBlock, LBM2P_SWEEP_MINB) k_pressure(const __g
         const int y = t / tiles_x;
         const int x0 = ((t - y * tiles_x) * kBlock + threadIdx.x) * 4;
         const int o = y * p + x0;
-        float sd = 0.0f, sdd = 0.0f, sp = 0.0f, spp = 0.0f;
         const bool row_inner = y > 0 && y < g.ny - 1;     // uniform over the block
         bool fast = false;
         float4 f[8], r0, it, F;
@@ -204,10 +203,7 @@ __global__ void __launch_bounds__(kBlock, LBM2P_SWEEP_MINB) k_pressure(const __g
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
                     const float d = (dPv[c] - (&Pp.x)[c]) - dshift, q = ((&r0.x)[c] - shift) + dPv[c];
-                    sd += d;
-                    sdd += d * d;
-                    sp += q;
-                    spp += q * q;
+                    racc.add(d, q);
                 }
             }
             if (WRITE_P)
@@ -233,36 +229,23 @@ __global__ void __launch_bounds__(kBlock, LBM2P_SWEEP_MINB) k_pressure(const __g
                     a.fout[i][oc] = collide1(fc[i], wgt(i + 1), dP, itc, Fq);
                 if (CHECK) {
                     const float d = (dP - a.Pio[oc]) - dshift, q = (a.R[oc] - shift) + dP;
-                    sd += d;
-                    sdd += d * d;
-                    sp += q;
-                    spp += q * q;
+                    racc.add(d, q);
                 }
                 if (WRITE_P)
                     a.Pio[oc] = dP;
-            }
-        }
-        if (CHECK) {
-            sd = warp_sum(sd);
-            sdd = warp_sum(sdd);
-            sp = warp_sum(sp);
-            spp = warp_sum(spp);
-            if (lane == 0) {
-                acc0 += sd;
-                acc1 += sdd;
-                acc2 += sp;
-                acc3 += spp;
             }
         }
     }
     if (CHECK) {
         __shared__ double red[kBlock / 32][4];
         const int warp = threadIdx.x >> 5;
+        double v[4];
+        racc.warp_totals(v);
         if (lane == 0) {
-            red[warp][0] = acc0;
-            red[warp][1] = acc1;
-            red[warp][2] = acc2;
-            red[warp][3] = acc3;
+            red[warp][0] = v[0];
+            red[warp][1] = v[1];
+            red[warp][2] = v[2];
+            red[warp][3] = v[3];
         }
         __syncthreads();
         if (threadIdx.x < 4) {
@@ -339,7 +322,7 @@ __global__ void __launch_bounds__(128) k_pressure_tb(const __grid_constant__ Pre
     const int w0 = L.width(0);
     const float shift = CHECK ? a.shift[0] : 0.0f;
     const float dshift = CHECK ? a.shift[1] : 0.0f;
-    float sd = 0.0f, sdd = 0.0f, sp = 0.0f, spp = 0.0f;
+    ResAcc racc;                                   // residual sums of this thread
 
     // global loads of input row r (8 planes, R, 1/tau_f, F~_p) at this thread's column
     auto fetch = [&](int r, TBRow &row) {
@@ -472,10 +455,7 @@ __global__ void __launch_bounds__(128) k_pressure_tb(const __grid_constant__ Pre
                         if (CHECK) {
                             const float d = (dP - sm[L.dpring() + (rl % 3) * L.width(T - 1) + c + 1]) - dshift;
                             const float q = (r0 - shift) + dP;
-                            sd += d;
-                            sdd += d * d;
-                            sp += q;
-                            spp += q * q;
+                            racc.add(d, q);
                         }
                     }
                 }
@@ -487,16 +467,14 @@ __global__ void __launch_bounds__(128) k_pressure_tb(const __grid_constant__ Pre
     }
     if (CHECK) {
         const int lane = tid & 31, warp = tid >> 5;
-        sd = warp_sum(sd);
-        sdd = warp_sum(sdd);
-        sp = warp_sum(sp);
-        spp = warp_sum(spp);
+        double v[4];
+        racc.warp_totals(v);
         __shared__ double red[4][4];
         if (lane == 0) {
-            red[warp][0] = sd;
-            red[warp][1] = sdd;
-            red[warp][2] = sp;
-            red[warp][3] = spp;
+            red[warp][0] = v[0];
+            red[warp][1] = v[1];
+            red[warp][2] = v[2];
+            red[warp][3] = v[3];
         }
         __syncthreads();
         if (tid < 4) {
@@ -515,33 +493,31 @@ __global__ void __launch_bounds__(kBlock) k_pressure_scalar(const __grid_constan
 {
     const Geom &g = a.g;
     const int lane = threadIdx.x & 31;
-    // residual sums: per thread over its nodes (FP32, the values are shifted to be centred),
-    // then per warp (FP32 shuffles) and per block (FP64) once, after the sweep
-    float acc0 = 0.0f, acc1 = 0.0f, acc2 = 0.0f, acc3 = 0.0f;
+    // residual sums: per thread over its nodes, then per warp and per block once, after the
+    // sweep
+    ResAcc racc;
     const float shift = CHECK ? a.shift[0] : 0.0f;
     const float dshift = CHECK ? a.shift[1] : 0.0f;
     for (int t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
         const int y = t / g.tiles_x;
         const int x = (t - y * g.tiles_x) * kBlock + threadIdx.x;
         float d = 0.0f, q = 0.0f;
-        if (x < g.nx)
+        if (x < g.nx) {
             sweep_node<CHECK, WRITE_P>(a, x, y, y * g.pitch + x, shift, dshift, d, q);
-        if (CHECK) {
-            acc0 += d;
-            acc1 = fmaf(d, d, acc1);
-            acc2 += q;
-            acc3 = fmaf(q, q, acc3);
+            if (CHECK)
+                racc.add(d, q);
         }
     }
     if (CHECK) {
         __shared__ double red[kBlock / 32][4];
         const int warp = threadIdx.x >> 5;
-        const float s0 = warp_sum(acc0), s1 = warp_sum(acc1), s2 = warp_sum(acc2), s3 = warp_sum(acc3);
+        double v[4];
+        racc.warp_totals(v);
         if (lane == 0) {
-            red[warp][0] = s0;
-            red[warp][1] = s1;
-            red[warp][2] = s2;
-            red[warp][3] = s3;
+            red[warp][0] = v[0];
+            red[warp][1] = v[1];
+            red[warp][2] = v[2];
+            red[warp][3] = v[3];
         }
         __syncthreads();
         if (threadIdx.x < 4) {

@@ -29,7 +29,8 @@ struct lbm2p {
     int grid_check = 0;        // blocks of a pressure sweep that accumulates the residual
     int sweep_kind = 0;        // single-sweep kernel: 0 = four nodes per thread, 1 = one
                                // node per thread, 2 = staged rows
-    int grid_k[2] = {}, grid_check_k[2] = {};
+    int grid_sweep = 0;        // blocks of a single sweep without the residual (autotuned)
+    int grid_k[2] = {}, grid_check_k[2] = {}, grid_cap_k[2] = {};
     int rows_w = 0, rows_slots = 0, rows_H = 0, rows_grid = 0;   // staged-rows kernel shape
     int tb_T = 0, tb_W = 0, tb_H = 0, tb_grid = 0;   // fused sweeps per launch and tile shape
     int tb_T_graph = 0;        // fused sweeps used inside the graph loop body (0: single sweeps)

@@ -232,6 +232,66 @@ __device__ __forceinline__ float warp_sum(float v)
     return v;
 }
 
+// Residual sums of a checking sweep (a3): sum d, sum d^2, sum q, sum q^2 over the nodes of a
+// warp, accurate whatever the shift constants already subtracted from d and q.  Each thread
+// sums in FP32 the differences of its values from the first ones it saw (its pivots), which
+// are of the size of the spread of d and q, not of their offset; at the end the lanes move
+// their sums to the pivots of the warp's lowest active lane (again a difference of two
+// samples), the warp adds them in FP32, and lane 0 restores the raw sums in FP64:
+// sum x = S1 + n c, sum x^2 = S2 + 2 c S1 + n c^2.
+struct ResAcc {
+    int n = 0;
+    float cd = 0.0f, cq = 0.0f;                    // pivots of this thread
+    float s1 = 0.0f, s2 = 0.0f, t1 = 0.0f, t2 = 0.0f;
+
+    __device__ __forceinline__ void add(float d, float q)
+    {
+        if (n == 0) {
+            cd = d;
+            cq = q;
+        }
+        const float e = d - cd, u = q - cq;
+        s1 += e;
+        s2 = fmaf(e, e, s2);
+        t1 += u;
+        t2 = fmaf(u, u, t2);
+        ++n;
+    }
+
+    // called by all 32 lanes together; lane 0 receives the warp's raw sums
+    __device__ __forceinline__ void warp_totals(double (&v)[4]) const
+    {
+        const unsigned act = __ballot_sync(0xffffffffu, n > 0);
+        const int src = act ? __ffs(act) - 1 : 0;
+        const float wd = __shfl_sync(0xffffffffu, cd, src);
+        const float wq = __shfl_sync(0xffffffffu, cq, src);
+        const float nf = (float)n;
+        float a1 = 0.0f, a2 = 0.0f, b1 = 0.0f, b2 = 0.0f;
+        if (n > 0) {
+            const float od = cd - wd, oq = cq - wq;  // this thread's pivots from the warp's
+            a1 = fmaf(nf, od, s1);
+            a2 = fmaf(nf * od, od, fmaf(2.0f * od, s1, s2));
+            b1 = fmaf(nf, oq, t1);
+            b2 = fmaf(nf * oq, oq, fmaf(2.0f * oq, t1, t2));
+        }
+        a1 = warp_sum(a1);
+        a2 = warp_sum(a2);
+        b1 = warp_sum(b1);
+        b2 = warp_sum(b2);
+        int cnt = n;
+#pragma unroll
+        for (int sh = 16; sh > 0; sh >>= 1)
+            cnt += __shfl_xor_sync(0xffffffffu, cnt, sh);
+        if ((threadIdx.x & 31) == 0) {
+            const double N = (double)cnt, c = (double)wd, b = (double)wq;
+            v[0] = (double)a1 + N * c;
+            v[1] = (double)a2 + 2.0 * c * (double)a1 + N * c * c;
+            v[2] = (double)b1 + N * b;
+            v[3] = (double)b2 + 2.0 * b * (double)b1 + N * b * b;
+        }
+    }
+};
+
 
 // --------------------------------------------------------------------------------------
 // per-node bodies shared by the single-lattice kernels and the batched kernels

@@ -261,7 +261,7 @@ void launch_sweep(lbm2p *h, const PressureArgs &a, bool check, bool write_p)
         lbm2p_launch::pressure_sweep_rows(a, check, write_p, h->rows_w, h->rows_slots, h->rows_H,
                                           h->rows_grid, h->stream);
     else
-        lbm2p_launch::pressure_sweep(a, check, write_p, check ? h->grid_check : h->grid, h->stream,
+        lbm2p_launch::pressure_sweep(a, check, write_p, check ? h->grid_check : h->grid_sweep, h->stream,
                                      h->sweep_kind);
 }
 
@@ -272,7 +272,7 @@ cudaError_t add_sweep_node(lbm2p *h, cudaGraphNode_t *n, cudaGraph_t g, const cu
         return lbm2p_launch::node_pressure_rows(n, g, dep, a, check, write_p, h->rows_w,
                                                 h->rows_slots, h->rows_H, h->rows_grid);
     return lbm2p_launch::node_pressure(n, g, dep, a, check, write_p,
-                                       check ? h->grid_check : h->grid, h->sweep_kind);
+                                       check ? h->grid_check : h->grid_sweep, h->sweep_kind);
 }
 
 // residual partials written by one checking single sweep
@@ -942,18 +942,36 @@ lbm2p_status autotune_sweeps(lbm2p *h)
     h->tb_T = 0;
     h->sweep_kind = forced == LBM2P_SWEEP_AUTO ? 0 : forced - 1;
     if (!fused_only || forced != LBM2P_SWEEP_AUTO) {
+        // grid-stride kernels: resident blocks per SM from the occupancy limit down to half
+        // of it (fewer, fuller rounds of row tiles per block can beat a full machine)
         for (int kind = 0; kind < 2; ++kind) {
             if (!allowed(kind))
                 continue;
-            float ms = 0.0f;
-            if (!timed([&](int k) {
-                    PressureArgs a = pressure_args(h, k % 2);
-                    lbm2p_launch::pressure_sweep(a, false, false, h->grid_k[kind], h->stream, kind);
-                }, &ms))
-                goto done;
-            note(kind == 0 ? "single_vec4" : "single_scalar", h->grid_k[kind], 0, 0, 0, ms * 1e3f);
-            if (ms < best) {
-                best = ms;
+            const int maxb = lbm2p_launch::max_blocks_per_sm_pressure(false, kind);
+            float best_kind = 1e30f;
+            int best_grid = h->grid_k[kind], last_grid = -1;
+            for (int b = maxb; b >= 1 && 2 * b >= maxb; --b) {
+                long long want = (long long)sms * b;
+                want = want < h->geom.ntiles ? want : h->geom.ntiles;
+                const int grid = (int)(want > 0 ? want : 1);
+                if (grid == last_grid)
+                    continue;
+                last_grid = grid;
+                float ms = 0.0f;
+                if (!timed([&](int k) {
+                        PressureArgs a = pressure_args(h, k % 2);
+                        lbm2p_launch::pressure_sweep(a, false, false, grid, h->stream, kind);
+                    }, &ms))
+                    goto done;
+                note(kind == 0 ? "single_vec4" : "single_scalar", grid, 0, 0, 0, ms * 1e3f);
+                if (ms < best_kind) {
+                    best_kind = ms;
+                    best_grid = grid;
+                }
+            }
+            h->grid_k[kind] = best_grid;
+            if (best_kind < best) {
+                best = best_kind;
                 h->sweep_kind = kind;
             }
         }
@@ -1271,7 +1289,8 @@ lbm2p_status build(lbm2p *h, const lbm2p_inputs *in, lbm2p_step_stats *init_stat
         return (int)(blocks > 0 ? blocks : 1);
     };
     for (int kind = 0; kind < 2; ++kind) {
-        h->grid_k[kind] = cap_grid((long long)sms * lbm2p_launch::max_blocks_per_sm_pressure(false, kind));
+        h->grid_cap_k[kind] = cap_grid((long long)sms * lbm2p_launch::max_blocks_per_sm_pressure(false, kind));
+        h->grid_k[kind] = h->grid_cap_k[kind];
         h->grid_check_k[kind] = cap_grid((long long)sms * lbm2p_launch::max_blocks_per_sm_pressure(true, kind));
     }
     h->sweep_kind = 0;
@@ -1337,7 +1356,8 @@ lbm2p_status build(lbm2p *h, const lbm2p_inputs *in, lbm2p_step_stats *init_stat
     }
     // grid-stride lattice kernels keep the one-node-per-thread capacity when the staged
     // sweep is chosen
-    h->grid = h->grid_k[h->sweep_kind < 2 ? h->sweep_kind : 1];
+    h->grid = h->grid_cap_k[h->sweep_kind < 2 ? h->sweep_kind : 1];
+    h->grid_sweep = h->grid_k[h->sweep_kind < 2 ? h->sweep_kind : 1];
     h->grid_check = h->grid_check_k[h->sweep_kind < 2 ? h->sweep_kind : 1];
     {
         int np = h->tb_grid > h->rows_grid ? h->tb_grid : h->rows_grid;

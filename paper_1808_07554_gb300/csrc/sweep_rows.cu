@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(32 * (CW + 1)) k_pressure_rows(const __grid_co
         // ---- consumers -----------------------------------------------------------------
         const float shift = CHECK ? a.shift[0] : 0.0f;
         const float dshift = CHECK ? a.shift[1] : 0.0f;
-        double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
+        ResAcc racc;                          // residual sums of this lane over its rows
         const int lx = warp * 32 + lane + kRowsHalo;
         const int x = x0 + lx - kRowsHalo;
         bool ok = true;
@@ -139,7 +139,6 @@ __global__ void __launch_bounds__(32 * (CW + 1)) k_pressure_rows(const __grid_co
             const float *sm = ring + (size_t)((t - 2) % S) * slot_floats;
             const float *s0 = ring + (size_t)((t - 1) % S) * slot_floats;
             const float *sp = ring + (size_t)(t % S) * slot_floats;
-            float d = 0.0f, q = 0.0f;
             if (x < g.nx) {
                 const int o = y * p + x;
                 const float r0 = s0[8 * RW + lx];
@@ -166,22 +165,10 @@ __global__ void __launch_bounds__(32 * (CW + 1)) k_pressure_rows(const __grid_co
 #pragma unroll
                 for (int i = 0; i < 8; ++i)
                     a.fout[i][o] = collide1(f[i], wgt(i + 1), dP, it, Fq);
-                if (CHECK) {
-                    d = (dP - a.Pio[o]) - dshift;
-                    q = (r0 - shift) + dP;
-                }
+                if (CHECK)
+                    racc.add((dP - a.Pio[o]) - dshift, (r0 - shift) + dP);
                 if (WRITE_P)
                     a.Pio[o] = dP;
-            }
-            if (CHECK) {
-                const float s0s = warp_sum(d), s1s = warp_sum(d * d);
-                const float s2s = warp_sum(q), s3s = warp_sum(q * q);
-                if (lane == 0) {
-                    acc0 += s0s;
-                    acc1 += s1s;
-                    acc2 += s2s;
-                    acc3 += s3s;
-                }
             }
             // row t - 2 is no longer needed by this warp
             __syncwarp();
@@ -197,11 +184,15 @@ __global__ void __launch_bounds__(32 * (CW + 1)) k_pressure_rows(const __grid_co
                     for (int i = 0; i < 8; ++i)
                         a.fout[i][y * p + x] = nan;
         }
-        if (CHECK && lane == 0) {
-            red[warp][0] = acc0;
-            red[warp][1] = acc1;
-            red[warp][2] = acc2;
-            red[warp][3] = acc3;
+        if (CHECK) {
+            double v[4];
+            racc.warp_totals(v);
+            if (lane == 0) {
+                red[warp][0] = v[0];
+                red[warp][1] = v[1];
+                red[warp][2] = v[2];
+                red[warp][3] = v[3];
+            }
         }
     }
     __syncthreads();
