@@ -191,6 +191,26 @@ def test_batch_against_oracle():
         assert all(v <= 1e-5 for v in err.values()), err
 
 
+def test_large_members_bit_identical():
+    """Members of the sizes the batched workload draws from, up to 1024^2 (128^2, 256^2,
+    512^2, 1024^2 and a ragged 1000 x 600), one replayed step: every member's state equals
+    that of the same handle stepped alone."""
+    pkg = _pkg()
+    probs = [W.quarter_five_spot(n, seed=30 + n) for n in (128, 256, 512, 1024)]
+    probs.append(W.quarter_five_spot(1000, 600, seed=31, corr_len=12.0))
+    alone = [_solver(p, init_replay=50) for p in probs]
+    inb = [_solver(p, init_replay=50) for p in probs]
+    counts = [24, 40, 8, 64, 16]
+    with pkg.Batch(inb) as batch:
+        for s, c in zip(alone, counts):
+            s.step(1, replay=[c])
+        batch.step(1, replay=counts)
+        for a, b in zip(alone, inb):
+            assert np.array_equal(a.get_state(), b.get_state())
+    for s in alone + inb:
+        s.close()
+
+
 def test_rejects_bad_members_and_counts():
     pkg = _pkg()
     p = W.quarter_five_spot(32, seed=4)

@@ -279,6 +279,43 @@ def test_full_size_single_kernels():
     orc.close()
 
 
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+def test_full_size_4096_sweeps(storage):
+    """The 4096^2 five-spot in the launch configuration the benchmark times there (the
+    autotuned kernels: one sweep by a single-sweep kernel, two by the fused launch when it
+    wins), from one seeded state, element by element against the oracle; FP16 storage of
+    the populations to the FP16 bar."""
+    pkg = _pkg()
+    prob = W.quarter_five_spot(4096, seed=2)
+    rng = np.random.default_rng(4096)
+    n, g, inv_tau, S, R = _random_state(prob, rng)
+    kw = {"storage": pkg.STORE_FP16_DEV} if storage == "fp16" else {}
+    gpu = pkg.Solver.from_problem(prob, init_replay=0, **kw)
+    gpu.set_state(np.concatenate([n, g, inv_tau[None], S[None], R[None]]))
+    orc = O.Oracle(prob, init_replay=0)
+    w = np.array([1 / 9] * 4 + [1 / 36] * 4)
+    f = n.astype(np.float64) + w[:, None, None] * R.astype(np.float64)[None]
+    del n, g
+    orc.set_state(f=np.concatenate([np.zeros((1,) + f.shape[1:]), f]),
+                  g=gpu.get_state()[8:17].astype(np.float64),
+                  tau_f=1.0 / inv_tau.astype(np.float64), S=S.astype(np.float64))
+    del f
+    tol = 2e-3 if storage == "fp16" else 2e-6
+    for sweeps in (1, 2):
+        gpu.pressure_sweeps(sweeps)
+        orc.pressure(sweeps)
+        st = gpu.get_state()
+        fo = orc.get_state()["f"][1:]
+        scale = np.max(np.abs(fo))
+        for i in range(8):
+            fg = st[i].astype(np.float64) + w[i] * st[19].astype(np.float64)
+            err = np.max(np.abs(fg - fo[i]))
+            assert err <= tol * scale, (storage, sweeps, i, err / scale)
+        del st, fo
+    gpu.close()
+    orc.close()
+
+
 # ------------------------------------------------------------------------------------------
 # edge cases: degenerate and ragged lattices, every wall kind
 # ------------------------------------------------------------------------------------------
