@@ -258,6 +258,20 @@ void pressure_sweep_rows(const PressureArgs &a, bool check, bool write_p, int wi
 cudaError_t node_pressure_rows(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
                                const PressureArgs &a, bool check, bool write_p, int width,
                                int slots, int H, int grid);
+// two sweeps per launch on staged rows (sweep_rows.cu), lattices without periodic sides:
+// cw consumer warps of 30 owned columns each (4 or 8), ring slots (6/8 with 4 warps, 4/6
+// with 8), H output rows per block; grid = rows2_grid(...)
+bool rows2_shape_ok(int cw, int slots);
+int rows2_width(int cw);
+size_t rows2_smem_bytes(int cw, int slots, bool has_fp);
+long long rows2_grid(int cw, int H, int nx, int ny);
+cudaError_t rows2_prepare(int cw, int slots);
+int rows2_blocks_per_sm(int cw, int slots, bool has_fp);
+void pressure_sweeps_rows2(const PressureArgs &a, bool check, int cw, int slots, int H, int grid,
+                           void *stream);
+cudaError_t node_pressure_rows2(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
+                                const PressureArgs &a, bool check, int cw, int slots, int H,
+                                int grid);
 // FP16 storage (fp16.cu): narrow = max |n| -> scale -> convert; one sweep; widen
 int max_blocks_per_sm_pressure_h();
 void half_narrow(const HalfConvertArgs &a, int grid, void *stream);

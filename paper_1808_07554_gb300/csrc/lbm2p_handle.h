@@ -33,6 +33,9 @@ struct lbm2p {
     int grid_k[2] = {}, grid_check_k[2] = {}, grid_cap_k[2] = {};
     int rows_w = 0, rows_slots = 0, rows_H = 0, rows_grid = 0;   // staged-rows kernel shape
     int tb_T = 0, tb_W = 0, tb_H = 0, tb_grid = 0;   // fused sweeps per launch and tile shape
+    int tb_kind = 0;           // fused kernel: 0 = k_pressure_tb (shared-memory stages), 1 =
+                               // k_pressure_rows2 (two sweeps on staged rows; tb_W = 30 x warps)
+    int tb_slots = 0;          // ring slots of k_pressure_rows2
     int tb_T_graph = 0;        // fused sweeps used inside the graph loop body (0: single sweeps)
     bool fp16 = false;         // storage FP16_DEV: sweeps run on FP16 copies inside a solve
     __half *hbuf[2][8] = {};

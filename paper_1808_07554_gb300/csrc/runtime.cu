@@ -309,8 +309,14 @@ lbm2p_status add_loop(lbm2p *h, cudaGraph_t G, const cudaGraphNode_t *dep, int p
         for (int kk = T; kk <= m; kk += T) {
             cudaGraphNode_t n;
             PressureArgs a = pressure_args(h, src);
-            CUDA_TRY(h, lbm2p_launch::node_pressure_fused(&n, body, prev ? &prev : nullptr, a, T,
-                                                          h->tb_W, h->tb_H, kk == m, h->tb_grid));
+            if (h->tb_kind == 1)
+                CUDA_TRY(h, lbm2p_launch::node_pressure_rows2(&n, body, prev ? &prev : nullptr, a,
+                                                              kk == m, h->tb_W / 30, h->tb_slots,
+                                                              h->tb_H, h->tb_grid));
+            else
+                CUDA_TRY(h, lbm2p_launch::node_pressure_fused(&n, body, prev ? &prev : nullptr, a,
+                                                              T, h->tb_W, h->tb_H, kk == m,
+                                                              h->tb_grid));
             prev = n;
             src = 1 - src;
         }
@@ -621,8 +627,13 @@ lbm2p_status pressure_solve(lbm2p *h, int replay, int *k_out, double *r_out, flo
         }
         for (int q = 0; q < nf; ++q) {
             PressureArgs a = pressure_args(h, h->cur_f);
-            lbm2p_launch::pressure_sweeps_fused(a, T, h->tb_W, h->tb_H, q == nf - 1 && final_check,
-                                                h->tb_grid, h->stream);
+            if (h->tb_kind == 1)
+                lbm2p_launch::pressure_sweeps_rows2(a, q == nf - 1 && final_check, h->tb_W / 30,
+                                                    h->tb_slots, h->tb_H, h->tb_grid, h->stream);
+            else
+                lbm2p_launch::pressure_sweeps_fused(a, T, h->tb_W, h->tb_H,
+                                                    q == nf - 1 && final_check, h->tb_grid,
+                                                    h->stream);
             LAUNCHED(h, "fused pressure sweeps");
             h->cur_f = 1 - h->cur_f;
             h->sweeps += T;
@@ -1037,8 +1048,13 @@ lbm2p_status autotune_sweeps(lbm2p *h)
     if (fused_only)
         best = 1e30f;
     if (h->p.fuse_sweeps != 1) {
+        bool walls = true;
+        for (int sd = 0; sd < 4; ++sd)
+            walls = walls && h->p.bc[sd] != LBM2P_BC_PERIODIC;
+        // fuse_sweeps 2 with the ROWS kernel pinned asks for the staged-rows two-sweep kernel
+        const bool rows2_only = walls && h->p.fuse_sweeps == 2 && forced == LBM2P_SWEEP_ROWS;
         for (int T : {2, 4}) {
-            if (h->p.fuse_sweeps != 0 && h->p.fuse_sweeps != T)
+            if ((h->p.fuse_sweeps != 0 && h->p.fuse_sweeps != T) || rows2_only)
                 continue;
             for (int W : {128, 64, 32}) {
                 cudaError_t ce = lbm2p_launch::tb_prepare(T, W);
@@ -1061,8 +1077,50 @@ lbm2p_status autotune_sweeps(lbm2p *h)
                     if (ms / T < best) {
                         best = ms / T;
                         h->tb_T = T;
+                        h->tb_kind = 0;
                         h->tb_W = W;
                         h->tb_H = H;
+                        h->tb_grid = (int)blocks;
+                    }
+                }
+            }
+        }
+        // two sweeps per launch on rows staged by bulk copies (lattices with walls on every
+        // side): consumer warps x ring slots, and output rows per block
+        if (walls && (h->p.fuse_sweeps == 0 || h->p.fuse_sweeps == 2) &&
+            (forced == LBM2P_SWEEP_AUTO || forced == LBM2P_SWEEP_ROWS)) {
+            const int shapes2[4][2] = {{4, 6}, {4, 8}, {8, 4}, {8, 6}};
+            for (const auto &sh : shapes2) {
+                const int cw = sh[0], slots = sh[1];
+                if (lbm2p_launch::rows2_prepare(cw, slots) != cudaSuccess ||
+                    lbm2p_launch::rows2_blocks_per_sm(cw, slots, h->Fp != nullptr) < 1) {
+                    cudaGetLastError();
+                    continue;
+                }
+                int last_H = -1;
+                for (int H : {16, 32, 64, 128}) {
+                    const int Hc = H < h->ny ? H : h->ny;
+                    if (Hc == last_H)
+                        continue;
+                    last_H = Hc;
+                    const long long blocks = lbm2p_launch::rows2_grid(cw, Hc, h->nx, h->ny);
+                    if (blocks > (1LL << 30))
+                        continue;
+                    float ms = 0.0f;
+                    if (!timed([&](int k) {
+                            PressureArgs a = pressure_args(h, k % 2);
+                            lbm2p_launch::pressure_sweeps_rows2(a, false, cw, slots, Hc,
+                                                                (int)blocks, h->stream);
+                        }, &ms))
+                        goto done;
+                    note("fused_rows", cw, slots, Hc, (int)blocks, ms / 2 * 1e3f);
+                    if (ms / 2 < best) {
+                        best = ms / 2;
+                        h->tb_T = 2;
+                        h->tb_kind = 1;
+                        h->tb_W = lbm2p_launch::rows2_width(cw);
+                        h->tb_slots = slots;
+                        h->tb_H = Hc;
                         h->tb_grid = (int)blocks;
                     }
                 }

@@ -204,6 +204,311 @@ __global__ void __launch_bounds__(32 * (CW + 1)) k_pressure_rows(const __grid_co
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Two sweeps per launch on staged rows (walls on every side; no periodic side).
+//
+// The producer stages input rows exactly as above.  Consumer warp w owns the 30 output
+// columns [x0 + 30 w, x0 + 30 w + 30) of a strip of W = 30 CW columns; its 32 lanes compute
+// the first sweep on those columns plus one on each side (the halo the second sweep pulls
+// from), into a warp-private ring of three rows in shared memory, and lanes 1..30 compute
+// the second sweep from that ring one row behind, writing the populations to global memory.
+// Input row t (y = y0 - 2 + t) feeds the first sweep at rows y - 1 .. y + 1; a warp releases
+// it after the first sweep at row y + 1.  The second sweep at row y takes R, 1/tau_f and
+// w_bar F~_p of its node from the lane's registers (kept from its first-sweep rows) and R of
+// the neighbouring columns by warp shuffles.
+// A node on a wall applies the wall rules of Sec. 4 to its own first-sweep values.  Both
+// sweeps use the per-node arithmetic of the single sweep, so the result equals two single
+// sweeps bit for bit.  CHECK: the residual sums of the second sweep against the first
+// (no increment plane).  Waits are bounded as in k_pressure_rows; a warp that gives up
+// poisons its columns with NaN.
+// ---------------------------------------------------------------------------------------
+constexpr int kPairRowFloats = 9 * 32;        // first-sweep row of a warp: 8 planes + dP
+
+// R around the node, rows y - 1 (m), y (c), y + 1 (p) and columns x - 1 (0), x (1), x + 1 (2)
+struct RNbhd {
+    float m0, m1, m2, c0, c1, c2, p0, p1, p2;
+    __device__ __forceinline__ float at(int ex, int ey) const
+    {
+        // the source x - c_i of a pull: column offset -ex, row offset -ey
+        if (ey == 1)
+            return ex == 1 ? m0 : (ex == -1 ? m2 : m1);
+        if (ey == -1)
+            return ex == 1 ? p0 : (ex == -1 ? p2 : p1);
+        return ex == 1 ? c0 : (ex == -1 ? c2 : c1);
+    }
+};
+
+// a_I of the second sweep at a wall node: the first sweep's value of the neighbour x - c_I
+// (in this warp's ring), or the wall rule of Sec. 4 on the node's own first-sweep values
+template <int I>
+__device__ __forceinline__ float second_pull(const float *n_m, const float *n_0, const float *n_p,
+                                             const RNbhd &R, const Geom &g, const float *const *Pb,
+                                             int x, int y, int lane, float r0)
+{
+    constexpr int ex = cx(I), ey = cy(I);
+    int side = -1;
+    if (x - ex < 0 || x - ex >= g.nx)
+        side = x - ex < 0 ? 0 : 1;
+    else if (y - ey < 0 || y - ey >= g.ny)
+        side = y - ey < 0 ? 2 : 3;
+    if (side < 0) {
+        const float *row = ey == 1 ? n_m : (ey == -1 ? n_p : n_0);
+        return dev1(row[(I - 1) * 32 + lane - ex], wgt(I), R.at(ex, ey), r0);
+    }
+    const float b = n_0[(opp(I) - 1) * 32 + lane];
+    if (g.bc[side] == BC_NOFLUX)
+        return b;
+    const int k = side < 2 ? 2 * y + 1 - ey : 2 * x + 1 - ex;
+    return -b + 2.0f * wgt(I) * (Pb[side][k] - r0);
+}
+
+template <bool CHECK, int CW, int S>
+__global__ void __launch_bounds__(32 * (CW + 1)) k_pressure_rows2(const __grid_constant__ PressureArgs a,
+                                                                  int H)
+{
+    constexpr int W = 30 * CW;
+    constexpr int RW = W + 2 * kRowsHalo;          // floats per staged plane row
+    const int npl = a.Fp ? 11 : 10;
+    const int slot_floats = npl * RW;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem);
+    uint64_t *empty = full + S;
+    float *ring = reinterpret_cast<float *>(smem + kRowsBarBytes);
+    float *first = ring + (size_t)S * slot_floats;   // CW warps x 3 rows x kPairRowFloats
+    __shared__ double red[CW][4];
+    __shared__ int failed;
+    const Geom &g = a.g;
+    const int p = g.pitch;
+    const int strips = (g.nx + W - 1) / W;
+    const int x0 = (blockIdx.x % strips) * W;
+    const int y0 = (blockIdx.x / strips) * H;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (y0 >= g.ny) {                              // not produced by rows_grid; kept safe
+        if (CHECK && threadIdx.x < 4)
+            a.partials[4 * blockIdx.x + threadIdx.x] = 0.0;
+        return;
+    }
+    const int y1 = y0 + H < g.ny ? y0 + H : g.ny;
+    const int nrows = y1 - y0 + 4;                 // input rows y0 - 2 .. y1 + 1
+    const int xa = x0 - kRowsHalo > 0 ? x0 - kRowsHalo : 0;
+    const int xb = x0 + W + kRowsHalo < p ? x0 + W + kRowsHalo : p;
+    const unsigned seg = (unsigned)(xb - xa) * 4u;
+    const int soff = xa - (x0 - kRowsHalo);
+
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < S; ++q) {
+            bar_init(full + q, 1);
+            bar_init(empty + q, CW);
+        }
+        failed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    if (warp == CW) {
+        // ---- producer ------------------------------------------------------------------
+        if (lane == 0) {
+            int issued = 0;
+            for (int t = 0; t < nrows; ++t) {
+                const int q = t % S;
+                if (t >= S && !bar_wait_bounded(empty + q, (unsigned)(t / S - 1) & 1u)) {
+                    failed = 1;
+                    break;
+                }
+                // the first row feeds only the c_y = +1 pulls of the first sweep's top row,
+                // the last only the c_y = -1 pulls of its bottom row; both also give R
+                const int r = y0 - 2 + t;
+                unsigned m = npl == 11 ? 0x7FFu : 0x3FFu;
+                if (r < 0 || r >= g.ny)
+                    m = 0u;
+                else if (t == 0)
+                    m = (1u << 1) | (1u << 4) | (1u << 5) | (1u << 8);
+                else if (t == nrows - 1)
+                    m = (1u << 3) | (1u << 6) | (1u << 7) | (1u << 8);
+                if (!m) {
+                    bar_arrive(full + q);
+                } else {
+                    bar_arrive_tx(full + q, (unsigned)__popc(m) * seg);
+                    const size_t roff = (size_t)r * p + xa;
+                    float *slot = ring + (size_t)q * slot_floats + soff;
+#pragma unroll
+                    for (int pl = 0; pl < kRowsMaxPlanes; ++pl) {
+                        if (!(m & (1u << pl)))
+                            continue;
+                        const float *src = pl < 8 ? a.fin[pl]
+                                                  : (pl == 8 ? a.R : (pl == 9 ? a.inv_tau : a.Fp));
+                        bulk_g2s(slot + pl * RW, src + roff, seg, full + q);
+                    }
+                }
+                issued = t + 1;
+            }
+            for (int t = issued - S > 0 ? issued - S : 0; t < issued; ++t)
+                bar_wait_bounded(full + t % S, (unsigned)(t / S) & 1u);
+        }
+    } else {
+        // ---- consumers -----------------------------------------------------------------
+        const float shift = CHECK ? a.shift[0] : 0.0f;
+        const float dshift = CHECK ? a.shift[1] : 0.0f;
+        ResAcc racc;
+        float *mine = first + (size_t)warp * 3 * kPairRowFloats;
+        const int x = x0 - 1 + 30 * warp + lane;    // this lane's column (both sweeps)
+        const int lx = x - (x0 - kRowsHalo);        // its column in a staged row
+        const bool xin = x >= 0 && x < g.nx;
+        const bool owner = lane >= 1 && lane <= 30 && x < g.nx;
+        // this lane's R, 1/tau_f, w_bar F~_p and first-sweep dP of its last three first-sweep
+        // rows (a: two arrivals ago, b: one, c: this one): the second sweep reads them from
+        // registers and its neighbours' by shuffles, so a staged row is released as soon as
+        // the first sweep is done with it
+        float ra = 0.0f, rb = 0.0f, rc = 0.0f, tb = 0.0f, tc = 0.0f, qb = 0.0f, qc = 0.0f;
+        float db = 0.0f, dc = 0.0f;
+        bool ok = true;
+        for (int t = 0; t < nrows && ok; ++t) {
+            ok = bar_wait_bounded(full + t % S, (unsigned)(t / S) & 1u);
+            if (!ok)
+                break;
+            if (t < 2)
+                continue;
+            // first sweep at row ys from input rows ys - 1, ys, ys + 1 (arrivals t-2..t)
+            const int ys = y0 - 3 + t;
+            {
+                const float *sm = ring + (size_t)((t - 2) % S) * slot_floats;
+                const float *s0 = ring + (size_t)((t - 1) % S) * slot_floats;
+                const float *sp = ring + (size_t)(t % S) * slot_floats;
+                float *dst = mine + (t % 3) * kPairRowFloats;
+                ra = rb;
+                rb = rc;
+                tb = tc;
+                qb = qc;
+                db = dc;
+                rc = tc = qc = dc = 0.0f;
+                if (xin && ys >= 0 && ys < g.ny) {
+                    const int o = ys * p + x;
+                    const float r0 = s0[8 * RW + lx];
+                    float f[8];
+                    if (interior(g, x, ys)) {
+                        f[0] = dev1(s0[0 * RW + lx - 1], wgt(1), s0[8 * RW + lx - 1], r0);
+                        f[1] = dev1(sm[1 * RW + lx], wgt(2), sm[8 * RW + lx], r0);
+                        f[2] = dev1(s0[2 * RW + lx + 1], wgt(3), s0[8 * RW + lx + 1], r0);
+                        f[3] = dev1(sp[3 * RW + lx], wgt(4), sp[8 * RW + lx], r0);
+                        f[4] = dev1(sm[4 * RW + lx - 1], wgt(5), sm[8 * RW + lx - 1], r0);
+                        f[5] = dev1(sm[5 * RW + lx + 1], wgt(6), sm[8 * RW + lx + 1], r0);
+                        f[6] = dev1(sp[6 * RW + lx + 1], wgt(7), sp[8 * RW + lx + 1], r0);
+                        f[7] = dev1(sp[7 * RW + lx - 1], wgt(8), sp[8 * RW + lx - 1], r0);
+                    } else {
+                        gather_a(a.fin, a.R, g, a.Pb, x, ys, o, f);
+                    }
+                    const float dP = pressure_of(f);
+                    const float it = s0[9 * RW + lx];
+                    float F = a.Fp ? s0[10 * RW + lx] : 0.0f;
+                    for (int w = 0; w < a.w.n; ++w)
+                        if (o == a.w.idx[w])
+                            F += a.w.fp[w];
+                    const float Fq = 0.125f * F;   // w_bar_i = 1/8 (Eq. 3-5a)
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        dst[i * 32 + lane] = collide1(f[i], wgt(i + 1), dP, it, Fq);
+                    rc = r0;
+                    tc = it;
+                    qc = Fq;
+                    dc = dP;
+                }
+                __syncwarp();
+                // input row t - 2 is no longer needed by this warp
+                if (lane == 0)
+                    bar_arrive(empty + (t - 2) % S);
+            }
+            if (t < 4)
+                continue;
+            // second sweep at row y2 = ys - 1 from the first sweep's rows y2 - 1, y2, y2 + 1
+            const int y2 = ys - 1;
+            RNbhd Rn;
+            Rn.m1 = ra;
+            Rn.c1 = rb;
+            Rn.p1 = rc;
+            Rn.m0 = __shfl_up_sync(0xffffffffu, ra, 1);
+            Rn.c0 = __shfl_up_sync(0xffffffffu, rb, 1);
+            Rn.p0 = __shfl_up_sync(0xffffffffu, rc, 1);
+            Rn.m2 = __shfl_down_sync(0xffffffffu, ra, 1);
+            Rn.c2 = __shfl_down_sync(0xffffffffu, rb, 1);
+            Rn.p2 = __shfl_down_sync(0xffffffffu, rc, 1);
+            if (owner && y2 < g.ny) {
+                const float *n_m = mine + ((t - 2) % 3) * kPairRowFloats;
+                const float *n_0 = mine + ((t - 1) % 3) * kPairRowFloats;
+                const float *n_p = mine + (t % 3) * kPairRowFloats;
+                const float r0 = rb;
+                float f[8];
+                if (interior(g, x, y2)) {
+                    f[0] = dev1(n_0[0 * 32 + lane - 1], wgt(1), Rn.c0, r0);
+                    f[1] = dev1(n_m[1 * 32 + lane], wgt(2), Rn.m1, r0);
+                    f[2] = dev1(n_0[2 * 32 + lane + 1], wgt(3), Rn.c2, r0);
+                    f[3] = dev1(n_p[3 * 32 + lane], wgt(4), Rn.p1, r0);
+                    f[4] = dev1(n_m[4 * 32 + lane - 1], wgt(5), Rn.m0, r0);
+                    f[5] = dev1(n_m[5 * 32 + lane + 1], wgt(6), Rn.m2, r0);
+                    f[6] = dev1(n_p[6 * 32 + lane + 1], wgt(7), Rn.p2, r0);
+                    f[7] = dev1(n_p[7 * 32 + lane - 1], wgt(8), Rn.p0, r0);
+                } else {
+                    f[0] = second_pull<1>(n_m, n_0, n_p, Rn, g, a.Pb, x, y2, lane, r0);
+                    f[1] = second_pull<2>(n_m, n_0, n_p, Rn, g, a.Pb, x, y2, lane, r0);
+                    f[2] = second_pull<3>(n_m, n_0, n_p, Rn, g, a.Pb, x, y2, lane, r0);
+                    f[3] = second_pull<4>(n_m, n_0, n_p, Rn, g, a.Pb, x, y2, lane, r0);
+                    f[4] = second_pull<5>(n_m, n_0, n_p, Rn, g, a.Pb, x, y2, lane, r0);
+                    f[5] = second_pull<6>(n_m, n_0, n_p, Rn, g, a.Pb, x, y2, lane, r0);
+                    f[6] = second_pull<7>(n_m, n_0, n_p, Rn, g, a.Pb, x, y2, lane, r0);
+                    f[7] = second_pull<8>(n_m, n_0, n_p, Rn, g, a.Pb, x, y2, lane, r0);
+                }
+                const int o = y2 * p + x;
+                const float dP = pressure_of(f);
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    a.fout[i][o] = collide1(f[i], wgt(i + 1), dP, tb, qb);
+                if (CHECK)
+                    racc.add((dP - db) - dshift, (r0 - shift) + dP);
+            }
+            __syncwarp();
+        }
+        if (!ok) {
+            failed = 1;
+            const float nan = __int_as_float(0x7fc00000);
+            if (owner)
+                for (int y = y0; y < y1; ++y)
+                    for (int i = 0; i < 8; ++i)
+                        a.fout[i][y * p + x] = nan;
+        }
+        if (CHECK) {
+            double v[4];
+            racc.warp_totals(v);
+            if (lane == 0) {
+                red[warp][0] = v[0];
+                red[warp][1] = v[1];
+                red[warp][2] = v[2];
+                red[warp][3] = v[3];
+            }
+        }
+    }
+    __syncthreads();
+    if (CHECK && threadIdx.x < 4) {
+        double sum = 0.0;
+        for (int w = 0; w < CW; ++w)
+            sum += red[w][threadIdx.x];
+        a.partials[4 * blockIdx.x + threadIdx.x] = failed ? (double)__int_as_float(0x7fc00000) : sum;
+    }
+}
+
+template <int CW, int S>
+void *rows2_func_t(bool check)
+{
+    return check ? (void *)k_pressure_rows2<true, CW, S> : (void *)k_pressure_rows2<false, CW, S>;
+}
+
+// the two-sweep shapes built: (consumer warps, ring slots)
+void *rows2_func(int cw, int slots, bool check)
+{
+    if (cw == 4)
+        return slots == 6 ? rows2_func_t<4, 6>(check) : rows2_func_t<4, 8>(check);
+    return slots == 4 ? rows2_func_t<8, 4>(check) : rows2_func_t<8, 6>(check);
+}
+
 template <int CW, int S>
 void *rows_func_t(bool check, bool write_p)
 {
@@ -294,6 +599,79 @@ cudaError_t node_pressure_rows(cudaGraphNode_t *n, cudaGraph_t g, const cudaGrap
     prm.gridDim = dim3((unsigned)grid);
     prm.blockDim = dim3((unsigned)rows_threads(width));
     prm.sharedMemBytes = (unsigned)rows_smem_bytes(width, slots, a.Fp != nullptr);
+    void *args[] = {(void *)&a, (void *)&H};
+    prm.kernelParams = args;
+    prm.extra = nullptr;
+    return cudaGraphAddKernelNode(n, g, dep, dep ? 1 : 0, &prm);
+}
+
+
+// ---- two sweeps per launch on staged rows ----------------------------------------------
+bool rows2_shape_ok(int cw, int slots)
+{
+    return (cw == 4 && (slots == 6 || slots == 8)) || (cw == 8 && (slots == 4 || slots == 6));
+}
+
+int rows2_width(int cw)
+{
+    return 30 * cw;
+}
+
+size_t rows2_smem_bytes(int cw, int slots, bool has_fp)
+{
+    const size_t rw = (size_t)rows2_width(cw) + 2 * lbm2p_dev::kRowsHalo;
+    return 128 + lbm2p_dev::kRowsBarBytes + (size_t)slots * (has_fp ? 11 : 10) * rw * sizeof(float) +
+           (size_t)cw * 3 * lbm2p_dev::kPairRowFloats * sizeof(float);
+}
+
+long long rows2_grid(int cw, int H, int nx, int ny)
+{
+    const int w = rows2_width(cw);
+    return (long long)((nx + w - 1) / w) * ((ny + H - 1) / H);
+}
+
+cudaError_t rows2_prepare(int cw, int slots)
+{
+    const int bytes = (int)rows2_smem_bytes(cw, slots, true);
+    for (bool c : {false, true}) {
+        cudaError_t e = cudaFuncSetAttribute(lbm2p_dev::rows2_func(cw, slots, c),
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e != cudaSuccess)
+            return e;
+    }
+    return cudaSuccess;
+}
+
+int rows2_blocks_per_sm(int cw, int slots, bool has_fp)
+{
+    int lo = 1 << 30;
+    for (bool c : {false, true}) {
+        int b = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, lbm2p_dev::rows2_func(cw, slots, c),
+                                                      32 * (cw + 1), rows2_smem_bytes(cw, slots, has_fp));
+        lo = b < lo ? b : lo;
+    }
+    return lo;
+}
+
+void pressure_sweeps_rows2(const PressureArgs &a, bool check, int cw, int slots, int H, int grid,
+                           void *stream)
+{
+    void *args[] = {(void *)&a, (void *)&H};
+    cudaLaunchKernel(lbm2p_dev::rows2_func(cw, slots, check), dim3(grid), dim3(32 * (cw + 1)), args,
+                     rows2_smem_bytes(cw, slots, a.Fp != nullptr),
+                     reinterpret_cast<cudaStream_t>(stream));
+}
+
+cudaError_t node_pressure_rows2(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
+                                const PressureArgs &a, bool check, int cw, int slots, int H,
+                                int grid)
+{
+    cudaKernelNodeParams prm{};
+    prm.func = lbm2p_dev::rows2_func(cw, slots, check);
+    prm.gridDim = dim3((unsigned)grid);
+    prm.blockDim = dim3((unsigned)(32 * (cw + 1)));
+    prm.sharedMemBytes = (unsigned)rows2_smem_bytes(cw, slots, a.Fp != nullptr);
     void *args[] = {(void *)&a, (void *)&H};
     prm.kernelParams = args;
     prm.extra = nullptr;

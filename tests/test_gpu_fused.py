@@ -42,15 +42,26 @@ def _problem(kind):
 
 @pytest.mark.parametrize("kind", ["five_spot_ragged", "wide_ragged", "periodic", "dirichlet",
                                   "mixed", "tiny", "column", "tall"])
-@pytest.mark.parametrize("T", [2, 4])
+@pytest.mark.parametrize("T", [2, 4, "2rows"])
 def test_fused_equals_single_sweeps(kind, T):
+    """T = 2 or 4 sweeps on shared-memory stages; "2rows": two sweeps on rows staged by
+    bulk copies (lattices with walls on every side only)."""
     import paper_1808_07554_gb300 as pkg
     prob = _problem(kind)
     single = pkg.Solver.from_problem(prob, init_replay=0, fuse_sweeps=1)
-    fused = pkg.Solver.from_problem(prob, init_replay=0, fuse_sweeps=T)
+    if T == "2rows":
+        if W.PERIODIC in prob.bc:
+            pytest.skip("the staged-rows two-sweep kernel needs walls on every side")
+        T = 2
+        fused = pkg.Solver.from_problem(prob, init_replay=0, fuse_sweeps=2,
+                                        sweep_kernel=pkg.SWEEP_ROWS)
+        cfg = fused.sweep_config()
+        assert cfg[0] == 2 and cfg[2] in (120, 240) and 1 <= cfg[3] <= 128
+    else:
+        fused = pkg.Solver.from_problem(prob, init_replay=0, fuse_sweeps=T)
+        cfg = fused.sweep_config()
+        assert cfg[0] == T and cfg[2] in (32, 64, 128, 120, 240) and 1 <= cfg[3] <= 128
     assert single.sweep_config()[0] == 1 and single.sweep_config()[1] in (1, 2, 3)
-    cfg = fused.sweep_config()
-    assert cfg[0] == T and cfg[2] in (32, 64, 128) and cfg[3] in (8, 16, 32, 64)
     rng = np.random.default_rng(3)
     state = single.get_state()
     state[:8] = 0.01 * rng.standard_normal(state[:8].shape)
