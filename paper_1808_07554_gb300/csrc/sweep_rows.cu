@@ -362,20 +362,41 @@ __global__ void __launch_bounds__(32 * (CW + 1)) k_pressure_rows2(const __grid_c
         // the first sweep is done with it
         float ra = 0.0f, rb = 0.0f, rc = 0.0f, tb = 0.0f, tc = 0.0f, qb = 0.0f, qc = 0.0f;
         float db = 0.0f, dc = 0.0f;
+        // wells in this lane's column (the source test runs only there)
+        bool wcol = false;
+        for (int w = 0; w < a.w.n; ++w)
+            wcol = wcol || (xin && a.w.idx[w] % p == x);
+        const bool xinner = x > 0 && x < g.nx - 1;
+        // slots and parity advance by increments (no division in the row loop): input rows
+        // t - 2, t - 1, t in slots qm, q0, qp; the warp's first-sweep rows rotate likewise
+        int q = 0, qm = 0, q0 = 0;
+        unsigned ph = 0u;
+        float *d_m = mine, *d_0 = mine + kPairRowFloats, *d_p = mine + 2 * kPairRowFloats;
         bool ok = true;
         for (int t = 0; t < nrows && ok; ++t) {
-            ok = bar_wait_bounded(full + t % S, (unsigned)(t / S) & 1u);
+            ok = bar_wait_bounded(full + q, ph);
+            const int qp = q;
+            if (++q == S) {
+                q = 0;
+                ph ^= 1u;
+            }
             if (!ok)
                 break;
-            if (t < 2)
+            if (t < 2) {
+                qm = q0;
+                q0 = qp;
                 continue;
+            }
             // first sweep at row ys from input rows ys - 1, ys, ys + 1 (arrivals t-2..t)
             const int ys = y0 - 3 + t;
             {
-                const float *sm = ring + (size_t)((t - 2) % S) * slot_floats;
-                const float *s0 = ring + (size_t)((t - 1) % S) * slot_floats;
-                const float *sp = ring + (size_t)(t % S) * slot_floats;
-                float *dst = mine + (t % 3) * kPairRowFloats;
+                const float *sm = ring + (size_t)qm * slot_floats;
+                const float *s0 = ring + (size_t)q0 * slot_floats;
+                const float *sp = ring + (size_t)qp * slot_floats;
+                float *dst = d_m;                    // the oldest first-sweep row is reused
+                d_m = d_0;
+                d_0 = d_p;
+                d_p = dst;
                 ra = rb;
                 rb = rc;
                 tb = tc;
@@ -386,7 +407,7 @@ __global__ void __launch_bounds__(32 * (CW + 1)) k_pressure_rows2(const __grid_c
                     const int o = ys * p + x;
                     const float r0 = s0[8 * RW + lx];
                     float f[8];
-                    if (interior(g, x, ys)) {
+                    if (xinner && ys > 0 && ys < g.ny - 1) {
                         f[0] = dev1(s0[0 * RW + lx - 1], wgt(1), s0[8 * RW + lx - 1], r0);
                         f[1] = dev1(sm[1 * RW + lx], wgt(2), sm[8 * RW + lx], r0);
                         f[2] = dev1(s0[2 * RW + lx + 1], wgt(3), s0[8 * RW + lx + 1], r0);
@@ -401,9 +422,10 @@ __global__ void __launch_bounds__(32 * (CW + 1)) k_pressure_rows2(const __grid_c
                     const float dP = pressure_of(f);
                     const float it = s0[9 * RW + lx];
                     float F = a.Fp ? s0[10 * RW + lx] : 0.0f;
-                    for (int w = 0; w < a.w.n; ++w)
-                        if (o == a.w.idx[w])
-                            F += a.w.fp[w];
+                    if (wcol)
+                        for (int w = 0; w < a.w.n; ++w)
+                            if (o == a.w.idx[w])
+                                F += a.w.fp[w];
                     const float Fq = 0.125f * F;   // w_bar_i = 1/8 (Eq. 3-5a)
 #pragma unroll
                     for (int i = 0; i < 8; ++i)
@@ -416,7 +438,9 @@ __global__ void __launch_bounds__(32 * (CW + 1)) k_pressure_rows2(const __grid_c
                 __syncwarp();
                 // input row t - 2 is no longer needed by this warp
                 if (lane == 0)
-                    bar_arrive(empty + (t - 2) % S);
+                    bar_arrive(empty + qm);
+                qm = q0;
+                q0 = qp;
             }
             if (t < 4)
                 continue;
@@ -433,12 +457,10 @@ __global__ void __launch_bounds__(32 * (CW + 1)) k_pressure_rows2(const __grid_c
             Rn.c2 = __shfl_down_sync(0xffffffffu, rb, 1);
             Rn.p2 = __shfl_down_sync(0xffffffffu, rc, 1);
             if (owner && y2 < g.ny) {
-                const float *n_m = mine + ((t - 2) % 3) * kPairRowFloats;
-                const float *n_0 = mine + ((t - 1) % 3) * kPairRowFloats;
-                const float *n_p = mine + (t % 3) * kPairRowFloats;
+                const float *n_m = d_m, *n_0 = d_0, *n_p = d_p;
                 const float r0 = rb;
                 float f[8];
-                if (interior(g, x, y2)) {
+                if (xinner && y2 > 0 && y2 < g.ny - 1) {
                     f[0] = dev1(n_0[0 * 32 + lane - 1], wgt(1), Rn.c0, r0);
                     f[1] = dev1(n_m[1 * 32 + lane], wgt(2), Rn.m1, r0);
                     f[2] = dev1(n_0[2 * 32 + lane + 1], wgt(3), Rn.c2, r0);
