@@ -397,7 +397,11 @@ def run_ours(args):
                      "kernel": ("pressure sweep (fused stream + collide, Eq. 3-1), "
                                 + (("FP16 populations, " + SWEEP_KERNEL_NAMES.get(sweep_cfg[1], "?"))
                                    if args.storage == "fp16"
-                                   else (f"{fused} sweeps per launch" if fused > 1 else
+                                   else ((f"{fused} sweeps per launch"
+                                          + (" on rows staged by bulk copies"
+                                             if sweep_cfg[2] in (120, 240) else
+                                             " on shared-memory stages"))
+                                         if fused > 1 else
                                          SWEEP_KERNEL_NAMES.get(sweep_cfg[1], "?"))
                                    + (", autotuned" if args.sweep_kernel == 0 else ""))),
                      "bytes_per_launch": bpn * nodes,
