@@ -55,11 +55,14 @@ WORKLOADS = {
 SWEEP_KERNEL_NAMES = {1: "four nodes per thread (128-bit accesses)", 2: "one node per thread",
                       3: "rows staged in shared memory by bulk async copies"}
 # DRAM bytes per pressure-sweep launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum),
-# keyed by workload; None until captured for the current kernel.
-# five_spot_1024: k_pressure_scalar<0,0> (the kernel the autotuner picks there), 42.0 MB read +
-# 0.9 MB written per launch, L2 flushed by ncu before the launch (profiles/).
-NCU_TRAFFIC_PER_SWEEP = {"five_spot_1024": 42.87e6, "five_spot_4096": None, "manufactured_64": None,
-                         "batch_five_spot_64": None}
+# keyed by workload and launch form (sweeps per launch, fused tile width or single kernel
+# kind); absent until captured for the current kernel (profiles/).
+# five_spot_1024, one node per thread (the autotuner's choice there): 42.0 MB read + 0.9 MB
+# written per launch, L2 flushed by ncu before the launch.
+# five_spot_4096, two sweeps on staged rows, 120-column blocks (the autotuner's choice there):
+# 702.1 MB read + 493.3 MB written per launch (a launch without the residual).
+NCU_TRAFFIC_PER_LAUNCH = {("five_spot_1024", 1, 2): 42.87e6,
+                          ("five_spot_4096", 2, 120): 1195.4e6}
 
 
 def batch_members(name: str, rank: int = 0):
@@ -370,10 +373,10 @@ def run_ours(args):
     avg_launch_s = avg_sweep_s * fused
     bpn = BYTES_PER_SWEEP_NODE_FP16 if args.storage == "fp16" else BYTES_PER_SWEEP_NODE
     achieved = bpn * nodes / avg_launch_s / 1e9
-    # the captured traffic belongs to the one-node-per-thread FP32 sweep; any other choice
-    # of the autotuner has no capture here
-    traffic = (NCU_TRAFFIC_PER_SWEEP.get(args.workload)
-               if args.storage == "fp32" and sweep_cfg[0] == 1 and sweep_cfg[1] == 2 else None)
+    # the captured traffic belongs to one FP32 launch form; any other choice of the
+    # autotuner has no capture here
+    form = (args.workload, fused, sweep_cfg[2] if fused > 1 else sweep_cfg[1])
+    traffic = NCU_TRAFFIC_PER_LAUNCH.get(form) if args.storage == "fp32" else None
     line = {
         "metric": "MLUPS", "value": updates_all / time_max / 1e6, "unit": "MLUPS",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -554,7 +557,7 @@ def run_batch(args):
                    "parallelism": f"{world} x {len(probs)} independent realisations"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
-                     "traffic": NCU_TRAFFIC_PER_SWEEP.get(args.workload),
+                     "traffic": None,
                      "kernel": "whole batched step (kb_sweep dominant): algorithmic bytes of "
                                "every kernel / step time",
                      "bytes_per_step": step_bytes / args.steps, "peak_kind": peak_kind},
