@@ -88,6 +88,37 @@ def test_fp16_kernels_agree_bit_for_bit(name):
             assert rb == pytest.approx(ra, rel=1e-3, abs=1e-30)
 
 
+def test_fp16_and_fp32_on_a_256_crop_of_the_4096_field():
+    """The precision study at matching resolution: the 4096^2 five-spot's ln K field (same
+    seed rule), cropped to its first 256 x 256 nodes, run with FP32 and with FP16 storage on
+    the oracle's sweep counts; every field against the FP64 oracle, FP32 to 1e-5 and FP16 to
+    2e-3."""
+    import paper_1808_07554_gb300 as pkg
+    big = W.quarter_five_spot(4096, seed=2)
+    prob = W.quarter_five_spot(256, seed=2)
+    prob.K = np.ascontiguousarray(big.K[:256, :256])
+    del big
+    # a fixed number of sweeps for the t = 0 solve and for each step (a converged start would
+    # take ~2e5 oracle sweeps); both sides run the same counts
+    log = [4000] + [400] * 6
+    orc = O.Oracle(prob, tol=1e-8, check_every=8, init_replay=log[0])
+    for c in log[1:]:
+        orc.step(1, replay=[c])
+    errs = {}
+    for name, storage in (("fp32", pkg.STORE_FP32), ("fp16", pkg.STORE_FP16_DEV)):
+        gpu = pkg.Solver.from_problem(prob, tol=1e-8, check_every=8, init_replay=log[0],
+                                      storage=storage)
+        for c in log[1:]:
+            gst, stats = gpu.step(1, replay=[c])
+            assert stats[0].sub_iters == c
+        errs[name] = compare(orc, gpu, gauge_free=True)
+        gpu.close()
+    orc.close()
+    print("256 crop of the 4096 field", errs)
+    assert all(v <= 1e-5 for v in errs["fp32"].values()), errs
+    assert all(v <= TOL16 for v in errs["fp16"].values()), errs
+
+
 def test_fp16_and_fp32_storage_agree_on_the_same_counts():
     import paper_1808_07554_gb300 as pkg
     prob = W.quarter_five_spot(128, seed=9, corr_len=12.0)
