@@ -210,20 +210,20 @@ __global__ void __launch_bounds__(32 * (CW + 1)) k_pressure_rows(const __grid_co
 // The producer stages input rows exactly as above.  Consumer warp w owns the 30 output
 // columns [x0 + 30 w, x0 + 30 w + 30) of a strip of W = 30 CW columns; its 32 lanes compute
 // the first sweep on those columns plus one on each side (the halo the second sweep pulls
-// from), into a warp-private ring of three rows in shared memory, and lanes 1..30 compute
-// the second sweep from that ring one row behind, writing the populations to global memory.
-// Input row t (y = y0 - 2 + t) feeds the first sweep at rows y - 1 .. y + 1; a warp releases
-// it after the first sweep at row y + 1.  The second sweep at row y takes R, 1/tau_f and
-// w_bar F~_p of its node from the lane's registers (kept from its first-sweep rows) and R of
-// the neighbouring columns by warp shuffles.
+// from), row after row, and lanes 1..30 compute the second sweep one row behind, writing the
+// populations to global memory.  Each lane keeps its column's first-sweep values of the
+// last rows in registers (all eight of the previous row, the three pulled from below of the
+// row before); a pull from a neighbouring column takes the neighbour lane's value by a warp
+// shuffle, so the two sweeps exchange nothing through shared memory.  Input row t
+// (y = y0 - 2 + t) feeds the first sweep at rows y - 1 .. y + 1; a warp releases it after the
+// first sweep at row y + 1.  The second sweep at row y takes R, 1/tau_f and w_bar F~_p of its
+// node from the lane's registers and R of the neighbouring columns by shuffles.
 // A node on a wall applies the wall rules of Sec. 4 to its own first-sweep values.  Both
 // sweeps use the per-node arithmetic of the single sweep, so the result equals two single
 // sweeps bit for bit.  CHECK: the residual sums of the second sweep against the first
 // (no increment plane).  Waits are bounded as in k_pressure_rows; a warp that gives up
 // poisons its columns with NaN.
 // ---------------------------------------------------------------------------------------
-constexpr int kPairRowFloats = 9 * 32;        // first-sweep row of a warp: 8 planes + dP
-
 // R around the node, rows y - 1 (m), y (c), y + 1 (p) and columns x - 1 (0), x (1), x + 1 (2)
 struct RNbhd {
     float m0, m1, m2, c0, c1, c2, p0, p1, p2;
@@ -238,12 +238,13 @@ struct RNbhd {
     }
 };
 
-// a_I of the second sweep at a wall node: the first sweep's value of the neighbour x - c_I
-// (in this warp's ring), or the wall rule of Sec. 4 on the node's own first-sweep values
+// a_I of the second sweep at a wall node: the first sweep's value nb of the neighbour
+// x - c_I (already fetched from that neighbour's lane), or the wall rule of Sec. 4 on the
+// node's own first-sweep value own_opp of direction opp(I)
 template <int I>
-__device__ __forceinline__ float second_pull(const float *n_m, const float *n_0, const float *n_p,
-                                             const RNbhd &R, const Geom &g, const float *const *Pb,
-                                             int x, int y, int lane, float r0)
+__device__ __forceinline__ float second_pull(float nb, float own_opp, const RNbhd &R,
+                                             const Geom &g, const float *const *Pb, int x, int y,
+                                             float r0)
 {
     constexpr int ex = cx(I), ey = cy(I);
     int side = -1;
@@ -251,11 +252,9 @@ __device__ __forceinline__ float second_pull(const float *n_m, const float *n_0,
         side = x - ex < 0 ? 0 : 1;
     else if (y - ey < 0 || y - ey >= g.ny)
         side = y - ey < 0 ? 2 : 3;
-    if (side < 0) {
-        const float *row = ey == 1 ? n_m : (ey == -1 ? n_p : n_0);
-        return dev1(row[(I - 1) * 32 + lane - ex], wgt(I), R.at(ex, ey), r0);
-    }
-    const float b = n_0[(opp(I) - 1) * 32 + lane];
+    if (side < 0)
+        return dev1(nb, wgt(I), R.at(ex, ey), r0);
+    const float b = own_opp;
     if (g.bc[side] == BC_NOFLUX)
         return b;
     const int k = side < 2 ? 2 * y + 1 - ey : 2 * x + 1 - ex;
@@ -275,7 +274,6 @@ __global__ void __launch_bounds__(32 * (CW + 1)) k_pressure_rows2(const __grid_c
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
     uint64_t *empty = full + S;
     float *ring = reinterpret_cast<float *>(smem + kRowsBarBytes);
-    float *first = ring + (size_t)S * slot_floats;   // CW warps x 3 rows x kPairRowFloats
     __shared__ double red[CW][4];
     __shared__ int failed;
     const Geom &g = a.g;
@@ -351,7 +349,6 @@ __global__ void __launch_bounds__(32 * (CW + 1)) k_pressure_rows2(const __grid_c
         const float shift = CHECK ? a.shift[0] : 0.0f;
         const float dshift = CHECK ? a.shift[1] : 0.0f;
         ResAcc racc;
-        float *mine = first + (size_t)warp * 3 * kPairRowFloats;
         const int x = x0 - 1 + 30 * warp + lane;    // this lane's column (both sweeps)
         const int lx = x - (x0 - kRowsHalo);        // its column in a staged row
         const bool xin = x >= 0 && x < g.nx;
@@ -362,16 +359,23 @@ __global__ void __launch_bounds__(32 * (CW + 1)) k_pressure_rows2(const __grid_c
         // the first sweep is done with it
         float ra = 0.0f, rb = 0.0f, rc = 0.0f, tb = 0.0f, tc = 0.0f, qb = 0.0f, qc = 0.0f;
         float db = 0.0f, dc = 0.0f;
+        // first-sweep populations of this lane's column: v = the newest row, h1 = the one
+        // before (all planes: the wall rules read the node's own values), h2 = the one before
+        // that (only the planes pulled from the row below: directions 2, 5, 6)
+        float v[8], h1[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            v[i] = h1[i] = 0.0f;
+        float h2_1 = 0.0f, h2_4 = 0.0f, h2_5 = 0.0f;
         // wells in this lane's column (the source test runs only there)
         bool wcol = false;
         for (int w = 0; w < a.w.n; ++w)
             wcol = wcol || (xin && a.w.idx[w] % p == x);
         const bool xinner = x > 0 && x < g.nx - 1;
         // slots and parity advance by increments (no division in the row loop): input rows
-        // t - 2, t - 1, t in slots qm, q0, qp; the warp's first-sweep rows rotate likewise
+        // t - 2, t - 1, t in slots qm, q0, qp
         int q = 0, qm = 0, q0 = 0;
         unsigned ph = 0u;
-        float *d_m = mine, *d_0 = mine + kPairRowFloats, *d_p = mine + 2 * kPairRowFloats;
         bool ok = true;
         for (int t = 0; t < nrows && ok; ++t) {
             ok = bar_wait_bounded(full + q, ph);
@@ -393,10 +397,14 @@ __global__ void __launch_bounds__(32 * (CW + 1)) k_pressure_rows2(const __grid_c
                 const float *sm = ring + (size_t)qm * slot_floats;
                 const float *s0 = ring + (size_t)q0 * slot_floats;
                 const float *sp = ring + (size_t)qp * slot_floats;
-                float *dst = d_m;                    // the oldest first-sweep row is reused
-                d_m = d_0;
-                d_0 = d_p;
-                d_p = dst;
+                h2_1 = h1[1];
+                h2_4 = h1[4];
+                h2_5 = h1[5];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    h1[i] = v[i];
+                    v[i] = 0.0f;
+                }
                 ra = rb;
                 rb = rc;
                 tb = tc;
@@ -429,7 +437,7 @@ __global__ void __launch_bounds__(32 * (CW + 1)) k_pressure_rows2(const __grid_c
                     const float Fq = 0.125f * F;   // w_bar_i = 1/8 (Eq. 3-5a)
 #pragma unroll
                     for (int i = 0; i < 8; ++i)
-                        dst[i * 32 + lane] = collide1(f[i], wgt(i + 1), dP, it, Fq);
+                        v[i] = collide1(f[i], wgt(i + 1), dP, it, Fq);
                     rc = r0;
                     tc = it;
                     qc = Fq;
@@ -444,7 +452,8 @@ __global__ void __launch_bounds__(32 * (CW + 1)) k_pressure_rows2(const __grid_c
             }
             if (t < 4)
                 continue;
-            // second sweep at row y2 = ys - 1 from the first sweep's rows y2 - 1, y2, y2 + 1
+            // second sweep at row y2 = ys - 1 from the first sweep's rows y2 - 1, y2, y2 + 1:
+            // the neighbour x - c_i of each pull sits in this lane or the next one over
             const int y2 = ys - 1;
             RNbhd Rn;
             Rn.m1 = ra;
@@ -456,28 +465,36 @@ __global__ void __launch_bounds__(32 * (CW + 1)) k_pressure_rows2(const __grid_c
             Rn.m2 = __shfl_down_sync(0xffffffffu, ra, 1);
             Rn.c2 = __shfl_down_sync(0xffffffffu, rb, 1);
             Rn.p2 = __shfl_down_sync(0xffffffffu, rc, 1);
+            float nb[8];
+            nb[0] = __shfl_up_sync(0xffffffffu, h1[0], 1);     // 1: from (x-1, y2)
+            nb[1] = h2_1;                                      // 2: from (x, y2-1)
+            nb[2] = __shfl_down_sync(0xffffffffu, h1[2], 1);   // 3: from (x+1, y2)
+            nb[3] = v[3];                                      // 4: from (x, y2+1)
+            nb[4] = __shfl_up_sync(0xffffffffu, h2_4, 1);      // 5: from (x-1, y2-1)
+            nb[5] = __shfl_down_sync(0xffffffffu, h2_5, 1);    // 6: from (x+1, y2-1)
+            nb[6] = __shfl_down_sync(0xffffffffu, v[6], 1);    // 7: from (x+1, y2+1)
+            nb[7] = __shfl_up_sync(0xffffffffu, v[7], 1);      // 8: from (x-1, y2+1)
             if (owner && y2 < g.ny) {
-                const float *n_m = d_m, *n_0 = d_0, *n_p = d_p;
                 const float r0 = rb;
                 float f[8];
                 if (xinner && y2 > 0 && y2 < g.ny - 1) {
-                    f[0] = dev1(n_0[0 * 32 + lane - 1], wgt(1), Rn.c0, r0);
-                    f[1] = dev1(n_m[1 * 32 + lane], wgt(2), Rn.m1, r0);
-                    f[2] = dev1(n_0[2 * 32 + lane + 1], wgt(3), Rn.c2, r0);
-                    f[3] = dev1(n_p[3 * 32 + lane], wgt(4), Rn.p1, r0);
-                    f[4] = dev1(n_m[4 * 32 + lane - 1], wgt(5), Rn.m0, r0);
-                    f[5] = dev1(n_m[5 * 32 + lane + 1], wgt(6), Rn.m2, r0);
-                    f[6] = dev1(n_p[6 * 32 + lane + 1], wgt(7), Rn.p2, r0);
-                    f[7] = dev1(n_p[7 * 32 + lane - 1], wgt(8), Rn.p0, r0);
+                    f[0] = dev1(nb[0], wgt(1), Rn.c0, r0);
+                    f[1] = dev1(nb[1], wgt(2), Rn.m1, r0);
+                    f[2] = dev1(nb[2], wgt(3), Rn.c2, r0);
+                    f[3] = dev1(nb[3], wgt(4), Rn.p1, r0);
+                    f[4] = dev1(nb[4], wgt(5), Rn.m0, r0);
+                    f[5] = dev1(nb[5], wgt(6), Rn.m2, r0);
+                    f[6] = dev1(nb[6], wgt(7), Rn.p2, r0);
+                    f[7] = dev1(nb[7], wgt(8), Rn.p0, r0);
                 } else {
-                    f[0] = second_pull<1>(n_m, n_0, n_p, Rn, g, a.Pb, x, y2, lane, r0);
-                    f[1] = second_pull<2>(n_m, n_0, n_p, Rn, g, a.Pb, x, y2, lane, r0);
-                    f[2] = second_pull<3>(n_m, n_0, n_p, Rn, g, a.Pb, x, y2, lane, r0);
-                    f[3] = second_pull<4>(n_m, n_0, n_p, Rn, g, a.Pb, x, y2, lane, r0);
-                    f[4] = second_pull<5>(n_m, n_0, n_p, Rn, g, a.Pb, x, y2, lane, r0);
-                    f[5] = second_pull<6>(n_m, n_0, n_p, Rn, g, a.Pb, x, y2, lane, r0);
-                    f[6] = second_pull<7>(n_m, n_0, n_p, Rn, g, a.Pb, x, y2, lane, r0);
-                    f[7] = second_pull<8>(n_m, n_0, n_p, Rn, g, a.Pb, x, y2, lane, r0);
+                    f[0] = second_pull<1>(nb[0], h1[opp(1) - 1], Rn, g, a.Pb, x, y2, r0);
+                    f[1] = second_pull<2>(nb[1], h1[opp(2) - 1], Rn, g, a.Pb, x, y2, r0);
+                    f[2] = second_pull<3>(nb[2], h1[opp(3) - 1], Rn, g, a.Pb, x, y2, r0);
+                    f[3] = second_pull<4>(nb[3], h1[opp(4) - 1], Rn, g, a.Pb, x, y2, r0);
+                    f[4] = second_pull<5>(nb[4], h1[opp(5) - 1], Rn, g, a.Pb, x, y2, r0);
+                    f[5] = second_pull<6>(nb[5], h1[opp(6) - 1], Rn, g, a.Pb, x, y2, r0);
+                    f[6] = second_pull<7>(nb[6], h1[opp(7) - 1], Rn, g, a.Pb, x, y2, r0);
+                    f[7] = second_pull<8>(nb[7], h1[opp(8) - 1], Rn, g, a.Pb, x, y2, r0);
                 }
                 const int o = y2 * p + x;
                 const float dP = pressure_of(f);
@@ -487,7 +504,6 @@ __global__ void __launch_bounds__(32 * (CW + 1)) k_pressure_rows2(const __grid_c
                 if (CHECK)
                     racc.add((dP - db) - dshift, (r0 - shift) + dP);
             }
-            __syncwarp();
         }
         if (!ok) {
             failed = 1;
@@ -642,8 +658,7 @@ int rows2_width(int cw)
 size_t rows2_smem_bytes(int cw, int slots, bool has_fp)
 {
     const size_t rw = (size_t)rows2_width(cw) + 2 * lbm2p_dev::kRowsHalo;
-    return 128 + lbm2p_dev::kRowsBarBytes + (size_t)slots * (has_fp ? 11 : 10) * rw * sizeof(float) +
-           (size_t)cw * 3 * lbm2p_dev::kPairRowFloats * sizeof(float);
+    return 128 + lbm2p_dev::kRowsBarBytes + (size_t)slots * (has_fp ? 11 : 10) * rw * sizeof(float);
 }
 
 long long rows2_grid(int cw, int H, int nx, int ny)
