@@ -262,7 +262,7 @@ __device__ __forceinline__ float second_pull(float nb, float own_opp, const RNbh
 }
 
 template <bool CHECK, int CW, int S>
-__global__ void __launch_bounds__(32 * (CW + 1)) k_pressure_rows2(const __grid_constant__ PressureArgs a,
+__global__ void __launch_bounds__(32 * (CW + 1), CW == 4 ? 6 : 3) k_pressure_rows2(const __grid_constant__ PressureArgs a,
                                                                   int H)
 {
     constexpr int W = 30 * CW;
