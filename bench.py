@@ -60,9 +60,9 @@ SWEEP_KERNEL_NAMES = {1: "four nodes per thread (128-bit accesses)", 2: "one nod
 # five_spot_1024, one node per thread (the autotuner's choice there): 42.0 MB read + 0.9 MB
 # written per launch, L2 flushed by ncu before the launch.
 # five_spot_4096, two sweeps on staged rows, 120-column blocks (the autotuner's choice there):
-# 702.1 MB read + 493.3 MB written per launch (a launch without the residual).
+# 720.9 MB read + 493.1 MB written per launch (a launch without the residual).
 NCU_TRAFFIC_PER_LAUNCH = {("five_spot_1024", 1, 2): 42.87e6,
-                          ("five_spot_4096", 2, 120): 1195.4e6}
+                          ("five_spot_4096", 2, 120): 1214.0e6}
 
 
 def batch_members(name: str, rank: int = 0):
