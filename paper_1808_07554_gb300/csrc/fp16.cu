@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(kBlock) k_pressure_h(const __grid_constant__ H
     const Geom &g = a.g;
     const int lane = threadIdx.x & 31;
     const float s = a.scale[0], inv_s = a.scale[1];
-    double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
+    ResAcc racc;                                  // residual sums of this thread
     float nmax = 0.0f;
     const float shift = CHECK ? a.shift[0] : 0.0f;
     const float dshift = CHECK ? a.shift[1] : 0.0f;
@@ -212,18 +212,10 @@ __global__ void __launch_bounds__(kBlock) k_pressure_h(const __grid_constant__ H
             if (CHECK) {
                 d = dP - dshift;
                 q = (r0 - shift) + dP;
+                racc.add(d, q);
 #pragma unroll
                 for (int i = 0; i < 8; ++i)
                     nmax = fmaxf(nmax, fabsf(__half2float(a.nout[i][o])));
-            }
-        }
-        if (CHECK) {
-            const float s0 = warp_sum(d), s1 = warp_sum(d * d), s2 = warp_sum(q), s3 = warp_sum(q * q);
-            if (lane == 0) {
-                acc0 += s0;
-                acc1 += s1;
-                acc2 += s2;
-                acc3 += s3;
             }
         }
     }
@@ -238,11 +230,13 @@ __global__ void __launch_bounds__(kBlock) k_pressure_h(const __grid_constant__ H
     if (CHECK) {
         __shared__ double red[kBlock / 32][4];
         const int warp = threadIdx.x >> 5;
+        double v[4];
+        racc.warp_totals(v);
         if (lane == 0) {
-            red[warp][0] = acc0;
-            red[warp][1] = acc1;
-            red[warp][2] = acc2;
-            red[warp][3] = acc3;
+            red[warp][0] = v[0];
+            red[warp][1] = v[1];
+            red[warp][2] = v[2];
+            red[warp][3] = v[3];
         }
         __syncthreads();
         if (threadIdx.x < 4) {
@@ -358,7 +352,7 @@ __global__ void __launch_bounds__(32 * (CW + 1)) k_pressure_rows_h(const __grid_
         const float s = a.scale[0], inv_s = a.scale[1];
         const float shift = CHECK ? a.shift[0] : 0.0f;
         const float dshift = CHECK ? a.shift[1] : 0.0f;
-        double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
+        ResAcc racc;                          // residual sums of this lane over its rows
         float nmax = 0.0f;
         const int col = warp * 32 + lane;
         const int lh = col + kHaloH, lf = col + kHaloF;
@@ -422,16 +416,7 @@ __global__ void __launch_bounds__(32 * (CW + 1)) k_pressure_rows_h(const __grid_
                 if (CHECK) {
                     d = dP - dshift;
                     q = (r0 - shift) + dP;
-                }
-            }
-            if (CHECK) {
-                const float s0s = warp_sum(d), s1s = warp_sum(d * d);
-                const float s2s = warp_sum(q), s3s = warp_sum(q * q);
-                if (lane == 0) {
-                    acc0 += s0s;
-                    acc1 += s1s;
-                    acc2 += s2s;
-                    acc3 += s3s;
+                    racc.add(d, q);
                 }
             }
             __syncwarp();
@@ -450,11 +435,13 @@ __global__ void __launch_bounds__(32 * (CW + 1)) k_pressure_rows_h(const __grid_
 #pragma unroll
             for (int sh = 16; sh > 0; sh >>= 1)
                 nmax = fmaxf(nmax, __shfl_xor_sync(0xffffffffu, nmax, sh));
+            double v[4];
+            racc.warp_totals(v);
             if (lane == 0) {
-                red[warp][0] = acc0;
-                red[warp][1] = acc1;
-                red[warp][2] = acc2;
-                red[warp][3] = acc3;
+                red[warp][0] = v[0];
+                red[warp][1] = v[1];
+                red[warp][2] = v[2];
+                red[warp][3] = v[3];
                 wmax[warp] = nmax;
             }
         }
