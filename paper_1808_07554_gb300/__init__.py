@@ -486,9 +486,18 @@ class Solver:
         return out
 
     # -- outputs --------------------------------------------------------------------------
-    def fields(self, mean_free_P=False):
-        P = np.empty((self.ny, self.nx), np.float32)
-        S = np.empty((self.ny, self.nx), np.float32)
+    def fields(self, mean_free_P=False, out=None):
+        """P and S of the current time level as float32 [ny, nx] host arrays; ``out`` = a
+        pair of C-contiguous float32 arrays of that shape to fill instead (page-locked ones
+        make the copy a direct DMA)."""
+        if out is None:
+            P = np.empty((self.ny, self.nx), np.float32)
+            S = np.empty((self.ny, self.nx), np.float32)
+        else:
+            P, S = out
+            for a in (P, S):
+                if a.dtype != np.float32 or a.shape != (self.ny, self.nx) or not a.flags.c_contiguous:
+                    raise ValueError("out arrays must be C-contiguous float32 of shape (ny, nx)")
         lbm2p_fields(self.h, _fp(P), _fp(S), int(bool(mean_free_P)), 0)
         return P, S
 
