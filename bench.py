@@ -61,8 +61,11 @@ SWEEP_KERNEL_NAMES = {1: "four nodes per thread (128-bit accesses)", 2: "one nod
 # written per launch, L2 flushed by ncu before the launch.
 # five_spot_4096, two sweeps on staged rows, 120-column blocks (the autotuner's choice there):
 # 720.9 MB read + 493.1 MB written per launch (a launch without the residual).
-NCU_TRAFFIC_PER_LAUNCH = {("five_spot_1024", 1, 2): 42.87e6,
-                          ("five_spot_4096", 2, 120): 1214.0e6}
+NCU_TRAFFIC_PER_LAUNCH = {("five_spot_1024", "single", 2): 42.87e6,
+                          ("five_spot_4096", "staged_rows", 120): 1214.0e6}
+FUSED_FORM_NAMES = {1: "stages", 2: "staged_rows", 3: "direct"}
+FUSED_FORM_TEXT = {1: "on shared-memory stages", 2: "on rows staged by bulk copies",
+                   3: "with direct loads"}
 
 
 def batch_members(name: str, rank: int = 0):
@@ -298,6 +301,7 @@ def run_ours(args):
     init_sweeps = solver.init_stats.sub_iters
     solver.set_timing(True)
     sweep_cfg = solver.sweep_config()
+    fform = solver.fused_form()
 
     # problems with time-dependent sources get them uploaded every step (host buffers)
     def upload(n):
@@ -378,7 +382,8 @@ def run_ours(args):
     achieved = bpn * nodes / avg_launch_s / 1e9
     # the captured traffic belongs to one FP32 launch form; any other choice of the
     # autotuner has no capture here
-    form = (args.workload, fused, sweep_cfg[2] if fused > 1 else sweep_cfg[1])
+    form = ((args.workload, FUSED_FORM_NAMES.get(fform, "?"), sweep_cfg[2]) if fused > 1
+            else (args.workload, "single", sweep_cfg[1]))
     traffic = NCU_TRAFFIC_PER_LAUNCH.get(form) if args.storage == "fp32" else None
     line = {
         "metric": "MLUPS", "value": updates_all / time_max / 1e6, "unit": "MLUPS",
@@ -390,6 +395,7 @@ def run_ours(args):
                    "storage": args.storage, "warm_start": args.warm_start,
                    "check_every": args.check_every, "fuse_sweeps": args.fuse_sweeps,
                    "sweep_kernel": sweep_cfg[1], "sweep_tile": [sweep_cfg[2], sweep_cfg[3]],
+                   "fused_form": FUSED_FORM_NAMES.get(fform, "none"),
                    "l2": "flushed before every timed step",
                    "sub_iters_per_step": ksub, "statuses": statuses,
                    "init_sweeps": init_sweeps, "setup_s": round(setup_s, 2),
@@ -403,10 +409,8 @@ def run_ours(args):
                      "kernel": ("pressure sweep (fused stream + collide, Eq. 3-1), "
                                 + (("FP16 populations, " + SWEEP_KERNEL_NAMES.get(sweep_cfg[1], "?"))
                                    if args.storage == "fp16"
-                                   else ((f"{fused} sweeps per launch"
-                                          + (" on rows staged by bulk copies"
-                                             if sweep_cfg[2] in (120, 240) else
-                                             " on shared-memory stages"))
+                                   else ((f"{fused} sweeps per launch "
+                                          + FUSED_FORM_TEXT.get(fform, "?"))
                                          if fused > 1 else
                                          SWEEP_KERNEL_NAMES.get(sweep_cfg[1], "?"))
                                    + (", autotuned" if args.sweep_kernel == 0 else ""))),

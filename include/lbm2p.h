@@ -42,7 +42,7 @@
 extern "C" {
 #endif
 
-#define LBM2P_ABI_VERSION 5
+#define LBM2P_ABI_VERSION 6
 /* Sparse wells passed to the sweep kernels as launch arguments (more wells: error). */
 #define LBM2P_MAX_WELLS 16
 
@@ -131,8 +131,9 @@ typedef struct {
                                    tile shapes on the lattice and keeps the fastest.  Fused
                                    kernels: T = 2 or 4 sweeps on shared-memory stages, and, on
                                    lattices with walls on every side, 2 sweeps on rows staged
-                                   by bulk copies (fuse_sweeps 2 with sweep_kernel ROWS pins
-                                   the latter). */
+                                   by bulk copies and 2 sweeps with direct loads (fuse_sweeps
+                                   2 with sweep_kernel ROWS pins the former, with SCALAR the
+                                   latter). */
     int sweep_kernel;           /* lbm2p_sweep_kernel: the single-sweep kernel (AUTO: timed) */
     int sat_lattice;            /* saturation lattice: 9 (D2Q9, Eq. 3-4) or 5 (D2Q5, Remark V,
                                    Eq. 3-4b, weights 1/3 and 1/6; needs beta <= 1.5 phi) */
@@ -247,17 +248,28 @@ lbm2p_status lbm2p_set_timing(lbm2p *h, int enable);
 /* How the pressure sweeps run on this handle, as chosen at create: sweeps fused per launch
    (1, 2 or 4); the single-sweep kernel (an lbm2p_sweep_kernel value, never AUTO); the tile
    of the kernel that runs the sweeps: for fused sweeps its threads per block (columns per
-   block for the staged-rows two-sweep kernel: 120 or 240) and rows per block, for the ROWS
+   block for the two-sweep row-walking kernels: 120 or 240) and rows per block, for the ROWS
    kernel its strip width and rows per block, otherwise 0 and 0. */
 lbm2p_status lbm2p_sweep_config(const lbm2p *h, int *fused, int *kind, int *tile_w, int *tile_h);
+
+/* Which fused kernel runs the sweeps when lbm2p_sweep_config reports fused > 1. */
+typedef enum {
+    LBM2P_FUSED_NONE = 0,        /* single sweeps */
+    LBM2P_FUSED_STAGES = 1,      /* T sweeps on shared-memory stages (T = 2 or 4) */
+    LBM2P_FUSED_STAGED_ROWS = 2, /* two sweeps on rows staged by bulk copies */
+    LBM2P_FUSED_DIRECT = 3       /* two sweeps, inputs loaded directly (lattices held in L2) */
+} lbm2p_fused_form;
+int lbm2p_fused_form_of(const lbm2p *h);
 
 /* The candidates create timed to choose the sweep kernel, one line each:
  *   "single_vec4 <grid> 0 0 0 <us>", "single_scalar <grid> 0 0 0 <us>",
  *   "single_rows <strip width> <ring slots> <rows per block> <grid> <us>",
  *   "fused <sweeps per launch> <threads per block> <rows per block> <grid> <us>",
- *   "fused_rows <consumer warps> <ring slots> <rows per block> <grid> <us>"
- * with <us> the time per sweep (the first two kinds once per grid tried: the resident-block
- * capacity of the GPU down to half of it).  Owned by h; valid until the next create-time tuning. */
+ *   "fused_rows <consumer warps> <ring slots> <rows per block> <grid> <us>",
+ *   "fused_direct <warps> 0 <rows per block> <grid> <us>"
+ * with <us> the time per sweep inside the solve loop: a check period of check_every sweeps
+ * timed as its plain launches plus the one launch that also sums the residual (the first two
+ * kinds once per grid tried: the resident-block capacity of the GPU down to half of it).  Owned by h; valid until the next create-time tuning. */
 const char *lbm2p_autotune_report(const lbm2p *h);
 
 /* Running totals since creation: kernels launched by the library, pressure sweeps run. */

@@ -105,6 +105,7 @@ def load_library(path: str = LIB_PATH):
         "lbm2p_set_timing": (C.c_int, [H, C.c_int]),
         "lbm2p_counters": (C.c_int, [H, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
         "lbm2p_sweep_config": (C.c_int, [H] + [C.POINTER(C.c_int)] * 4),
+        "lbm2p_fused_form_of": (C.c_int, [H]),
         "lbm2p_autotune_report": (C.c_char_p, [H]),
         "lbm2p_warm_start": (C.c_int, [H, fp, C.c_int]),
         "lbm2p_pressure_sweep_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int),
@@ -231,6 +232,14 @@ def lbm2p_pressure_sweep_noalloc(nx, ny, pitch, bc, n_in, n_out, R, inv_tau, Fp,
         cast(dP), C.byref(r), C.c_void_p(stream) if stream else None)
     _check(st, None)
     return r.value
+
+
+FUSED_NONE, FUSED_STAGES, FUSED_STAGED_ROWS, FUSED_DIRECT = 0, 1, 2, 3
+
+
+def lbm2p_fused_form_of(h):
+    """Which fused kernel runs the sweeps (FUSED_*)."""
+    return _lib_or_raise().lbm2p_fused_form_of(h)
 
 
 def lbm2p_sweep_config(h):
@@ -476,6 +485,9 @@ class Solver:
 
     def sweep_config(self):
         return lbm2p_sweep_config(self.h)
+
+    def fused_form(self):
+        return lbm2p_fused_form_of(self.h)
 
     def autotune_report(self):
         """[(candidate, a1, a2, a3, a4, us per sweep)] as timed at create."""

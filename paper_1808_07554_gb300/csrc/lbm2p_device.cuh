@@ -272,6 +272,13 @@ void pressure_sweeps_rows2(const PressureArgs &a, bool check, int cw, int slots,
 cudaError_t node_pressure_rows2(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
                                 const PressureArgs &a, bool check, int cw, int slots, int H,
                                 int grid);
+// two sweeps per launch with direct loads (sweep_rows.cu), lattices without periodic sides:
+// cw warps of 30 owned columns (4 or 8), H rows per block; grid = pair_direct_grid(...)
+long long pair_direct_grid(int cw, int H, int nx, int ny);
+void pressure_sweeps_pair_direct(const PressureArgs &a, bool check, int cw, int H, int grid,
+                                 void *stream);
+cudaError_t node_pressure_pair_direct(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
+                                      const PressureArgs &a, bool check, int cw, int H, int grid);
 // FP16 storage (fp16.cu): narrow = max |n| -> scale -> convert; one sweep; widen
 int max_blocks_per_sm_pressure_h();
 void half_narrow(const HalfConvertArgs &a, int grid, void *stream);

@@ -30,11 +30,14 @@ struct lbm2p {
     int sweep_kind = 0;        // single-sweep kernel: 0 = four nodes per thread, 1 = one
                                // node per thread, 2 = staged rows
     int grid_sweep = 0;        // blocks of a single sweep without the residual (autotuned)
+    long long partials_cap = 0;   // residual partials the partials array holds
     int grid_k[2] = {}, grid_check_k[2] = {}, grid_cap_k[2] = {};
     int rows_w = 0, rows_slots = 0, rows_H = 0, rows_grid = 0;   // staged-rows kernel shape
     int tb_T = 0, tb_W = 0, tb_H = 0, tb_grid = 0;   // fused sweeps per launch and tile shape
     int tb_kind = 0;           // fused kernel: 0 = k_pressure_tb (shared-memory stages), 1 =
-                               // k_pressure_rows2 (two sweeps on staged rows; tb_W = 30 x warps)
+                               // k_pressure_rows2 (two sweeps on staged rows), 2 =
+                               // k_pressure_pair_direct (two sweeps, direct loads); for 1 and
+                               // 2 tb_W = 30 x warps
     int tb_slots = 0;          // ring slots of k_pressure_rows2
     int tb_T_graph = 0;        // fused sweeps used inside the graph loop body (0: single sweeps)
     bool fp16 = false;         // storage FP16_DEV: sweeps run on FP16 copies inside a solve

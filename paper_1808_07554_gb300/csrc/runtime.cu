@@ -309,7 +309,11 @@ lbm2p_status add_loop(lbm2p *h, cudaGraph_t G, const cudaGraphNode_t *dep, int p
         for (int kk = T; kk <= m; kk += T) {
             cudaGraphNode_t n;
             PressureArgs a = pressure_args(h, src);
-            if (h->tb_kind == 1)
+            if (h->tb_kind == 2)
+                CUDA_TRY(h, lbm2p_launch::node_pressure_pair_direct(&n, body, prev ? &prev : nullptr,
+                                                                    a, kk == m, h->tb_W / 30,
+                                                                    h->tb_H, h->tb_grid));
+            else if (h->tb_kind == 1)
                 CUDA_TRY(h, lbm2p_launch::node_pressure_rows2(&n, body, prev ? &prev : nullptr, a,
                                                               kk == m, h->tb_W / 30, h->tb_slots,
                                                               h->tb_H, h->tb_grid));
@@ -627,7 +631,11 @@ lbm2p_status pressure_solve(lbm2p *h, int replay, int *k_out, double *r_out, flo
         }
         for (int q = 0; q < nf; ++q) {
             PressureArgs a = pressure_args(h, h->cur_f);
-            if (h->tb_kind == 1)
+            if (h->tb_kind == 2)
+                lbm2p_launch::pressure_sweeps_pair_direct(a, q == nf - 1 && final_check,
+                                                          h->tb_W / 30, h->tb_H, h->tb_grid,
+                                                          h->stream);
+            else if (h->tb_kind == 1)
                 lbm2p_launch::pressure_sweeps_rows2(a, q == nf - 1 && final_check, h->tb_W / 30,
                                                     h->tb_slots, h->tb_H, h->tb_grid, h->stream);
             else
@@ -906,6 +914,9 @@ lbm2p_status check_params(const lbm2p_params *p, const lbm2p_inputs *in)
 // single-sweep kernel is the only one timed; requested fused sweeps win over single ones.
 // Each candidate runs once untimed, then the best of two timed groups of reps launches
 // counts.  Runs on the zeroed buffers before initialisation; they are zeroed again after.
+// a fused form must take at most this fraction of the best single sweep's time per sweep
+constexpr float kFusedMargin = 0.85f;
+
 lbm2p_status autotune_sweeps(lbm2p *h)
 {
     cudaStream_t st = (cudaStream_t)h->stream;
@@ -944,11 +955,32 @@ lbm2p_status autotune_sweeps(lbm2p *h)
     auto allowed = [&](int kind) { return forced == LBM2P_SWEEP_AUTO || forced == kind + 1; };
     const bool fused_only = h->p.fuse_sweeps == 2 || h->p.fuse_sweeps == 4;
     float best = 1e30f;                                    // per-sweep time of the choice
+    // a fused form replaces single sweeps only when it is clearly faster: in the timed solve
+    // loop the forms come out closer than in these isolated timings (1024^2 five-spot: the
+    // two-sweep direct form timed 12 % ahead here and about even in the loop)
+    float single_best = 1e30f;
+    auto fused_wins = [&](float per) {
+        return h->tb_T > 1 ? per < best : (per < best && per < kFusedMargin * single_best);
+    };
     h->autotune_log.clear();
     auto note = [&](const char *what, int a1, int a2, int a3, int a4, float us) {
         char line[160];
         snprintf(line, sizeof line, "%s %d %d %d %d %.3f\n", what, a1, a2, a3, a4, us);
         h->autotune_log += line;
+    };
+    // what a candidate costs per sweep inside the solve loop: a check period of check_every
+    // sweeps runs (launches - 1) plain launches and one that also sums the residual
+    const int m_chk = h->p.check_every;
+    auto in_loop = [&](float plain, float check, int T) {
+        const int nl = m_chk / T > 0 ? m_chk / T : 1;
+        return ((float)(nl - 1) * plain + check) / (float)(nl * T);
+    };
+    // the checking launch's time, when its residual partials fit the scratch array
+    auto timed_check = [&](auto launch, long long parts, float plain, float *ms) -> bool {
+        *ms = plain;
+        if (parts > h->partials_cap)
+            return true;
+        return timed(launch, ms);
     };
     h->tb_T = 0;
     h->sweep_kind = forced == LBM2P_SWEEP_AUTO ? 0 : forced - 1;
@@ -968,12 +1000,19 @@ lbm2p_status autotune_sweeps(lbm2p *h)
                 if (grid == last_grid)
                     continue;
                 last_grid = grid;
-                float ms = 0.0f;
+                float ms = 0.0f, mc = 0.0f;
                 if (!timed([&](int k) {
                         PressureArgs a = pressure_args(h, k % 2);
                         lbm2p_launch::pressure_sweep(a, false, false, grid, h->stream, kind);
                     }, &ms))
                     goto done;
+                if (!timed_check([&](int k) {
+                        PressureArgs a = pressure_args(h, k % 2);
+                        lbm2p_launch::pressure_sweep(a, true, false, h->grid_check_k[kind], h->stream,
+                                                     kind);
+                    }, h->grid_check_k[kind], ms, &mc))
+                    goto done;
+                ms = in_loop(ms, mc, 1);
                 note(kind == 0 ? "single_vec4" : "single_scalar", grid, 0, 0, 0, ms * 1e3f);
                 if (ms < best_kind) {
                     best_kind = ms;
@@ -1013,13 +1052,20 @@ lbm2p_status autotune_sweeps(lbm2p *h)
                     continue;
                 last_H = H;
                 const int grid = (int)lbm2p_launch::rows_grid(width, H, h->nx, h->ny);
-                float ms = 0.0f;
+                float ms = 0.0f, mc = 0.0f;
                 if (!timed([&](int k) {
                         PressureArgs a = pressure_args(h, k % 2);
                         lbm2p_launch::pressure_sweep_rows(a, false, false, width, slots, H, grid,
                                                           h->stream);
                     }, &ms))
                     goto done;
+                if (!timed_check([&](int k) {
+                        PressureArgs a = pressure_args(h, k % 2);
+                        lbm2p_launch::pressure_sweep_rows(a, true, false, width, slots, H, grid,
+                                                          h->stream);
+                    }, grid, ms, &mc))
+                    goto done;
+                ms = in_loop(ms, mc, 1);
                 note("single_rows", width, slots, H, grid, ms * 1e3f);
                 if (ms < best_rows) {
                     best_rows = ms;
@@ -1047,14 +1093,17 @@ lbm2p_status autotune_sweeps(lbm2p *h)
     }
     if (fused_only)
         best = 1e30f;
+    single_best = best;
     if (h->p.fuse_sweeps != 1) {
         bool walls = true;
         for (int sd = 0; sd < 4; ++sd)
             walls = walls && h->p.bc[sd] != LBM2P_BC_PERIODIC;
-        // fuse_sweeps 2 with the ROWS kernel pinned asks for the staged-rows two-sweep kernel
+        // fuse_sweeps 2 with the ROWS kernel pinned asks for the staged-rows two-sweep kernel,
+        // with the SCALAR kernel pinned for the direct-load one
         const bool rows2_only = walls && h->p.fuse_sweeps == 2 && forced == LBM2P_SWEEP_ROWS;
+        const bool direct_only = walls && h->p.fuse_sweeps == 2 && forced == LBM2P_SWEEP_SCALAR;
         for (int T : {2, 4}) {
-            if ((h->p.fuse_sweeps != 0 && h->p.fuse_sweeps != T) || rows2_only)
+            if ((h->p.fuse_sweeps != 0 && h->p.fuse_sweeps != T) || rows2_only || direct_only)
                 continue;
             for (int W : {128, 64, 32}) {
                 cudaError_t ce = lbm2p_launch::tb_prepare(T, W);
@@ -1066,16 +1115,23 @@ lbm2p_status autotune_sweeps(lbm2p *h)
                     const long long blocks = lbm2p_launch::tb_grid(T, W, H, h->nx, h->ny);
                     if (blocks > (1LL << 30))
                         continue;
-                    float ms = 0.0f;
+                    float ms = 0.0f, mc = 0.0f;
                     if (!timed([&](int k) {
                             PressureArgs a = pressure_args(h, k % 2);
                             lbm2p_launch::pressure_sweeps_fused(a, T, W, H, false, (int)blocks,
                                                                 h->stream);
                         }, &ms))
                         goto done;
-                    note("fused", T, W, H, (int)blocks, ms / T * 1e3f);
-                    if (ms / T < best) {
-                        best = ms / T;
+                    if (!timed_check([&](int k) {
+                            PressureArgs a = pressure_args(h, k % 2);
+                            lbm2p_launch::pressure_sweeps_fused(a, T, W, H, true, (int)blocks,
+                                                                h->stream);
+                        }, blocks, ms, &mc))
+                        goto done;
+                    const float per = in_loop(ms, mc, T);
+                    note("fused", T, W, H, (int)blocks, per * 1e3f);
+                    if (fused_wins(per)) {
+                        best = per;
                         h->tb_T = T;
                         h->tb_kind = 0;
                         h->tb_W = W;
@@ -1087,7 +1143,47 @@ lbm2p_status autotune_sweeps(lbm2p *h)
         }
         // two sweeps per launch on rows staged by bulk copies (lattices with walls on every
         // side): consumer warps x ring slots, and output rows per block
+        // two sweeps per launch with direct loads (for lattices whose populations stay in L2)
         if (walls && (h->p.fuse_sweeps == 0 || h->p.fuse_sweeps == 2) &&
+            (forced == LBM2P_SWEEP_AUTO || forced == LBM2P_SWEEP_SCALAR)) {
+            for (int cw : {4, 8}) {
+                int last_H = -1;
+                for (int H : {2, 4, 8, 16, 32}) {
+                    const int Hc = H < h->ny ? H : h->ny;
+                    if (Hc == last_H)
+                        continue;
+                    last_H = Hc;
+                    const long long blocks = lbm2p_launch::pair_direct_grid(cw, Hc, h->nx, h->ny);
+                    if (blocks > (1LL << 30))
+                        continue;
+                    float ms = 0.0f, mc = 0.0f;
+                    if (!timed([&](int k) {
+                            PressureArgs a = pressure_args(h, k % 2);
+                            lbm2p_launch::pressure_sweeps_pair_direct(a, false, cw, Hc, (int)blocks,
+                                                                      h->stream);
+                        }, &ms))
+                        goto done;
+                    if (!timed_check([&](int k) {
+                            PressureArgs a = pressure_args(h, k % 2);
+                            lbm2p_launch::pressure_sweeps_pair_direct(a, true, cw, Hc, (int)blocks,
+                                                                      h->stream);
+                        }, blocks, ms, &mc))
+                        goto done;
+                    const float per = in_loop(ms, mc, 2);
+                    note("fused_direct", cw, 0, Hc, (int)blocks, per * 1e3f);
+                    if (fused_wins(per) || (direct_only && h->tb_kind != 2)) {
+                        best = per;
+                        h->tb_T = 2;
+                        h->tb_kind = 2;
+                        h->tb_W = 30 * cw;
+                        h->tb_slots = 0;
+                        h->tb_H = Hc;
+                        h->tb_grid = (int)blocks;
+                    }
+                }
+            }
+        }
+        if (walls && !direct_only && (h->p.fuse_sweeps == 0 || h->p.fuse_sweeps == 2) &&
             (forced == LBM2P_SWEEP_AUTO || forced == LBM2P_SWEEP_ROWS)) {
             const int shapes2[4][2] = {{4, 6}, {4, 8}, {8, 4}, {8, 6}};
             for (const auto &sh : shapes2) {
@@ -1106,16 +1202,23 @@ lbm2p_status autotune_sweeps(lbm2p *h)
                     const long long blocks = lbm2p_launch::rows2_grid(cw, Hc, h->nx, h->ny);
                     if (blocks > (1LL << 30))
                         continue;
-                    float ms = 0.0f;
+                    float ms = 0.0f, mc = 0.0f;
                     if (!timed([&](int k) {
                             PressureArgs a = pressure_args(h, k % 2);
                             lbm2p_launch::pressure_sweeps_rows2(a, false, cw, slots, Hc,
                                                                 (int)blocks, h->stream);
                         }, &ms))
                         goto done;
-                    note("fused_rows", cw, slots, Hc, (int)blocks, ms / 2 * 1e3f);
-                    if (ms / 2 < best) {
-                        best = ms / 2;
+                    if (!timed_check([&](int k) {
+                            PressureArgs a = pressure_args(h, k % 2);
+                            lbm2p_launch::pressure_sweeps_rows2(a, true, cw, slots, Hc,
+                                                                (int)blocks, h->stream);
+                        }, blocks, ms, &mc))
+                        goto done;
+                    const float per = in_loop(ms, mc, 2);
+                    note("fused_rows", cw, slots, Hc, (int)blocks, per * 1e3f);
+                    if (fused_wins(per)) {
+                        best = per;
                         h->tb_T = 2;
                         h->tb_kind = 1;
                         h->tb_W = lbm2p_launch::rows2_width(cw);
@@ -1402,6 +1505,14 @@ lbm2p_status build(lbm2p *h, const lbm2p_inputs *in, lbm2p_step_stats *init_stat
     // which single-sweep kernel, single or fused sweeps, and the fused tile shape: timed
     // on this lattice (within what fuse_sweeps allows); FP16 storage has one sweep kernel
     if (!h->fp16) {
+        // the timing of each candidate's checking launch needs residual partials and shift
+        // constants: a partials array sized for the finest candidate grid (a block owns at
+        // least 128 nodes), kept as the handle's own when it is large enough
+        h->partials_cap = h->nnodes / 128 + 4096;
+        h->partials = (double *)dev_alloc(h, (size_t)h->partials_cap * 4 * sizeof(double));
+        h->shift = (float *)dev_alloc(h, 64);
+        if (!h->partials || !h->shift)
+            return fail(h, LBM2P_ENOMEM, "device allocation of the residual partials failed");
         lbm2p_status e = autotune_sweeps(h);
         if (e != LBM2P_OK)
             return e;
@@ -1425,10 +1536,14 @@ lbm2p_status build(lbm2p *h, const lbm2p_inputs *in, lbm2p_step_stats *init_stat
             np = np > h->grid_k[kind] ? np : h->grid_k[kind];
             np = np > h->grid_check_k[kind] ? np : h->grid_check_k[kind];
         }
-        h->partials = (double *)dev_alloc(h, (size_t)np * 4 * sizeof(double));
+        if (!h->partials || np > h->partials_cap) {
+            h->partials = (double *)dev_alloc(h, (size_t)np * 4 * sizeof(double));
+            h->partials_cap = np;
+        }
     }
     h->mean = (double *)dev_alloc(h, 64);
-    h->shift = (float *)dev_alloc(h, 64);
+    if (!h->shift)
+        h->shift = (float *)dev_alloc(h, 64);
     h->res = (ResidualOut *)dev_alloc(h, sizeof(ResidualOut));
     h->ctl = (LoopCtl *)dev_alloc(h, sizeof(LoopCtl));
     h->stage = (float *)dev_alloc(h, (size_t)h->nnodes * sizeof(float) * 4);
@@ -1837,6 +1952,14 @@ lbm2p_status lbm2p_sweep_config(const lbm2p *h, int *fused, int *kind, int *tile
     if (tile_h)
         *tile_h = h->tb_T > 1 ? h->tb_H : (h->sweep_kind == 2 ? h->rows_H : 0);
     return LBM2P_OK;
+}
+
+int lbm2p_fused_form_of(const lbm2p *h)
+{
+    if (!h || h->fp16 || h->tb_T <= 1)
+        return LBM2P_FUSED_NONE;
+    return h->tb_kind == 2 ? LBM2P_FUSED_DIRECT
+                           : (h->tb_kind == 1 ? LBM2P_FUSED_STAGED_ROWS : LBM2P_FUSED_STAGES);
 }
 
 const char *lbm2p_autotune_report(const lbm2p *h)

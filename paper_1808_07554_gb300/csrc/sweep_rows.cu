@@ -533,6 +533,155 @@ __global__ void __launch_bounds__(32 * (CW + 1), CW == 4 ? 6 : 3) k_pressure_row
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Two sweeps per launch with the inputs read straight from global memory (lattices with walls
+// on every side).  The consumer logic of k_pressure_rows2 without the staging: warp w of a
+// block owns 30 columns, walks the block's H rows, computes the first sweep on its 32
+// columns with the scalar gather (L1/L2 hits where the lattice stays in L2) and the second
+// sweep one row behind from register history and shuffles.  No producer, no mbarrier, no
+// shared memory but the block's residual reduction: meant for lattices small enough that
+// their populations stay in L2 between sweeps, where the staged pipeline's per-row latency
+// dominates.  Same per-node arithmetic, so results equal two single sweeps bit for bit.
+// ---------------------------------------------------------------------------------------
+template <bool CHECK, int CW>
+__global__ void __launch_bounds__(32 * CW) k_pressure_pair_direct(const __grid_constant__ PressureArgs a,
+                                                                 int H)
+{
+    constexpr int W = 30 * CW;
+    __shared__ double red[CW][4];
+    const Geom &g = a.g;
+    const int p = g.pitch;
+    const int strips = (g.nx + W - 1) / W;
+    const int x0 = (blockIdx.x % strips) * W;
+    const int y0 = (blockIdx.x / strips) * H;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const float shift = CHECK ? a.shift[0] : 0.0f;
+    const float dshift = CHECK ? a.shift[1] : 0.0f;
+    ResAcc racc;
+    const int y1 = y0 + H < g.ny ? y0 + H : g.ny;
+    const int x = x0 - 1 + 30 * warp + lane;
+    const bool xin = x >= 0 && x < g.nx;
+    const bool owner = lane >= 1 && lane <= 30 && x < g.nx;
+    float ra = 0.0f, rb = 0.0f, rc = 0.0f, tb = 0.0f, tc = 0.0f, qb = 0.0f, qc = 0.0f;
+    float db = 0.0f, dc = 0.0f;
+    float v[8], h1[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        v[i] = h1[i] = 0.0f;
+    float h2_1 = 0.0f, h2_4 = 0.0f, h2_5 = 0.0f;
+    // the first sweep runs on rows y0 - 1 .. y1 (one more on each side), the second one row
+    // behind it on rows y0 .. y1 - 1
+    for (int ys = y0 - 1; ys <= y1 && y0 < g.ny; ++ys) {
+        h2_1 = h1[1];
+        h2_4 = h1[4];
+        h2_5 = h1[5];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            h1[i] = v[i];
+            v[i] = 0.0f;
+        }
+        ra = rb;
+        rb = rc;
+        tb = tc;
+        qb = qc;
+        db = dc;
+        rc = tc = qc = dc = 0.0f;
+        if (xin && ys >= 0 && ys < g.ny) {
+            const int o = ys * p + x;
+            const float r0 = a.R[o];
+            float f[8];
+            gather_a(a.fin, a.R, g, a.Pb, x, ys, o, f);
+            const float dP = pressure_of(f);
+            const float it = a.inv_tau[o];
+            float F = a.Fp ? a.Fp[o] : 0.0f;
+            for (int w = 0; w < a.w.n; ++w)
+                if (o == a.w.idx[w])
+                    F += a.w.fp[w];
+            const float Fq = 0.125f * F;   // w_bar_i = 1/8 (Eq. 3-5a)
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                v[i] = collide1(f[i], wgt(i + 1), dP, it, Fq);
+            rc = r0;
+            tc = it;
+            qc = Fq;
+            dc = dP;
+        }
+        const int y2 = ys - 1;
+        if (y2 < y0)
+            continue;
+        RNbhd Rn;
+        Rn.m1 = ra;
+        Rn.c1 = rb;
+        Rn.p1 = rc;
+        Rn.m0 = __shfl_up_sync(0xffffffffu, ra, 1);
+        Rn.c0 = __shfl_up_sync(0xffffffffu, rb, 1);
+        Rn.p0 = __shfl_up_sync(0xffffffffu, rc, 1);
+        Rn.m2 = __shfl_down_sync(0xffffffffu, ra, 1);
+        Rn.c2 = __shfl_down_sync(0xffffffffu, rb, 1);
+        Rn.p2 = __shfl_down_sync(0xffffffffu, rc, 1);
+        float nb[8];
+        nb[0] = __shfl_up_sync(0xffffffffu, h1[0], 1);
+        nb[1] = h2_1;
+        nb[2] = __shfl_down_sync(0xffffffffu, h1[2], 1);
+        nb[3] = v[3];
+        nb[4] = __shfl_up_sync(0xffffffffu, h2_4, 1);
+        nb[5] = __shfl_down_sync(0xffffffffu, h2_5, 1);
+        nb[6] = __shfl_down_sync(0xffffffffu, v[6], 1);
+        nb[7] = __shfl_up_sync(0xffffffffu, v[7], 1);
+        if (owner && y2 < g.ny) {
+            const float r0 = rb;
+            float f[8];
+            if (x > 0 && x < g.nx - 1 && y2 > 0 && y2 < g.ny - 1) {
+                f[0] = dev1(nb[0], wgt(1), Rn.c0, r0);
+                f[1] = dev1(nb[1], wgt(2), Rn.m1, r0);
+                f[2] = dev1(nb[2], wgt(3), Rn.c2, r0);
+                f[3] = dev1(nb[3], wgt(4), Rn.p1, r0);
+                f[4] = dev1(nb[4], wgt(5), Rn.m0, r0);
+                f[5] = dev1(nb[5], wgt(6), Rn.m2, r0);
+                f[6] = dev1(nb[6], wgt(7), Rn.p2, r0);
+                f[7] = dev1(nb[7], wgt(8), Rn.p0, r0);
+            } else {
+                f[0] = second_pull<1>(nb[0], h1[opp(1) - 1], Rn, g, a.Pb, x, y2, r0);
+                f[1] = second_pull<2>(nb[1], h1[opp(2) - 1], Rn, g, a.Pb, x, y2, r0);
+                f[2] = second_pull<3>(nb[2], h1[opp(3) - 1], Rn, g, a.Pb, x, y2, r0);
+                f[3] = second_pull<4>(nb[3], h1[opp(4) - 1], Rn, g, a.Pb, x, y2, r0);
+                f[4] = second_pull<5>(nb[4], h1[opp(5) - 1], Rn, g, a.Pb, x, y2, r0);
+                f[5] = second_pull<6>(nb[5], h1[opp(6) - 1], Rn, g, a.Pb, x, y2, r0);
+                f[6] = second_pull<7>(nb[6], h1[opp(7) - 1], Rn, g, a.Pb, x, y2, r0);
+                f[7] = second_pull<8>(nb[7], h1[opp(8) - 1], Rn, g, a.Pb, x, y2, r0);
+            }
+            const int o = y2 * p + x;
+            const float dP = pressure_of(f);
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                a.fout[i][o] = collide1(f[i], wgt(i + 1), dP, tb, qb);
+            if (CHECK)
+                racc.add((dP - db) - dshift, (r0 - shift) + dP);
+        }
+    }
+    if (CHECK) {
+        double vsum[4];
+        racc.warp_totals(vsum);
+        if (lane == 0)
+            for (int c = 0; c < 4; ++c)
+                red[warp][c] = vsum[c];
+        __syncthreads();
+        if (threadIdx.x < 4) {
+            double sum = 0.0;
+            for (int w = 0; w < CW; ++w)
+                sum += red[w][threadIdx.x];
+            a.partials[4 * blockIdx.x + threadIdx.x] = sum;
+        }
+    }
+}
+
+void *pair_direct_func(int cw, bool check)
+{
+    if (cw == 4)
+        return check ? (void *)k_pressure_pair_direct<true, 4> : (void *)k_pressure_pair_direct<false, 4>;
+    return check ? (void *)k_pressure_pair_direct<true, 8> : (void *)k_pressure_pair_direct<false, 8>;
+}
+
 template <int CW, int S>
 void *rows2_func_t(bool check)
 {
@@ -709,6 +858,37 @@ cudaError_t node_pressure_rows2(cudaGraphNode_t *n, cudaGraph_t g, const cudaGra
     prm.gridDim = dim3((unsigned)grid);
     prm.blockDim = dim3((unsigned)(32 * (cw + 1)));
     prm.sharedMemBytes = (unsigned)rows2_smem_bytes(cw, slots, a.Fp != nullptr);
+    void *args[] = {(void *)&a, (void *)&H};
+    prm.kernelParams = args;
+    prm.extra = nullptr;
+    return cudaGraphAddKernelNode(n, g, dep, dep ? 1 : 0, &prm);
+}
+
+
+// ---- two sweeps per launch with direct loads ------------------------------------------------
+long long pair_direct_grid(int cw, int H, int nx, int ny)
+{
+    const int w = 30 * cw;
+    return (long long)((nx + w - 1) / w) * ((ny + H - 1) / H);
+}
+
+
+void pressure_sweeps_pair_direct(const PressureArgs &a, bool check, int cw, int H, int grid,
+                                 void *stream)
+{
+    void *args[] = {(void *)&a, (void *)&H};
+    cudaLaunchKernel(lbm2p_dev::pair_direct_func(cw, check), dim3(grid), dim3(32 * cw), args, 0,
+                     reinterpret_cast<cudaStream_t>(stream));
+}
+
+cudaError_t node_pressure_pair_direct(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
+                                      const PressureArgs &a, bool check, int cw, int H, int grid)
+{
+    cudaKernelNodeParams prm{};
+    prm.func = lbm2p_dev::pair_direct_func(cw, check);
+    prm.gridDim = dim3((unsigned)grid);
+    prm.blockDim = dim3((unsigned)(32 * cw));
+    prm.sharedMemBytes = 0;
     void *args[] = {(void *)&a, (void *)&H};
     prm.kernelParams = args;
     prm.extra = nullptr;

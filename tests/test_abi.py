@@ -37,7 +37,7 @@ def test_every_declared_function_is_exported(lib):
 
 def test_abi_version_and_defaults(lib):
     import paper_1808_07554_gb300 as pkg
-    assert pkg.lbm2p_abi_version() == 5
+    assert pkg.lbm2p_abi_version() == 6
     p = pkg.lbm2p_default_params()
     assert (p.phi, p.beta, p.mu_w, p.mu_n, p.D_s, p.tau_p, p.tol) == (0.2, 0.4, 1.0, 2.0, 0.01, 1.0, 1e-8)
     assert p.check_every == 8 and list(p.bc) == [1, 1, 1, 1] and p.fuse_sweeps == 0

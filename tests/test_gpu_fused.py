@@ -42,19 +42,20 @@ def _problem(kind):
 
 @pytest.mark.parametrize("kind", ["five_spot_ragged", "wide_ragged", "periodic", "dirichlet",
                                   "mixed", "tiny", "column", "tall"])
-@pytest.mark.parametrize("T", [2, 4, "2rows"])
+@pytest.mark.parametrize("T", [2, 4, "2rows", "2direct"])
 def test_fused_equals_single_sweeps(kind, T):
     """T = 2 or 4 sweeps on shared-memory stages; "2rows": two sweeps on rows staged by
-    bulk copies (lattices with walls on every side only)."""
+    bulk copies; "2direct": two sweeps with direct loads (both for lattices with walls on every
+    side only)."""
     import paper_1808_07554_gb300 as pkg
     prob = _problem(kind)
     single = pkg.Solver.from_problem(prob, init_replay=0, fuse_sweeps=1)
-    if T == "2rows":
+    if T in ("2rows", "2direct"):
         if W.PERIODIC in prob.bc:
-            pytest.skip("the staged-rows two-sweep kernel needs walls on every side")
+            pytest.skip("the two-sweep row-walking kernels need walls on every side")
+        pin = pkg.SWEEP_ROWS if T == "2rows" else pkg.SWEEP_SCALAR
         T = 2
-        fused = pkg.Solver.from_problem(prob, init_replay=0, fuse_sweeps=2,
-                                        sweep_kernel=pkg.SWEEP_ROWS)
+        fused = pkg.Solver.from_problem(prob, init_replay=0, fuse_sweeps=2, sweep_kernel=pin)
         cfg = fused.sweep_config()
         assert cfg[0] == 2 and cfg[2] in (120, 240) and 1 <= cfg[3] <= 128
     else:
