@@ -102,4 +102,5 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.lbm2p_step(None, 1, None, None) == pkg.EINVAL
     assert lib.lbm2p_fields(None, None, None, 0, 0) == pkg.EINVAL
     assert lib.lbm2p_state_count(None) == 0
+    assert lib.lbm2p_fused_form_of(None) == pkg.FUSED_NONE
     lib.lbm2p_destroy(None)
