@@ -59,9 +59,13 @@ SWEEP_KERNEL_NAMES = {1: "four nodes per thread (128-bit accesses)", 2: "one nod
 # kind); absent until captured for the current kernel (profiles/).
 # five_spot_1024, one node per thread (the autotuner's choice there): 42.0 MB read + 0.9 MB
 # written per launch, L2 flushed by ncu before the launch.
+# five_spot_1024, two sweeps with direct loads, 120-column blocks of 4 rows (the autotuner's
+# choice there with the residual checked every 16 sweeps): 42.0 MB read + 0.95 MB written per
+# launch, L2 flushed by ncu before the launch.
 # five_spot_4096, two sweeps on staged rows, 120-column blocks (the autotuner's choice there):
 # 720.9 MB read + 493.1 MB written per launch (a launch without the residual).
 NCU_TRAFFIC_PER_LAUNCH = {("five_spot_1024", "single", 2): 42.87e6,
+                          ("five_spot_1024", "direct", 120): 42.94e6,
                           ("five_spot_4096", "staged_rows", 120): 1214.0e6}
 FUSED_FORM_NAMES = {1: "stages", 2: "staged_rows", 3: "direct"}
 FUSED_FORM_TEXT = {1: "on shared-memory stages", 2: "on rows staged by bulk copies",
