@@ -55,7 +55,7 @@ typedef enum {
     LBM2P_ECUDA = 3,           /* a CUDA call failed; the handle should be destroyed */
     LBM2P_ENOTCONVERGED = 4,   /* max_sub_iters reached before the residual met tol */
     LBM2P_ENONFINITE = 5,      /* the pressure residual became NaN (e.g. NaN sources) */
-    LBM2P_ENOTIMPL = 6         /* requested option is not available in this build */
+    LBM2P_ENOTIMPL = 6         /* requested option is not implemented by the library */
 } lbm2p_status;
 
 /* Wall kinds of Sec. 4: bounce-back for no-flux, anti-bounce-back for Dirichlet. */
