@@ -420,7 +420,11 @@ def run_ours(args):
                                    + (", autotuned" if args.sweep_kernel == 0 else ""))),
                      "bytes_per_launch": bpn * nodes, "sweeps_per_launch": fused,
                      "avg_launch_us": avg_launch_s * 1e6,
-                     "launch_time_includes": "the residual finalize kernel of every 8th sweep",
+                     # a launch of several sweeps moves one sweep's bytes: its sweeps at the
+                     # single-sweep byte count, for comparison with one-sweep kernels
+                     "sweep_equivalent_gbs": fused * achieved,
+                     "launch_time_includes": ("the residual finalize kernel of every "
+                                              f"{args.check_every}th sweep"),
                      "peak_kind": peak_kind},
         "e2e": {"value": e2e_all / e2e_max / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
