@@ -915,7 +915,7 @@ lbm2p_status check_params(const lbm2p_params *p, const lbm2p_inputs *in)
 // Each candidate runs once untimed, then the best of two timed groups of reps launches
 // counts.  Runs on the zeroed buffers before initialisation; they are zeroed again after.
 // a fused form must take at most this fraction of the best single sweep's time per sweep
-constexpr float kFusedMargin = 0.85f;
+constexpr float kFusedMargin = 0.95f;
 
 lbm2p_status autotune_sweeps(lbm2p *h)
 {
@@ -956,8 +956,9 @@ lbm2p_status autotune_sweeps(lbm2p *h)
     const bool fused_only = h->p.fuse_sweeps == 2 || h->p.fuse_sweeps == 4;
     float best = 1e30f;                                    // per-sweep time of the choice
     // a fused form replaces single sweeps only when it is clearly faster: in the timed solve
-    // loop the forms come out closer than in these isolated timings (1024^2 five-spot: the
-    // two-sweep direct form timed 12 % ahead here and about even in the loop)
+    // loop the forms come out closer than these timings say (1024^2 five-spot: the two-sweep
+    // direct form estimated 8 % ahead here with a 16-sweep check period and 3.5 % ahead in the
+    // loop; 8 % ahead with an 8-sweep period and about even in the loop)
     float single_best = 1e30f;
     auto fused_wins = [&](float per) {
         return h->tb_T > 1 ? per < best : (per < best && per < kFusedMargin * single_best);
