@@ -23,25 +23,39 @@ _lib = None
 OK, EINVAL, ENOMEM, ENOTCONVERGED, ENONFINITE = 0, 1, 2, 4, 5
 
 
+# Another build of the oracle to load instead of this one (the pin tests' planted-mistake
+# check compiles altered copies of the source and runs the pins against them)
+LIB_ENV = "LBM2P_ORACLE_LIB"
+
+
+def compile_source(src: str, out: str) -> str:
+    """gcc with the oracle's flags (IEEE double, no fast-math, no FMA contraction)."""
+    tmp = out + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+           "-fno-fast-math", "-fopenmp", "-o", tmp, src, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (IEEE double, no fast-math, no FMA contraction)."""
+    """Compile the oracle (once, or again when the source is newer)."""
     if (not force and os.path.exists(_LIB)
             and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
         return _LIB
-    tmp = _LIB + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-           "-fno-fast-math", "-fopenmp", "-o", tmp, _SRC, "-lm"]
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB)
-    return _LIB
+    return compile_source(_SRC, _LIB)
 
 
 def _load():
     global _lib
     with _lock:
         if _lib is None:
-            build()
-            lib = C.CDLL(_LIB)
+            alt = os.environ.get(LIB_ENV)
+            if alt:
+                lib = C.CDLL(alt)
+            else:
+                build()
+                lib = C.CDLL(_LIB)
             dp = C.POINTER(C.c_double)
             ip = C.POINTER(C.c_int)
             lib.orc_create.restype = C.c_void_p

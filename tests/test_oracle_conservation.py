@@ -65,3 +65,22 @@ def test_pressure_total_recursion(bc):
         assert abs(Tn - ((1 - 1 / tau) * T + srcsum)) <= 1e-12 * max(1.0, abs(Tn))
         T = Tn
     o.close()
+
+
+def test_producer_takes_out_what_the_injector_puts_in_when_only_water_moves():
+    """With the decoupled mobility of Sec. 4.1 (lambda_t = lambda_w) the water fraction
+    f_w = lambda_w / lambda_t is 1 at any saturation, so a producer removes exactly what an
+    injector of the same rate adds: in a closed box the lattice total of g stays put."""
+    nx, ny = 18, 14
+    rng = np.random.default_rng(12)
+    wells = [(1, 2, 1e-3, 0), (nx - 2, ny - 3, 1e-3, 1)]
+    p = constant_diffusivity(nx, ny, 0.03, 1.2, bc=(1, 1, 1, 1), wells=wells,
+                             S0=0.3 + 0.2 * rng.random((ny, nx)))
+    o = O.Oracle(p, tol=1e-9, init_replay=30)
+    total0 = o.sums()["g"]
+    for _ in range(4):
+        st, k, r = o.step(1, replay=[16])
+        src = o.saturation_source()
+        assert src[2, 1] > 0.0 and src[ny - 3, nx - 2] == -src[2, 1]
+        assert abs(o.sums()["g"] - total0) <= 1e-12 * abs(total0)
+    o.close()

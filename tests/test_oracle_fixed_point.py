@@ -11,7 +11,7 @@ import pytest
 
 import oracle as O
 import workloads as W
-from _problems import uniform
+from _problems import constant_diffusivity, uniform
 
 
 def _problem(bc):
@@ -77,3 +77,31 @@ def test_nan_source_is_reported():
     prob.Fp = Fp
     with pytest.raises(O.OracleError):
         O.Oracle(prob, tol=1e-8)
+
+
+@pytest.mark.parametrize("bc", [(0, 0, 0, 0), (1, 1, 1, 1)])
+def test_neutral_mode_does_not_block_convergence(bc):
+    """With periodic or bounce-back walls on every side a constant added to P is neutral.
+    Summing the collision over i >= 1 with Eq. 3-9a gives sum_i f_i^+ = sum_i f_i + F~ at
+    every node, and such streaming keeps each population total, so a source with a nonzero
+    total raises the mean of P by sum_x F~ / ((1 - w_0) n) every sweep while its shape
+    settles.  The stopping rule's numerator is mean-free, so the solves still end (a raw
+    increment would stay at the drift); between two solves the shape (mean-free P) stays put
+    and the mean moves by exactly the drift of the sweeps run."""
+    nx, ny = 16, 12
+    rng = np.random.default_rng(31)
+    Fp = 0.5 + rng.standard_normal((ny, nx))
+    # decoupled mobility: tau_f does not depend on S, so the pressure shape cannot either
+    prob = constant_diffusivity(nx, ny, 0.03, 1.2, bc=bc, Fp=Fp)
+    o = O.Oracle(prob, tol=1e-10, check_every=8, max_sub_iters=20_000)
+    assert o.init_status == O.OK, (o.init_status, o.init_sub_iters)
+    P0 = o.fields()["P"]
+    st, k, r = o.step(1)
+    assert st == O.OK and 0 < k[0] < 20_000 and r[0] <= 1e-10
+    P1 = o.fields()["P"]
+    src = (o.scalars()["s"] * prob.dx ** 2 * Fp).sum()
+    o.close()
+    drift = int(k[0]) * src / ((1.0 - 4.0 / 9.0) * nx * ny)
+    assert abs(drift) > 1e-2 * np.abs(P0 - P0.mean()).max()
+    assert abs((P1.mean() - P0.mean()) - drift) <= 1e-9 * abs(drift)
+    assert W.rel_l2(W.mean_free(P1), W.mean_free(P0)) < 1e-7
