@@ -542,6 +542,10 @@ __global__ void __launch_bounds__(32 * (CW + 1), CW == 4 ? 6 : 3) k_pressure_row
 // shared memory but the block's residual reduction: meant for lattices small enough that
 // their populations stay in L2 between sweeps, where the staged pipeline's per-row latency
 // dominates.  Same per-node arithmetic, so results equal two single sweeps bit for bit.
+// The register history and the second sweep are written out here as in k_pressure_rows2
+// rather than shared through a helper: the helper version compiled to different register
+// counts (64 instead of 48 for the 8-warp plain launch, 72 instead of 64 for the 4-warp
+// checking one), and these counts set the blocks resident per SM.
 // ---------------------------------------------------------------------------------------
 template <bool CHECK, int CW>
 __global__ void __launch_bounds__(32 * CW) k_pressure_pair_direct(const __grid_constant__ PressureArgs a,
