@@ -316,16 +316,18 @@ def test_full_size_4096_sweeps(storage):
     orc.close()
 
 
-def test_full_size_1024_steps_in_the_bench_loop():
-    """The 1024^2 five-spot stepped the way the benchmark steps it: the autotuned launch form
-    (two sweeps per launch where that wins) inside the graph-resident loop with the residual
-    checked every 16 sweeps; two steps of 256 sweeps from P0 = 0, the same counts on both
-    sides, every field against the oracle."""
+@pytest.mark.parametrize("n,sweeps", [(1024, 256), (4096, 64)])
+def test_full_size_steps_in_the_bench_loop(n, sweeps):
+    """The five-spot at the benchmark's sizes stepped the way the benchmark steps it: the
+    autotuned launch form (two sweeps per launch where that wins: direct loads at 1024^2,
+    staged rows at 4096^2) inside the graph-resident loop with the residual checked every 16
+    sweeps; two steps from P0 = 0, the same counts on both sides, every field against the
+    oracle."""
     pkg = _pkg()
-    prob = W.quarter_five_spot(1024, seed=2)
+    prob = W.quarter_five_spot(n, seed=2)
     orc = O.Oracle(prob, tol=1e-8, check_every=16, init_replay=0)
     gpu = pkg.Solver.from_problem(prob, tol=1e-8, check_every=16, init_replay=0)
-    for k in (256, 256):
+    for k in (sweeps, sweeps):
         st, ks, r = orc.step(1, replay=[k])
         assert st == O.OK and int(ks[0]) == k
         gst, stats = gpu.step(1, replay=[k])
