@@ -128,7 +128,10 @@ typedef struct {
                                    identical bit for bit whatever the choice; fusion reads and
                                    writes the populations once per fused group of sweeps.
                                    Within the choice, create times the candidate kernels and
-                                   tile shapes on the lattice and keeps the fastest.  Fused
+                                   tile shapes on the lattice and keeps the fastest; with 0 a
+                                   fused form replaces single sweeps only when its time per
+                                   sweep is at most 0.95 of the best single sweep's (these
+                                   timings favour the fused forms a little).  Fused
                                    kernels: T = 2 or 4 sweeps on shared-memory stages, and, on
                                    lattices with walls on every side, 2 sweeps on rows staged
                                    by bulk copies and 2 sweeps with direct loads (fuse_sweeps
