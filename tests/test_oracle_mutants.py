@@ -5,7 +5,9 @@ then fail, in a fresh process that loads the altered build (``LBM2P_ORACLE_LIB``
 unaltered source, built the same way, passes every pin used here.
 
 Mistakes confined to f_0 change no output (P sums i >= 1 only, Eq. 3-9a, and f_0 feeds no
-other population); only the nine-population total of the pressure recursion sees them.
+other population); only the nine-population total of the pressure recursion sees them.  The
+order in which a corner link tests the two walls is a reading (the x side first), not a
+mistake: no pin can fix it, and the GPU path takes the same reading.
 """
 import os
 import shutil
@@ -84,6 +86,15 @@ MUTANTS = {
     "d2q5_weights": ("o->wg[i] = i == 0 ? 1.0 / 3.0 : (i < 5 ? 1.0 / 6.0 : 0.0);",
                      "o->wg[i] = i == 0 ? 1.0 / 3.0 : (i < 5 ? 1.0 / 4.0 : 0.0);",
                      "tests/test_oracle_variants.py::test_d2q5_equilibrium_moments"),
+    "residual_without_square_roots": ("return sqrt(num) / sqrt(den);", "return num / den;", WALLS),
+    "variable_tau_g_without_beta": (
+        "return 0.5 + 3.0 * Ds * o->dt / (o->beta * o->dx * o->dx);",
+        "return 0.5 + 3.0 * Ds * o->dt / (o->dx * o->dx);",
+        "tests/test_oracle_variants.py::test_variants_second_order[variable_ds]"),
+    "saturation_wall_with_pressure_weights": (
+        "double eq = is_g ? o->Gam[OPP[i]] * o->Sb[side][k] : o->w[OPP[i]] * o->Pb[side][k];",
+        "double eq = is_g ? o->w[OPP[i]] * o->Sb[side][k] : o->w[OPP[i]] * o->Pb[side][k];",
+        "tests/test_oracle_variants.py::test_d2q5_linear_saturation_is_steady_for_phi_equal_beta"),
     "variable_ds_without_oil_mobility": (
         "o->D_c * o->K[a] * lw * (lt - lw) / lt", "o->D_c * o->K[a] * lw * lt / lt",
         "tests/test_oracle_variants.py::test_variants_second_order[variable_ds]"),
