@@ -84,3 +84,26 @@ def test_producer_takes_out_what_the_injector_puts_in_when_only_water_moves():
         assert src[2, 1] > 0.0 and src[ny - 3, nx - 2] == -src[2, 1]
         assert abs(o.sums()["g"] - total0) <= 1e-12 * abs(total0)
     o.close()
+
+
+def test_balanced_wells_keep_the_mean_pressure():
+    """An injector and a producer of the same rate in a closed box add no net pressure source
+    (F_p = +q/dx^2 and -q/dx^2), so by the recursion of the population total the mean of P does
+    not move from one converged step to the next, while P stands above its mean at the injector
+    and below it at the producer."""
+    nx, ny = 20, 16
+    rng = np.random.default_rng(17)
+    wells = [(2, 3, 1e-3, 0), (nx - 3, ny - 2, 1e-3, 1)]
+    p = constant_diffusivity(nx, ny, 0.03, 1.2, bc=(1, 1, 1, 1), wells=wells,
+                             S0=0.3 + 0.2 * rng.random((ny, nx)),
+                             P0=0.01 * rng.standard_normal((ny, nx)))
+    o = O.Oracle(p, tol=1e-10, check_every=8, max_sub_iters=20_000)
+    assert o.init_status == O.OK
+    P0 = o.fields()["P"]
+    st, k, r = o.step(1)
+    assert st == O.OK and k[0] > 0
+    P1 = o.fields()["P"]
+    o.close()
+    span = P1.max() - P1.min()
+    assert abs(P1.mean() - P0.mean()) <= 1e-10 * span
+    assert P1[3, 2] > P1.mean() + 0.2 * span and P1[ny - 2, nx - 3] < P1.mean() - 0.2 * span

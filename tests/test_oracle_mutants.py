@@ -95,6 +95,17 @@ MUTANTS = {
         "double eq = is_g ? o->Gam[OPP[i]] * o->Sb[side][k] : o->w[OPP[i]] * o->Pb[side][k];",
         "double eq = is_g ? o->w[OPP[i]] * o->Sb[side][k] : o->w[OPP[i]] * o->Pb[side][k];",
         "tests/test_oracle_variants.py::test_d2q5_linear_saturation_is_steady_for_phi_equal_beta"),
+    "producer_adds_to_the_pressure_source": (
+        "Fp_t[a] += o->s * o->dx * o->dx * (o->wprod[m] ? -q : q);",
+        "Fp_t[a] += o->s * o->dx * o->dx * q;",
+        "tests/test_oracle_conservation.py::test_balanced_wells_keep_the_mean_pressure"),
+    "initial_g_without_tau_g": ("double neq = -tg * ((o->Gam[i] / o->phi",
+                                "double neq = -((o->Gam[i] / o->phi",
+                                "tests/test_oracle_init.py::test_initial_g_moments_match_appendix_b"),
+    "initial_g_advective_sign": (
+        "+ o->Gam[i] * cS - gam_t * o->wg[i] * cP / tg);",
+        "+ o->Gam[i] * cS + gam_t * o->wg[i] * cP / tg);",
+        "tests/test_oracle_init.py::test_initial_g_moments_match_appendix_b"),
     "variable_ds_without_oil_mobility": (
         "o->D_c * o->K[a] * lw * (lt - lw) / lt", "o->D_c * o->K[a] * lw * lt / lt",
         "tests/test_oracle_variants.py::test_variants_second_order[variable_ds]"),
