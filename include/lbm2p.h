@@ -328,25 +328,28 @@ void lbm2p_batch_destroy(lbm2p_batch *b);
  * stopping rule, for one lattice whose planes the caller owns on the current device:
  *   n_in[8]  pressure populations in the library's deviation form n_i = f_i^+ - w_i R,
  *            directions c_1..c_8, each a [ny][pitch] FP32 plane (read);
- *   n_out[8] the populations after the sweep (written; must not alias n_in);
+ *   n_out[8] the populations after the sweep (written; no output plane may be an input
+ *            plane, another output plane, R, inv_tau, Fp or dP: EINVAL);
  *   R        reference pressure, inv_tau = 1/tau_f, Fp = dense pressure source already in
  *            lattice units (s dx^2 F_p) or NULL: [ny][pitch] FP32 planes (read);
  *   P_b[4]   Dirichlet wall traces (FP32, 2n+1 values) for sides whose bc is DIRICHLET;
  *   dP       [ny][pitch] FP32: on entry the pressure increment P - R of the previous
  *            sweep, on exit that of this sweep (so calls chain; the first call's residual
- *            compares with whatever dP held);
+ *            compares with whatever dP held); not R, inv_tau, Fp or an input plane (EINVAL);
  *   residual host double: r = ||dP_new - dP_old - mean|| / ||P_new - mean P_new||.
  * pitch is a multiple of 4 floats and every plane pointer is 16-byte aligned.  Wells are
  * not taken: put their sources into Fp.
- * Memory: allocates nothing.  The residual scratch (one FP64 partial per row tile of 1024
- * nodes) is a static device array of LBM2P_NOALLOC_MAX_TILES tiles (2 MiB) held by every
- * GPU that loads the library until the process exits; lattices with more row tiles
- * (ceil(nx / 1024) * ny) are rejected with LBM2P_EINVAL.  The first call on each device
- * looks up the array's device address (with that device current); make that first call
- * before any stream capture.  Every call shares the one array and each call clears what
- * must start at zero, so calls whose work overlaps on the GPU (other streams, other host
- * threads) race on it: serialise them.  Synchronises `stream` (a cudaStream_t) to return
- * the residual.  Errors: lbm2p_last_error(NULL) describes the failure. */
+ * Memory: allocates nothing.  The residual scratch (four FP64 partials per row tile of 1024
+ * nodes, the finalize output and two shifts) is a static device array sized for
+ * LBM2P_NOALLOC_MAX_TILES tiles (2 MiB), held by every GPU that loads the library until the
+ * process exits; lattices with more row tiles (ceil(nx / 1024) * ny) are rejected with
+ * LBM2P_EINVAL before anything is launched.  The first call on each device (and again the
+ * first after that device's context is re-created, e.g. by cudaDeviceReset) looks up the
+ * array's device address with that device current.  Every call shares the one array and
+ * each call clears what must start at zero, so calls whose work overlaps on the GPU (other
+ * streams, other host threads) race on it: serialise them.  Each call synchronises `stream`
+ * (a cudaStream_t) to return the residual to the host, so it cannot be used inside a stream
+ * capture.  Errors: lbm2p_last_error(NULL) describes the failure. */
 #define LBM2P_NOALLOC_MAX_TILES 65536
 lbm2p_status lbm2p_pressure_sweep_noalloc(int nx, int ny, int pitch, const int bc[4],
                                           const float *const n_in[8], float *const n_out[8],

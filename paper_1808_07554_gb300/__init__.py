@@ -28,6 +28,8 @@ TAU_REFERENCE, TAU_PHYSICAL_DT = 0, 1
 STORE_FP32, STORE_FP16_DEV = 0, 1
 SWEEP_AUTO, SWEEP_VEC4, SWEEP_SCALAR, SWEEP_ROWS = 0, 1, 2, 3
 MAX_WELLS = 16
+NOALLOC_MAX_TILES = 65536   # LBM2P_NOALLOC_MAX_TILES: row tiles the static sweep scratch holds
+NOALLOC_TILE_NODES = 1024   # nodes of one row tile of lbm2p_pressure_sweep_noalloc
 STATE_PLANES = 20   # n_1..n_8 (f^+ - w_i R), g_0..g_8, 1/tau_f, S, R
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)

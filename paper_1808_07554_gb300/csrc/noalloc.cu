@@ -6,8 +6,8 @@
 // after initialisation, and plug-ins running inside a host application that owns the
 // device allocator.  They can still run the solver's hot kernel on buffers they already
 // own.  The only device memory the sweep needs beyond its inputs and outputs is the
-// scratch of the residual reduction (one FP64 partial per row tile, the finalize output
-// and a shift), and here that scratch is a file-scope static device array: it is part of
+// scratch of the residual reduction (four FP64 partials per row tile, the finalize output
+// and two shifts), and here that scratch is a file-scope static device array: it is part of
 // the loaded library image, present on every GPU that loads the library until the process
 // exits, and no call of this entry point allocates or frees anything.
 #include <cuda_runtime.h>
@@ -32,23 +32,63 @@ static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
+// cached device address of the scratch array, per device, valid for the CUDA context whose
+// unique id is stored beside it (a context id is never reused within a process)
 double *g_scratch_ptr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};
+
+// driver calls reached through the runtime (no link against the driver library)
+using CtxGetCurrentFn = int (*)(void **);
+using CtxGetIdFn = int (*)(void *, unsigned long long *);
+
+// Unique id of the current device's context.  A cudaDeviceReset destroys the primary context
+// and the next call creates a new one, with the library's module loaded anew (the array can
+// move), and a new id.
+lbm2p_status current_context_id(unsigned long long *id)
+{
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    if (!get_current || !get_id) {
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+        cudaError_t e1 = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000,
+                                                          cudaEnableDefault, &q1);
+        cudaError_t e2 = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000,
+                                                          cudaEnableDefault, &q2);
+        if (e1 != cudaSuccess || e2 != cudaSuccess || q1 != cudaDriverEntryPointSuccess ||
+            q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+            return lbm2p_internal::set_global_error(LBM2P_ECUDA,
+                                                    "the driver's context queries are unavailable");
+        get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+        get_id = reinterpret_cast<CtxGetIdFn>(f2);
+    }
+    void *ctx = nullptr;
+    if (get_current(&ctx) != 0 || !ctx || get_id(ctx, id) != 0)
+        return lbm2p_internal::set_global_error(LBM2P_ECUDA, "no current CUDA context");
+    return LBM2P_OK;
+}
 
 // Device address of the scratch array on the current device.  The host-side name of the
-// array is only a stand-in, so the address is looked up once per device, with that device
-// current, and cached.
+// array is only a stand-in, so the address is looked up with that device current, once per
+// device and context (the first call after a context is created), and cached.
 lbm2p_status scratch_on_current_device(double **out)
 {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess)
+        e = cudaSetDevice(dev);         // makes the device's primary context current
     if (e != cudaSuccess)
-        return lbm2p_internal::set_global_error(LBM2P_ECUDA, "cudaGetDevice failed: %s",
+        return lbm2p_internal::set_global_error(LBM2P_ECUDA, "no usable CUDA device: %s",
                                                 cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices)
         return lbm2p_internal::set_global_error(LBM2P_EINVAL, "device ordinal %d above %d", dev,
                                                 kMaxDevices - 1);
+    unsigned long long ctx = 0;
+    lbm2p_status st = current_context_id(&ctx);
+    if (st != LBM2P_OK)
+        return st;
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_ptr[dev]) {
+    if (!g_scratch_ptr[dev] || g_scratch_ctx[dev] != ctx) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p)
@@ -57,6 +97,7 @@ lbm2p_status scratch_on_current_device(double **out)
                                                     "failed on device %d: %s",
                                                     dev, cudaGetErrorString(e));
         g_scratch_ptr[dev] = static_cast<double *>(p);
+        g_scratch_ctx[dev] = ctx;
     }
     *out = g_scratch_ptr[dev];
     return LBM2P_OK;
@@ -101,6 +142,22 @@ extern "C" lbm2p_status lbm2p_pressure_sweep_noalloc(int nx, int ny, int pitch, 
             return set_global_error(LBM2P_EINVAL, "population plane %d missing or not 16-byte aligned", i);
     if (!aligned16(R) || !aligned16(inv_tau) || !aligned16(dP) || (Fp && !aligned16(Fp)))
         return set_global_error(LBM2P_EINVAL, "R, inv_tau, dP and Fp must be 16-byte aligned");
+    // the sweep reads its inputs while it writes its outputs: no output may be an input
+    for (int i = 0; i < 8; ++i) {
+        for (int j = 0; j < 8; ++j)
+            if (n_out[i] == n_in[j])
+                return set_global_error(LBM2P_EINVAL, "n_out[%d] is the same plane as n_in[%d]", i, j);
+        if (n_out[i] == R || n_out[i] == inv_tau || n_out[i] == Fp || n_out[i] == dP)
+            return set_global_error(LBM2P_EINVAL, "n_out[%d] aliases R, inv_tau, Fp or dP", i);
+        for (int j = i + 1; j < 8; ++j)
+            if (n_out[i] == n_out[j])
+                return set_global_error(LBM2P_EINVAL, "n_out[%d] and n_out[%d] are the same plane", i, j);
+    }
+    for (int j = 0; j < 8; ++j)
+        if (dP == n_in[j])
+            return set_global_error(LBM2P_EINVAL, "dP is the same plane as n_in[%d]", j);
+    if (dP == R || dP == inv_tau || dP == Fp)
+        return set_global_error(LBM2P_EINVAL, "dP aliases R, inv_tau or Fp");
 
     double *scratch = nullptr;
     lbm2p_status st = scratch_on_current_device(&scratch);

@@ -104,3 +104,48 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.lbm2p_state_count(None) == 0
     assert lib.lbm2p_fused_form_of(None) == pkg.FUSED_NONE
     lib.lbm2p_destroy(None)
+
+
+def test_binding_constants_match_the_header():
+    import paper_1808_07554_gb300 as pkg
+    text = open(os.path.join(ROOT, "include", "lbm2p.h")).read()
+    m = re.search(r"#define\s+LBM2P_NOALLOC_MAX_TILES\s+(\d+)", text)
+    assert m and int(m.group(1)) == pkg.NOALLOC_MAX_TILES
+    assert "row tile of 1024" in text and pkg.NOALLOC_TILE_NODES == 1024
+    m = re.search(r"#define\s+LBM2P_MAX_WELLS\s+(\d+)", text)
+    assert m and int(m.group(1)) == pkg.MAX_WELLS
+
+
+def _cuda_present():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except ImportError:
+        return False
+
+
+@pytest.mark.skipif(_cuda_present(), reason="host-only check: it passes addresses that are not "
+                                            "device memory, so it never runs where a GPU is")
+def test_noalloc_rejects_aliased_planes_before_any_cuda_call(lib):
+    """The argument checks of the allocation-free sweep come before its first CUDA call, so
+    on a machine without a GPU a rejected call returns EINVAL with its reason."""
+    import paper_1808_07554_gb300 as pkg
+    planes_in = [4096 * (i + 1) for i in range(8)]
+    planes_out = [4096 * (i + 20) for i in range(8)]
+    R, it, dP = 4096 * 40, 4096 * 41, 4096 * 42
+    bad = list(planes_out)
+    bad[3] = planes_in[5]                      # an output plane that is an input plane
+    with pytest.raises(pkg.LBM2PError) as ei:
+        pkg.lbm2p_pressure_sweep_noalloc(64, 64, 64, (1, 1, 1, 1), planes_in, bad, R, it, 0,
+                                         None, dP)
+    assert ei.value.status == pkg.EINVAL and "n_in[5]" in str(ei.value)
+    bad = list(planes_out)
+    bad[0] = bad[7]                            # two outputs on one plane
+    with pytest.raises(pkg.LBM2PError) as ei:
+        pkg.lbm2p_pressure_sweep_noalloc(64, 64, 64, (1, 1, 1, 1), planes_in, bad, R, it, 0,
+                                         None, dP)
+    assert ei.value.status == pkg.EINVAL
+    with pytest.raises(pkg.LBM2PError) as ei:  # the increment plane on the reference pressure
+        pkg.lbm2p_pressure_sweep_noalloc(64, 64, 64, (1, 1, 1, 1), planes_in, planes_out, R, it,
+                                         0, None, R)
+    assert ei.value.status == pkg.EINVAL and "dP" in str(ei.value)

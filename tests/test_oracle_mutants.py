@@ -106,6 +106,22 @@ MUTANTS = {
         "+ o->Gam[i] * cS - gam_t * o->wg[i] * cP / tg);",
         "+ o->Gam[i] * cS + gam_t * o->wg[i] * cP / tg);",
         "tests/test_oracle_init.py::test_initial_g_moments_match_appendix_b"),
+    "initial_grad_S_mirror_about_the_node_at_the_low_wall": (
+        "lo = o->bc[lo_side] == PERIODIC ? AT(n - 1) : AT(c);",
+        "lo = o->bc[lo_side] == PERIODIC ? AT(n - 1) : AT(c + 1);",
+        "tests/test_oracle_init.py::test_initial_g_moments_at_walls[low_mirror]"),
+    "initial_grad_S_mirror_about_the_node_at_the_high_wall": (
+        "hi = o->bc[hi_side] == PERIODIC ? AT(0) : AT(c);",
+        "hi = o->bc[hi_side] == PERIODIC ? AT(0) : AT(c - 1);",
+        "tests/test_oracle_init.py::test_initial_g_moments_at_walls[high_mirror]"),
+    "initial_grad_S_first_order_at_the_low_dirichlet_wall": (
+        "return (-3.0 * AT(0) + 4.0 * AT(1) - AT(2)) / 2.0;",
+        "return AT(1) - AT(0);",
+        "tests/test_oracle_init.py::test_initial_g_moments_at_walls[high_mirror]"),
+    "initial_grad_S_sign_at_the_high_dirichlet_wall": (
+        "return (3.0 * AT(n - 1) - 4.0 * AT(n - 2) + AT(n - 3)) / 2.0;",
+        "return (-3.0 * AT(n - 1) + 4.0 * AT(n - 2) - AT(n - 3)) / 2.0;",
+        "tests/test_oracle_init.py::test_initial_g_moments_at_walls[low_mirror]"),
     "variable_ds_without_oil_mobility": (
         "o->D_c * o->K[a] * lw * (lt - lw) / lt", "o->D_c * o->K[a] * lw * lt / lt",
         "tests/test_oracle_variants.py::test_variants_second_order[variable_ds]"),

@@ -87,10 +87,17 @@ def test_noalloc_sweep_matches_handle_entry_point(env):
 
 
 def test_noalloc_rejects_lattices_beyond_its_scratch(env):
+    """A lattice one row tile beyond the scratch is refused before any launch: every plane
+    pointer is NULL, so no ordering of the argument checks can let a kernel start."""
     torch, pkg = env
-    nx, ny = 1025, 40000                     # 2 row tiles per row: 80000 > 65536
+    nx = pkg.NOALLOC_TILE_NODES + 1                 # two row tiles per row
+    ny = pkg.NOALLOC_MAX_TILES // 2 + 1             # just beyond what the scratch holds
+    assert 2 * ny == pkg.NOALLOC_MAX_TILES + 2
+    pitch = (nx + 31) // 32 * 32
+    torch.cuda.synchronize()
     with pytest.raises(pkg.LBM2PError) as ei:
-        pkg.lbm2p_pressure_sweep_noalloc(nx, ny, 1056, (1, 1, 1, 1), [16] * 8, [32] * 8, 48, 64,
-                                         0, None, 80)
+        pkg.lbm2p_pressure_sweep_noalloc(nx, ny, pitch, (1, 1, 1, 1), [0] * 8, [0] * 8, 0, 0,
+                                         0, None, 0)
     assert ei.value.status == pkg.EINVAL
     assert "row tiles" in str(ei.value)
+    torch.cuda.synchronize()                        # nothing was queued, nothing failed
