@@ -1,16 +1,25 @@
 """Benchmark of the two-phase Darcy LB solver (one JSON line on stdout).
 
-Workload (default): the quarter five-spot of 1024 x 1024 nodes (ln K a seeded Gaussian
+Workload (default): the quarter five-spot of 4096 x 4096 nodes (ln K a seeded Gaussian
 random field, sigma 1, correlation length 16 cells; no-flux walls; injector and producer
 of rate 1e-3 at opposite corners; S0 = 0.2; phi = 0.2, beta = 0.4, mu_w = 1, mu_n = 2,
-D_s = 0.01, tau_p = 1, tau_s = 0.8), each physical step sub-iterating the pressure to a
-relative increment of 1e-8.  A step = S refresh + pressure sub-iteration + saturation
-update.  The t = 0 initialisation (the pressure solve, started from the same problem
-solved on a 4x coarser lattice unless --cold-start) is set-up, outside the timing.
+D_s = 0.01, tau_p = 1, tau_s = 0.8), FP32 populations, each physical step sub-iterating the
+pressure to a relative increment of 1e-8.  A step = S refresh + pressure sub-iteration +
+saturation update.  The t = 0 initialisation (the pressure solve, started from the same
+problem solved on a 4x coarser lattice unless --cold-start) is set-up, outside the timing;
+its solve is timed on the device on its own and reported beside the line.
 
 Metric: MLUPS = nodes x (pressure sweeps + 1 saturation update) / time, summed over the
 timed steps (and over ranks).  L2 is flushed before every timed step; each step is timed
 with CUDA events on the solver's stream.
+
+Roofline of the dominant kernel (the pressure sweep launch): algorithmic bytes = 68 B per
+node and pressure sweep (8 populations read and written, plus 1/tau_f) x the sweeps one
+launch performs x nodes, over the launch's average device time (CUDA events around the
+sweep batches, on the solver's stream), against the measured HBM copy bandwidth.  A launch
+that carries two sweeps moves the populations once, so this fraction can exceed 1; the
+DRAM bytes such a launch really moves (from an ncu capture of the same kernel source) give
+the DRAM-actual fraction beside it.
 
 Workload batch_five_spot_64: 64 independent five-spot realisations with sizes drawn from
 {128, 256, 512}^2 (sigma, correlation length and viscosity ratio drawn per member), advanced
@@ -18,7 +27,7 @@ together by one lbm2p_batch per step; the line also reports the same members ste
 after another.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload five_spot_1024|five_spot_4096|manufactured_64|batch_five_spot_64]
+                    [--workload five_spot_4096|five_spot_1024|manufactured_64|batch_five_spot_64]
 """
 from __future__ import annotations
 
@@ -39,37 +48,48 @@ sys.path.insert(0, ROOT)
 
 import workloads as W  # noqa: E402
 
-# algorithmic bytes per node of one pressure-sweep launch: 8 populations read and written
-# (stored as FP32 deviations) + the reference pressure + 1/tau_f; a launch that fuses T
-# sweeps moves the same bytes once for T sweeps
-BYTES_PER_SWEEP_NODE = 72
+# algorithmic bytes per node and pressure sweep (the paper's form of the sweep): 8
+# populations read and written + 1/tau_f; f_0 is never needed, the sparse wells add nothing
+BYTES_PER_NODE_SWEEP = 68
+# bytes per node the FP32 deviation storage really moves per launch (one pass over the
+# populations whatever the sweeps per launch): the 68 above + the reference pressure R
+BYTES_MOVED_PER_NODE = 72
 # with FP16 storage: 8 populations x (2 + 2) B + the node pressure read and written + 1/tau_f
 BYTES_PER_SWEEP_NODE_FP16 = 44
 WORKLOADS = {
-    "five_spot_1024": dict(kind="five_spot", n=1024),
     "five_spot_4096": dict(kind="five_spot", n=4096),
+    "five_spot_1024": dict(kind="five_spot", n=1024),
     "manufactured_64": dict(kind="manufactured", n=64),
     # independent five-spot realisations of uneven sizes advanced by one batch (lbm2p_batch)
     "batch_five_spot_64": dict(kind="batch", count=64, sizes=(128, 256, 512)),
 }
+DEFAULT_WORKLOAD = "five_spot_4096"
 SWEEP_KERNEL_NAMES = {1: "four nodes per thread (128-bit accesses)", 2: "one node per thread",
                       3: "rows staged in shared memory by bulk async copies"}
-# DRAM bytes per pressure-sweep launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum),
-# keyed by workload and launch form (sweeps per launch, fused tile width or single kernel
-# kind); absent until captured for the current kernel (profiles/).
-# five_spot_1024, one node per thread (the autotuner's choice there): 42.0 MB read + 0.9 MB
-# written per launch, L2 flushed by ncu before the launch.
-# five_spot_1024, two sweeps with direct loads, 120-column blocks of 4 rows (the autotuner's
-# choice there with the residual checked every 16 sweeps): 42.0 MB read + 0.95 MB written per
-# launch, L2 flushed by ncu before the launch.
-# five_spot_4096, two sweeps on staged rows, 120-column blocks (the autotuner's choice there):
-# 720.9 MB read + 493.1 MB written per launch (a launch without the residual).
-NCU_TRAFFIC_PER_LAUNCH = {("five_spot_1024", "single", 2): 42.87e6,
-                          ("five_spot_1024", "direct", 120): 42.94e6,
-                          ("five_spot_4096", "staged_rows", 120): 1214.0e6}
+# CUDA sources each launch form is compiled from; their hash keys the ncu captures below
+KERNEL_SOURCES = {
+    "two_sweep": ["sweep_rows.cu", "lbm2p_node.cuh", "lbm2p_device.cuh", "lbm2p_async.cuh"],
+    "single": ["kernels.cu", "sweep_rows.cu", "lbm2p_node.cuh", "lbm2p_device.cuh",
+               "lbm2p_async.cuh"],
+}
+# DRAM bytes per pressure-sweep launch (dram__bytes_read.sum + dram__bytes_write.sum) from
+# one ncu capture, keyed by workload and launch form (sweeps per launch, fused form, tile
+# width); each entry carries the hash of the kernel sources it was taken from and the
+# summary under profiles/ that holds the command.  A capture whose hash differs from the
+# sources being run is stale and is not reported.
+NCU_TRAFFIC_PER_LAUNCH = {}
 FUSED_FORM_NAMES = {1: "stages", 2: "staged_rows", 3: "direct"}
 FUSED_FORM_TEXT = {1: "on shared-memory stages", 2: "on rows staged by bulk copies",
                    3: "with direct loads"}
+
+
+def kernel_source_hash(form: str) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[form]:
+        with open(os.path.join(ROOT, "paper_1808_07554_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def batch_members(name: str, rank: int = 0):
@@ -206,27 +226,66 @@ class ClockSampler:
 # ---------------------------------------------------------------------------------------
 # CPU baseline: the FP64 oracle on the host cores, bounded sample of the same workload
 # ---------------------------------------------------------------------------------------
-def cpu_baseline(name: str, budget_s: float = 12.0):
+# sweeps per sample step of the oracle: (all host cores, one thread); fixed counts, so that
+# every run times the same work (a step = S refresh + the sweeps + the saturation update)
+CPU_SAMPLE_SWEEPS = {"five_spot_4096": (48, 4), "five_spot_1024": (400, 40),
+                     "manufactured_64": (4000, 2000), "batch_five_spot_64": (400, 40)}
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), with the machine type."""
+    import platform
+    name = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        fields = {ln.split(":", 1)[0].strip(): ln.split(":", 1)[1].strip()
+                  for ln in out.splitlines() if ":" in ln}
+        name = fields.get("Model name") or fields.get("Vendor ID") or ""
+    except Exception:
+        pass
+    if not name:
+        try:
+            for ln in open("/proc/cpuinfo"):
+                if ln.lower().startswith(("model name", "cpu part")):
+                    name = ln.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return f"{name or 'unknown'} ({platform.machine()})"
+
+
+def oracle_sample(orc, nodes: int, sweeps: int):
+    """One physical step of the oracle with a replayed sweep count: (lattice updates, s)."""
+    t0 = time.perf_counter()
+    orc.step(1, replay=[sweeps])
+    return nodes * (sweeps + 1), time.perf_counter() - t0
+
+
+def cpu_baseline(name: str, reps: int = 3):
+    """The FP64 oracle as it stands on the host cores, on a bounded sample of the workload:
+    `reps` steps of a fixed sweep count on all cores (median), and fewer sweeps on one thread."""
     import oracle as O
     prob = make_problem(name)
     orc = O.Oracle(prob, tol=1e-8, init_replay=0)
     nodes = prob.nx * prob.ny
-    # calibrate: one step of 5 sweeps
-    t0 = time.perf_counter()
-    orc.step(1, replay=[5])
-    t1 = time.perf_counter()
-    per_update = (t1 - t0) / (nodes * 6)
-    sweeps = max(5, int(budget_s / (per_update * nodes)) - 1)
-    t0 = time.perf_counter()
-    orc.step(1, replay=[sweeps])
-    dt = time.perf_counter() - t0
+    sw_all, sw_one = CPU_SAMPLE_SWEEPS.get(name, (100, 10))
+    cores = O.set_threads(os.cpu_count() or 1)
+    runs = [oracle_sample(orc, nodes, sw_all) for _ in range(reps)]
+    all_rates = sorted(u / t / 1e6 for u, t in runs)
+    O.set_threads(1)
+    u1, t1 = oracle_sample(orc, nodes, sw_one)
+    O.set_threads(cores)
     orc.close()
-    updates = nodes * (sweeps + 1)
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": updates / dt / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
-            "sample": f"{name}: 1 physical step with {sweeps} pressure sweeps + 1 saturation "
-                      f"update on the {prob.nx}x{prob.ny} lattice, {dt:.1f} s",
-            "seconds": dt}
+    value = all_rates[len(all_rates) // 2]
+    return {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": (f"{name}: {reps} physical steps of {sw_all} pressure sweeps + 1 "
+                       f"saturation update on the {prob.nx}x{prob.ny} lattice, all "
+                       f"{cores} host threads ({sum(t for _, t in runs):.1f} s; median); one "
+                       f"thread: 1 step of {sw_one} sweeps ({t1:.1f} s)"),
+            "single_thread": {"value": u1 / t1 / 1e6, "unit": "MLUPS", "cores": 1},
+            "all_cores_runs": [round(x, 2) for x in all_rates],
+            "cpu_model": cpu_model(),
+            "seconds": sum(t for _, t in runs) + t1}
 
 
 def aggregate(local_vals, dist=None, device="cpu"):
@@ -245,19 +304,36 @@ def aggregate(local_vals, dist=None, device="cpu"):
 
 
 def run_reference(args):
+    """The oracle as it stands, on the machine's host cores: every warm-up and timed step is
+    one sample of the workload (one physical step with the same fixed sweep count as the
+    CPU baseline's all-core leg); the value is the median over the timed steps."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    res = []
-    for _ in range(args.steps):
-        res.append(cpu_baseline(args.workload, budget_s=max(3.0, 60.0 / max(1, args.steps))))
-    value = statistics.median(r["value"] for r in res)
+    import oracle as O
+    prob = make_problem(args.workload)
+    nodes = prob.nx * prob.ny
+    orc = O.Oracle(prob, tol=1e-8, init_replay=0)
+    cores = O.set_threads(os.cpu_count() or 1)
+    sweeps = CPU_SAMPLE_SWEEPS.get(args.workload, (100, 10))[0]
+    for _ in range(args.warmup):
+        oracle_sample(orc, nodes, sweeps)
+    runs = [oracle_sample(orc, nodes, sweeps) for _ in range(args.steps)]
+    orc.close()
+    rates = sorted(u / t / 1e6 for u, t in runs)
+    value = rates[len(rates) // 2]
+    total = sum(t for _, t in runs)
     line = {"metric": "MLUPS", "value": value, "unit": "MLUPS", "impl": "reference",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / max(1, args.steps),
             "higher_is_better": True, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "tol": 1e-8},
-            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": res[0]["cores"],
-                             "kind": "oracle", "sample": res[0]["sample"]},
+            "config": {"workload": args.workload, "nx": prob.nx, "ny": prob.ny, "tol": 1e-8},
+            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                             "sample": (f"{args.workload}: each step one physical step of "
+                                        f"{sweeps} pressure sweeps + 1 saturation update on "
+                                        f"the {prob.nx}x{prob.ny} lattice, {cores} host "
+                                        f"threads; median of {args.steps} ({total:.1f} s)"),
+                             "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -295,14 +371,20 @@ def run_ours(args):
         P0 = coarse_initial_pressure(prob, pkg, log=coarse_log)
         if P0 is not None:
             prob.P0 = P0
+    torch.cuda.synchronize()
+    coarse_s = time.perf_counter() - t_setup
+    t_create = time.perf_counter()
     solver = pkg.Solver.from_problem(prob, tol=args.tol, check_every=args.check_every,
                                      max_sub_iters=args.max_sub_iters, fuse_sweeps=args.fuse_sweeps,
                                      sweep_kernel=args.sweep_kernel,
                                      storage=1 if args.storage == "fp16" else 0,
                                      warm_start=1 if args.warm_start == "extrapolate" else 0)
     torch.cuda.synchronize()
+    create_s = time.perf_counter() - t_create
     setup_s = time.perf_counter() - t_setup
     init_sweeps = solver.init_stats.sub_iters
+    # the t = 0 solve alone (device time, CUDA events inside create around the solve)
+    init_solve_s = solver.init_stats.step_ms / 1e3 if solver.init_stats.step_ms >= 0 else None
     solver.set_timing(True)
     sweep_cfg = solver.sweep_config()
     fform = solver.fused_form()
@@ -351,8 +433,9 @@ def run_ours(args):
     gpu_launches = launches1 - launches0
 
     # end to end: the public API with host buffers (per step: the step's source upload when
-    # the problem has one, the step, and the P and S fields read back to host memory)
-    e2e_steps = max(1, min(args.steps, 5))
+    # the problem has one, the step, and the P and S fields read back to host memory), over
+    # as many steps as the timed region
+    e2e_steps = max(1, args.steps)
     h2d = 0 if prob.sources_at is None else 2 * 8 * nodes
     d2h = 2 * 4 * nodes
     # the step's result is read into page-locked host buffers (allocated once, outside)
@@ -382,52 +465,73 @@ def run_ours(args):
     avg_sweep_s = float(np.sum(sweep_ms)) / 1e3 / max(1, sweeps_timed)
     fused = sweep_cfg[0]
     avg_launch_s = avg_sweep_s * fused
-    bpn = BYTES_PER_SWEEP_NODE_FP16 if args.storage == "fp16" else BYTES_PER_SWEEP_NODE
+    fp16 = args.storage == "fp16"
+    # algorithmic bytes per launch: 68 B per node and sweep x the sweeps of one launch
+    bpn = BYTES_PER_SWEEP_NODE_FP16 if fp16 else BYTES_PER_NODE_SWEEP * fused
     achieved = bpn * nodes / avg_launch_s / 1e9
-    # the captured traffic belongs to one FP32 launch form; any other choice of the
-    # autotuner has no capture here
     form = ((args.workload, FUSED_FORM_NAMES.get(fform, "?"), sweep_cfg[2]) if fused > 1
             else (args.workload, "single", sweep_cfg[1]))
-    traffic = NCU_TRAFFIC_PER_LAUNCH.get(form) if args.storage == "fp32" else None
+    src_form = "two_sweep" if fused > 1 else "single"
+    src_hash = kernel_source_hash(src_form)
+    cap = NCU_TRAFFIC_PER_LAUNCH.get(form) if not fp16 else None
+    traffic = cap["bytes"] if cap is not None and cap["sources"] == src_hash else None
+    hist = {}
+    for k in ksub:
+        hist[str(k)] = hist.get(str(k), 0) + 1
+    kernel_text = ("pressure sweep (fused stream + collide, Eq. 3-1), "
+                   + (("FP16 populations, " + SWEEP_KERNEL_NAMES.get(sweep_cfg[1], "?"))
+                      if fp16 else
+                      ((f"{fused} sweeps per launch " + FUSED_FORM_TEXT.get(fform, "?"))
+                       if fused > 1 else SWEEP_KERNEL_NAMES.get(sweep_cfg[1], "?"))
+                      + (", autotuned" if args.sweep_kernel == 0 else "")))
     line = {
         "metric": "MLUPS", "value": updates_all / time_max / 1e6, "unit": "MLUPS",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32" if args.storage == "fp32" else "f16 storage, f32 arithmetic",
+        "vs_baseline": None, "dtype": "f16 storage, f32 arithmetic" if fp16 else "f32",
         "data": "synthetic",
         "config": {"workload": args.workload, "nx": prob.nx, "ny": prob.ny, "tol": args.tol,
                    "storage": args.storage, "warm_start": args.warm_start,
                    "check_every": args.check_every, "fuse_sweeps": args.fuse_sweeps,
                    "sweep_kernel": sweep_cfg[1], "sweep_tile": [sweep_cfg[2], sweep_cfg[3]],
                    "fused_form": FUSED_FORM_NAMES.get(fform, "none"),
-                   "l2": "flushed before every timed step",
-                   "sub_iters_per_step": ksub, "statuses": statuses,
-                   "init_sweeps": init_sweeps, "setup_s": round(setup_s, 2),
-                   "coarse_levels": coarse_log,
-                   "initial_guess": "P0 = 0" if args.cold_start or prob.wells == [] else
-                                    "P0 from the same problem on a 4x coarser lattice (set-up)",
+                   "l2": "flushed before every timed step (256 MB write)",
+                   "sub_iters_per_step": ksub, "sub_iters_histogram": hist,
+                   "statuses": statuses,
+                   "setup": {"coarse_guess_s": round(coarse_s, 2), "coarse_levels": coarse_log,
+                             "create_s": round(create_s, 2),
+                             "init_solve_sweeps": init_sweeps,
+                             "init_solve_s": (round(init_solve_s, 3)
+                                              if init_solve_s is not None else None),
+                             "init_solve_from": ("P0 = 0" if args.cold_start or prob.wells == []
+                                                 else "P0 from the same problem on a 4x "
+                                                      "coarser lattice"),
+                             "total_s": round(setup_s, 2),
+                             "note": ("create_s = kernel autotuning + uploads + the t = 0 "
+                                      "solve; init_solve_s is that solve alone")},
                    "wall_s": round(wall, 3),
                    "parallelism": f"{world} independent realisations (seed 2 + rank)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": ("pressure sweep (fused stream + collide, Eq. 3-1), "
-                                + (("FP16 populations, " + SWEEP_KERNEL_NAMES.get(sweep_cfg[1], "?"))
-                                   if args.storage == "fp16"
-                                   else ((f"{fused} sweeps per launch "
-                                          + FUSED_FORM_TEXT.get(fform, "?"))
-                                         if fused > 1 else
-                                         SWEEP_KERNEL_NAMES.get(sweep_cfg[1], "?"))
-                                   + (", autotuned" if args.sweep_kernel == 0 else ""))),
-                     "bytes_per_launch": bpn * nodes, "sweeps_per_launch": fused,
+                     "kernel": kernel_text,
+                     "bytes_per_launch": bpn * nodes,
+                     "bytes_model": ("44 B per node and sweep (FP16 storage)" if fp16 else
+                                     f"68 B per node and sweep x {fused} sweeps per launch"),
+                     "sweeps_per_launch": fused,
                      "avg_launch_us": avg_launch_s * 1e6,
-                     # a launch of several sweeps moves one sweep's bytes: its sweeps at the
-                     # single-sweep byte count, for comparison with one-sweep kernels
-                     "sweep_equivalent_gbs": fused * achieved,
                      "launch_time_includes": ("the residual finalize kernel of every "
                                               f"{args.check_every}th sweep"),
+                     "dram_bytes_moved_model": (None if fp16 else BYTES_MOVED_PER_NODE * nodes),
+                     "dram_frac": (traffic / avg_launch_s / 1e9 / peak
+                                   if traffic is not None else None),
+                     "traffic_source": (f"ncu capture, {cap['profile']}" if traffic is not None
+                                        else "no ncu capture of these kernel sources"),
+                     "kernel_sources": src_hash,
                      "peak_kind": peak_kind},
         "e2e": {"value": e2e_all / e2e_max / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+                "d2h_bytes_per_step": d2h, "steps": e2e_steps,
+                "note": ("the five-spot has no per-step inputs (its wells are fixed at create)"
+                         if h2d == 0 else "per-step dense sources uploaded from host memory")},
         "gpu_launches": int(gpu_launches),
         "clocks": clk,
     }
@@ -515,7 +619,7 @@ def run_batch(args):
     gpu_launches = batch.counters()[0] - launches0
     k = np.array(kmat, dtype=np.int64)                       # [steps, members]
     updates = int(np.sum(k * nodes[None, :]) + args.steps * nodes.sum())
-    step_bytes = float(np.sum((BYTES_PER_SWEEP_NODE * k + BYTES_PER_STEP_NODE) * nodes[None, :]))
+    step_bytes = float(np.sum((BYTES_MOVED_PER_NODE * k + BYTES_PER_STEP_NODE) * nodes[None, :]))
     total_ms = float(np.sum(step_ms))
 
     # end to end: batch step + P and S of every member read back to host memory
@@ -599,7 +703,7 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="five_spot_1024")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
     ap.add_argument("--check-every", type=int, default=None,
                     help="sweeps between residual checks (default: 16 for solves that continue "
                          "from the previous step, 8 with the warm start, whose steps take 16-24 "

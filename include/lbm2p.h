@@ -192,7 +192,9 @@ void lbm2p_default_params(lbm2p_params *p);
 /* Create a solver and run the t = 0 initialisation of Sec. 4: f = f^eq(P0) (Eq. 3-3),
  * tau_f from S0, the pressure solve, then g(0) = g^eq(S0) + eps g^(1) (Eqs. gini, gneq;
  * grad S0 by second-order central differences, grad P by Eq. 3-10a) followed by the t = 0
- * collision of g.  init_stats (may be NULL) receives the t = 0 solve's statistics.
+ * collision of g.  init_stats (may be NULL) receives the t = 0 solve's statistics; its
+ * step_ms is the device time of that solve alone (CUDA events around it, whatever the
+ * timing setting; the create-time kernel tuning and the uploads are not in it).
  * Returns EINVAL for inconsistent parameters (nothing allocated, *out = NULL). */
 lbm2p_status lbm2p_create(lbm2p **out, const lbm2p_params *p, const lbm2p_inputs *in,
                           lbm2p_step_stats *init_stats);

@@ -80,6 +80,8 @@ def _load():
             lib.orc_constants.argtypes = [C.c_void_p, dp]
             lib.orc_sums.argtypes = [C.c_void_p, dp]
             lib.orc_saturation_source.argtypes = [C.c_void_p, dp]
+            lib.orc_set_threads.argtypes = [C.c_int]
+            lib.orc_set_threads.restype = C.c_int
             _lib = lib
     return _lib
 
@@ -97,6 +99,12 @@ def _f64(a, shape=None):
     if shape is not None and a.shape != shape:
         a = a.reshape(shape)
     return a
+
+
+def set_threads(n: int = 0) -> int:
+    """Host threads the oracle's loops use from now on (n <= 0: leave as is); returns the
+    count in effect."""
+    return int(_load().orc_set_threads(int(n)))
 
 
 class OracleError(RuntimeError):

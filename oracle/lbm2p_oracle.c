@@ -47,6 +47,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_OK 0
 #define ORC_EINVAL 1
@@ -884,4 +887,19 @@ void orc_sums(const orc *o, double *out)
 void orc_saturation_source(const orc *o, double *out)
 {
     memcpy(out, o->Fs_t, o->n * sizeof(double));
+}
+
+/* Host threads of the oracle's node loops (OpenMP; 1 when built without it).  Used by the
+   timing of the CPU baseline, never by the arithmetic: every loop is over independent nodes,
+   so the results do not depend on the thread count. */
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0)
+        omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }
