@@ -261,6 +261,168 @@ __device__ __forceinline__ float second_pull(float nb, float own_opp, const RNbh
     return -b + 2.0f * wgt(I) * (Pb[side][k] - r0);
 }
 
+// Consumer warp of k_pressure_rows2 in a block whose first-sweep footprint (columns
+// x0 - 1 .. x0 + W, rows y0 - 1 .. y0 + H) holds no wall node and no well, so that every
+// pull of both sweeps comes from a lattice neighbour.  It runs the general consumer's
+// protocol (the same waits, releases and give-up rule) and the same per-node arithmetic, so
+// it writes the same populations bit for bit, without the wall and well tests.  The row loop
+// is unrolled by two: the values a row hands to the rows after it are kept in two register
+// sets indexed by the row's parity, so none is copied from row to row.
+//   one row later:  v_1, v_3 (directions 1, 3), 1/tau_f, w_bar F~_p, dP of the first sweep;
+//   two rows later: v_2, v_5, v_6 (directions pulled from below) and R.
+template <bool CHECK, bool HAS_FP, int CW, int S>
+struct Rows2Interior {
+    static constexpr int RW = 30 * CW + 2 * kRowsHalo;
+    const PressureArgs &a;
+    const float *ring;
+    int slot_floats;
+    uint64_t *full, *empty;
+    int lane, lx, q;
+    unsigned ph;
+    const float *sm, *s0, *sp;     // staged input rows t - 2, t - 1, t
+    int qm;                        // slot of row t - 2 (released after the first sweep)
+    int o;                         // output offset of the second sweep's node
+    bool owner, ok;
+    float c0[2], c2[2], d1[2], d4[2], d5[2], rr[2], tt[2], qq[2], dd[2];
+    ResAcc racc;
+    float shift, dshift;
+
+    __device__ __forceinline__ Rows2Interior(const PressureArgs &a_, const float *ring_, int sf,
+                                             uint64_t *full_, uint64_t *empty_, int lane_,
+                                             int lx_, int o0, bool owner_, float shift_,
+                                             float dshift_)
+        : a(a_), ring(ring_), slot_floats(sf), full(full_), empty(empty_), lane(lane_), lx(lx_),
+          q(0), ph(0u), sm(ring_), s0(ring_), sp(ring_), qm(0), o(o0), owner(owner_), ok(true),
+          shift(shift_), dshift(dshift_)
+    {
+    }
+
+    // wait for input row t (the next one) and make (sm, s0, sp) rows t - 2, t - 1, t
+    __device__ __forceinline__ bool next_row()
+    {
+        ok = bar_wait_bounded(full + q, ph);
+        sm = s0;
+        s0 = sp;
+        sp = ring + (size_t)q * slot_floats;
+        qm = q == 0 ? S - 2 : (q == 1 ? S - 1 : q - 2);
+        if (++q == S) {
+            q = 0;
+            ph ^= 1u;
+        }
+        return ok;
+    }
+
+    // first sweep at the row of s0 from the staged rows (sm, s0, sp); then row t - 2 is
+    // released
+    __device__ __forceinline__ void first(float (&v)[8], float &r0, float &it, float &Fq,
+                                          float &dP)
+    {
+        r0 = s0[8 * RW + lx];
+        float f[8];
+        f[0] = dev1(s0[0 * RW + lx - 1], wgt(1), s0[8 * RW + lx - 1], r0);
+        f[1] = dev1(sm[1 * RW + lx], wgt(2), sm[8 * RW + lx], r0);
+        f[2] = dev1(s0[2 * RW + lx + 1], wgt(3), s0[8 * RW + lx + 1], r0);
+        f[3] = dev1(sp[3 * RW + lx], wgt(4), sp[8 * RW + lx], r0);
+        f[4] = dev1(sm[4 * RW + lx - 1], wgt(5), sm[8 * RW + lx - 1], r0);
+        f[5] = dev1(sm[5 * RW + lx + 1], wgt(6), sm[8 * RW + lx + 1], r0);
+        f[6] = dev1(sp[6 * RW + lx + 1], wgt(7), sp[8 * RW + lx + 1], r0);
+        f[7] = dev1(sp[7 * RW + lx - 1], wgt(8), sp[8 * RW + lx - 1], r0);
+        dP = pressure_of(f);
+        it = s0[9 * RW + lx];
+        const float F = HAS_FP ? s0[10 * RW + lx] : 0.0f;
+        Fq = 0.125f * F;   // w_bar_i = 1/8 (Eq. 3-5a)
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            v[i] = collide1(f[i], wgt(i + 1), dP, it, Fq);
+        __syncwarp();
+        if (lane == 0)
+            bar_arrive(empty + qm);
+    }
+
+    template <int P>
+    __device__ __forceinline__ void keep(const float (&v)[8], float r0, float it, float Fq,
+                                         float dP)
+    {
+        c0[P] = v[0];
+        c2[P] = v[2];
+        d1[P] = v[1];
+        d4[P] = v[4];
+        d5[P] = v[5];
+        rr[P] = r0;
+        tt[P] = it;
+        if (HAS_FP)
+            qq[P] = Fq;
+        if (CHECK)
+            dd[P] = dP;
+    }
+
+    // a row whose first sweep has parity P (rows t >= 4): first sweep, then the second sweep
+    // one row behind it, from the register sets of both parities and warp shuffles
+    template <int P>
+    __device__ __forceinline__ void both()
+    {
+        float v[8], r0, it, Fq, dP1;
+        first(v, r0, it, Fq, dP1);
+        const float Rm = rr[P], Rc = rr[1 - P];
+        const float m0 = __shfl_up_sync(0xffffffffu, Rm, 1);
+        const float c0r = __shfl_up_sync(0xffffffffu, Rc, 1);
+        const float p0 = __shfl_up_sync(0xffffffffu, r0, 1);
+        const float m2 = __shfl_down_sync(0xffffffffu, Rm, 1);
+        const float c2r = __shfl_down_sync(0xffffffffu, Rc, 1);
+        const float p2 = __shfl_down_sync(0xffffffffu, r0, 1);
+        float f[8];
+        f[0] = dev1(__shfl_up_sync(0xffffffffu, c0[1 - P], 1), wgt(1), c0r, Rc);
+        f[1] = dev1(d1[P], wgt(2), Rm, Rc);
+        f[2] = dev1(__shfl_down_sync(0xffffffffu, c2[1 - P], 1), wgt(3), c2r, Rc);
+        f[3] = dev1(v[3], wgt(4), r0, Rc);
+        f[4] = dev1(__shfl_up_sync(0xffffffffu, d4[P], 1), wgt(5), m0, Rc);
+        f[5] = dev1(__shfl_down_sync(0xffffffffu, d5[P], 1), wgt(6), m2, Rc);
+        f[6] = dev1(__shfl_down_sync(0xffffffffu, v[6], 1), wgt(7), p2, Rc);
+        f[7] = dev1(__shfl_up_sync(0xffffffffu, v[7], 1), wgt(8), p0, Rc);
+        const float dP = pressure_of(f);
+        if (owner) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                a.fout[i][o] = collide1(f[i], wgt(i + 1), dP, tt[1 - P], HAS_FP ? qq[1 - P] : 0.0f);
+            if (CHECK)
+                racc.add((dP - dd[1 - P]) - dshift, (Rc - shift) + dP);
+        }
+        o += a.g.pitch;
+        keep<P>(v, r0, it, Fq, dP1);
+    }
+
+    // rows 0 .. nrows - 1 of the block; false when a wait gave up
+    __device__ __forceinline__ bool run(int nrows)
+    {
+        if (!next_row() || !next_row())
+            return false;
+        float v[8], r0, it, Fq, dP;
+        if (!next_row())
+            return false;
+        first(v, r0, it, Fq, dP);
+        keep<0>(v, r0, it, Fq, dP);
+        if (!next_row())
+            return false;
+        first(v, r0, it, Fq, dP);
+        keep<1>(v, r0, it, Fq, dP);
+        int t = 4;
+        for (; t + 1 < nrows; t += 2) {
+            if (!next_row())
+                return false;
+            both<0>();
+            if (!next_row())
+                return false;
+            both<1>();
+        }
+        if (t < nrows) {
+            if (!next_row())
+                return false;
+            both<0>();
+        }
+        return true;
+    }
+};
+
 template <bool CHECK, int CW, int S>
 __global__ void __launch_bounds__(32 * (CW + 1), CW == 4 ? 6 : 3) k_pressure_rows2(const __grid_constant__ PressureArgs a,
                                                                   int H)
@@ -293,6 +455,14 @@ __global__ void __launch_bounds__(32 * (CW + 1), CW == 4 ? 6 : 3) k_pressure_row
     const int xb = x0 + W + kRowsHalo < p ? x0 + W + kRowsHalo : p;
     const unsigned seg = (unsigned)(xb - xa) * 4u;
     const int soff = xa - (x0 - kRowsHalo);
+    // no wall node and no well among the first sweep's nodes x0 - 1 .. x0 + W,
+    // y0 - 1 .. y1 (the second sweep's nodes lie inside them)
+    bool interior_block = x0 >= 2 && x0 + W <= g.nx - 2 && y0 >= 2 && y1 <= g.ny - 2;
+    for (int w = 0; w < a.w.n && interior_block; ++w) {
+        const int wy = a.w.idx[w] / p, wx = a.w.idx[w] - wy * p;
+        if (wx >= x0 - 1 && wx <= x0 + W && wy >= y0 - 1 && wy <= y1)
+            interior_block = false;
+    }
 
     if (threadIdx.x == 0) {
         for (int q = 0; q < S; ++q) {
@@ -343,6 +513,45 @@ __global__ void __launch_bounds__(32 * (CW + 1), CW == 4 ? 6 : 3) k_pressure_row
             }
             for (int t = issued - S > 0 ? issued - S : 0; t < issued; ++t)
                 bar_wait_bounded(full + t % S, (unsigned)(t / S) & 1u);
+        }
+    } else if (interior_block) {
+        // ---- consumers of a block without walls or wells -------------------------------
+        const int x = x0 - 1 + 30 * warp + lane;
+        const bool owner = lane >= 1 && lane <= 30;
+        bool done;
+        ResAcc racc;
+        if (a.Fp) {
+            Rows2Interior<CHECK, true, CW, S> c(a, ring, slot_floats, full, empty, lane,
+                                                x - (x0 - kRowsHalo), y0 * p + x, owner,
+                                                CHECK ? a.shift[0] : 0.0f,
+                                                CHECK ? a.shift[1] : 0.0f);
+            done = c.run(nrows);
+            racc = c.racc;
+        } else {
+            Rows2Interior<CHECK, false, CW, S> c(a, ring, slot_floats, full, empty, lane,
+                                                 x - (x0 - kRowsHalo), y0 * p + x, owner,
+                                                 CHECK ? a.shift[0] : 0.0f,
+                                                 CHECK ? a.shift[1] : 0.0f);
+            done = c.run(nrows);
+            racc = c.racc;
+        }
+        if (!done) {
+            failed = 1;
+            const float nan = __int_as_float(0x7fc00000);
+            if (owner)
+                for (int y = y0; y < y1; ++y)
+                    for (int i = 0; i < 8; ++i)
+                        a.fout[i][y * p + x] = nan;
+        }
+        if (CHECK) {
+            double v[4];
+            racc.warp_totals(v);
+            if (lane == 0) {
+                red[warp][0] = v[0];
+                red[warp][1] = v[1];
+                red[warp][2] = v[2];
+                red[warp][3] = v[3];
+            }
         }
     } else {
         // ---- consumers -----------------------------------------------------------------

@@ -30,7 +30,10 @@ def _problem(kind):
         return W.quarter_five_spot(2049, 17, seed=6, corr_len=4.0)
     if kind == "periodic":
         return W.manufactured_periodic(96)
+    # "wide_dirichlet": wide enough that the two-sweep row-walking kernels have blocks with
+    # no wall and no well (their interior path), here with a dense pressure source
     nx, ny, bc = {"dirichlet": (97, 70, (2, 2, 2, 2)), "mixed": (65, 129, (0, 0, 2, 2)),
+                  "wide_dirichlet": (523, 161, (2, 2, 1, 1)),
                   "tiny": (5, 3, (1, 1, 0, 0)), "column": (1, 7, (0, 0, 0, 0)),
                   "tall": (31, 300, (2, 2, 1, 1))}[kind]
     Pb = [rng.random(2 * (ny if s < 2 else nx) + 1) for s in range(4)]
@@ -41,7 +44,7 @@ def _problem(kind):
 
 
 @pytest.mark.parametrize("kind", ["five_spot_ragged", "wide_ragged", "periodic", "dirichlet",
-                                  "mixed", "tiny", "column", "tall"])
+                                  "mixed", "tiny", "column", "tall", "wide_dirichlet"])
 @pytest.mark.parametrize("T", [2, 4, "2rows", "2direct"])
 def test_fused_equals_single_sweeps(kind, T):
     """T = 2 or 4 sweeps on shared-memory stages; "2rows": two sweeps on rows staged by
