@@ -47,6 +47,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 import workloads as W  # noqa: E402
+from paper_1808_07554_gb300.initial_guess import coarse_initial_pressure  # noqa: E402
 
 # algorithmic bytes per node and pressure sweep (the paper's form of the sweep): 8
 # populations read and written + 1/tau_f; f_0 is never needed, the sparse wells add nothing
@@ -117,29 +118,30 @@ def make_problem(name: str, rank: int = 0):
     return W.manufactured_periodic(w["n"])
 
 
-def coarse_initial_pressure(prob, pkg, factor=4, min_n=64, log=None):
-    """Initial pressure guess for a five-spot from the same problem on a coarser lattice
-    (set-up only; the paper leaves the t = 0 guess free).  K is averaged geometrically
-    over factor x factor blocks, the wells stay at the corner nodes, dt scales with dx^2;
-    the coarse solve itself starts from a still coarser guess, down to min_n nodes, and is
-    only converged to a relative increment of 1e-6 (a guess, not a solution)."""
-    if prob.wells == [] or prob.nx % factor or prob.ny % factor or prob.nx // factor < min_n:
-        return None
-    nx, ny = prob.nx // factor, prob.ny // factor
-    lnK = np.log(prob.K).reshape(ny, factor, nx, factor).mean(axis=(1, 3))
-    c = W.quarter_five_spot(nx, ny, seed=0)
-    c.K = np.exp(lnK)
-    c.dx, c.dt = prob.dx * factor, prob.dt * factor * factor
-    c.mu_w, c.mu_n, c.tau_p = prob.mu_w, prob.mu_n, prob.tau_p
-    c.wells = [(0, 0, prob.wells[0][2], 0), (nx - 1, ny - 1, prob.wells[1][2], 1)]
-    c.S0 = prob.S0.reshape(ny, factor, nx, factor).mean(axis=(1, 3))
-    c.P0 = coarse_initial_pressure(c, pkg, factor, min_n, log)
-    s = pkg.Solver.from_problem(c, tol=1e-6, max_sub_iters=200_000)
-    if log is not None:
-        log.append({"n": nx, "sweeps": s.init_stats.sub_iters, "r": s.init_stats.residual})
-    P, _ = s.fields()
-    s.close()
-    return np.kron(P.astype(np.float64), np.ones((factor, factor)))
+def train_operator(pkg, args):
+    """Set-up of --warm-start learned: quarter five-spot realisations at the training size
+    (GRF ln K with sigma 1 and correlation length 16 cells, seeds 6000 + r) stepped by the
+    solver, their converged fields recorded, and the five-layer operator trained on them."""
+    import torch
+    from paper_1808_07554_gb300.operator import PressureOperator, record_snapshots, train
+    t0 = time.perf_counter()
+    probs = [W.quarter_five_spot(args.op_size, seed=6000 + r) for r in range(args.op_realisations)]
+    gen_log = []
+    runs = record_snapshots(pkg, probs, args.op_steps, log=gen_log)
+    t1 = time.perf_counter()
+    op = PressureOperator(seed=1)
+    train_log = []
+    losses = train(op, runs, epochs=args.op_epochs, batch=16, lr=1e-3,
+                   max_seconds=args.op_seconds, log=train_log)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    del runs
+    snaps = args.op_realisations * (args.op_steps - 1)
+    return op, {"training_size": args.op_size, "realisations": args.op_realisations,
+                "steps_each": args.op_steps, "snapshots": snaps,
+                "data_s": round(t1 - t0, 1), "train_s": round(t2 - t1, 1),
+                "epochs": train_log, "final_loss": losses[-1] if losses else None,
+                "sweeps_in_data": int(sum(g["sweeps"] for g in gen_log))}
 
 
 def peaks():
@@ -373,6 +375,9 @@ def run_ours(args):
             prob.P0 = P0
     torch.cuda.synchronize()
     coarse_s = time.perf_counter() - t_setup
+    op_log = None
+    if args.warm_start == "learned":
+        op, op_log = train_operator(pkg, args)
     t_create = time.perf_counter()
     solver = pkg.Solver.from_problem(prob, tol=args.tol, check_every=args.check_every,
                                      max_sub_iters=args.max_sub_iters, fuse_sweeps=args.fuse_sweeps,
@@ -381,6 +386,14 @@ def run_ours(args):
                                      warm_start=1 if args.warm_start == "extrapolate" else 0)
     torch.cuda.synchronize()
     create_s = time.perf_counter() - t_create
+    do_step = lambda: solver.step(1)          # noqa: E731
+    if args.warm_start == "learned":
+        from paper_1808_07554_gb300.operator import LearnedWarmStart
+        lw = LearnedWarmStart(op, solver, np.log(prob.K))
+        for _ in range(2):                     # the features need two time levels
+            solver.step(1)
+            lw.prime()
+        do_step = lw.step
     setup_s = time.perf_counter() - t_setup
     init_sweeps = solver.init_stats.sub_iters
     # the t = 0 solve alone (device time, CUDA events inside create around the solve)
@@ -388,6 +401,9 @@ def run_ours(args):
     solver.set_timing(True)
     sweep_cfg = solver.sweep_config()
     fform = solver.fused_form()
+    # the autotuner's candidates (us per sweep in the solve loop), fastest first
+    report = sorted(solver.autotune_report(), key=lambda r: r[-1])
+    autotune_best = [" ".join(str(v) for v in r) for r in report[:8]]
 
     # problems with time-dependent sources get them uploaded every step (host buffers)
     def upload(n):
@@ -398,7 +414,7 @@ def run_ours(args):
     for _ in range(args.warmup):
         step_no += 1
         upload(step_no)
-        solver.step(1)
+        do_step()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -416,7 +432,7 @@ def run_ours(args):
         step_no += 1
         upload(step_no)
         ev0.record(stream)
-        st, stats = solver.step(1)
+        st, stats = do_step()
         ev1.record(stream)
         ev1.synchronize()
         step_ms.append(ev0.elapsed_time(ev1))
@@ -447,7 +463,7 @@ def run_ours(args):
     for _ in range(e2e_steps):
         step_no += 1
         upload(step_no)
-        st, stats = solver.step(1)
+        st, stats = do_step()
         solver.fields(out=host_out)
         e2e_updates += nodes * (stats[0].sub_iters + 1)
     e2e_s = time.perf_counter() - t0
@@ -495,6 +511,7 @@ def run_ours(args):
                    "check_every": args.check_every, "fuse_sweeps": args.fuse_sweeps,
                    "sweep_kernel": sweep_cfg[1], "sweep_tile": [sweep_cfg[2], sweep_cfg[3]],
                    "fused_form": FUSED_FORM_NAMES.get(fform, "none"),
+                   "autotune_best": autotune_best,
                    "l2": "flushed before every timed step (256 MB write)",
                    "sub_iters_per_step": ksub, "sub_iters_histogram": hist,
                    "statuses": statuses,
@@ -510,6 +527,7 @@ def run_ours(args):
                              "note": ("create_s = kernel autotuning + uploads + the t = 0 "
                                       "solve; init_solve_s is that solve alone")},
                    "wall_s": round(wall, 3),
+                   "learned_operator": op_log,
                    "parallelism": f"{world} independent realisations (seed 2 + rank)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
@@ -714,9 +732,17 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fuse-sweeps", type=int, default=0, choices=[0, 1, 2, 4],
                     help="pressure sweeps per launch: 0 = autotuned, 1, 2 or 4")
-    ap.add_argument("--warm-start", choices=["none", "extrapolate"], default="none",
-                    help="start of each pressure solve: the previous step's populations (none) "
-                         "or their equilibrium part moved to 2 P^n - P^(n-1) (extrapolate)")
+    ap.add_argument("--warm-start", choices=["none", "extrapolate", "learned"], default="none",
+                    help="start of each pressure solve: the previous step's populations (none), "
+                         "their equilibrium part moved to 2 P^n - P^(n-1) (extrapolate) or to "
+                         "the five-layer operator's prediction (learned; trained first, at set-up, "
+                         "on snapshots the solver produces)")
+    ap.add_argument("--op-size", type=int, default=256, help="training lattice size (learned)")
+    ap.add_argument("--op-realisations", type=int, default=20)
+    ap.add_argument("--op-steps", type=int, default=1001,
+                    help="steps recorded per training realisation")
+    ap.add_argument("--op-epochs", type=int, default=2)
+    ap.add_argument("--op-seconds", type=float, default=120.0, help="cap on training time")
     ap.add_argument("--storage", choices=["fp32", "fp16"], default="fp32",
                     help="pressure populations during the sub-iteration: FP32 or FP16 deviations")
     ap.add_argument("--tol", type=float, default=1e-8,
@@ -731,7 +757,7 @@ def main():
         # a check period has a fixed cost (the checking launch, the finalize kernel and the
         # graph's loop condition): at 1024^2 about 12 us, 10 % of eight sweeps; checking every
         # 16 sweeps halves it for 0.7 % more sweeps per converged step
-        args.check_every = 8 if args.warm_start == "extrapolate" else 16
+        args.check_every = 16 if args.warm_start == "none" else 8
     if args.impl == "reference":
         return run_reference(args)
     if WORKLOADS[args.workload]["kind"] == "batch":

@@ -122,6 +122,23 @@ def load_library(path: str = LIB_PATH):
         "lbm2p_batch_destroy": (None, [H]),
         "lbm2p_last_error": (C.c_char_p, [H]),
         "lbm2p_destroy": (None, [H]),
+        # the pressure operator (include/lbm2p_operator.h); device pointers as void *
+        "lbm2p_op_conv3x3": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                       C.c_void_p, C.c_void_p] + [C.c_int] * 6
+                             + [C.c_void_p, C.c_void_p]),
+        "lbm2p_op_conv3x3_wgrad": (C.c_int, [C.c_void_p] * 4 + [C.c_int] * 6
+                                   + [C.c_void_p, C.c_void_p]),
+        "lbm2p_op_flip_weights": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int,
+                                            C.c_void_p]),
+        "lbm2p_op_adam": (C.c_int, [C.c_void_p] * 5 + [C.c_longlong] + [C.c_float] * 4
+                          + [C.c_int, C.c_void_p]),
+        "lbm2p_op_diff_stats": (C.c_int, [C.c_void_p, C.c_void_p, C.c_longlong, C.c_void_p,
+                                          C.c_void_p]),
+        "lbm2p_op_features": (C.c_int, [C.c_void_p] * 8 + [C.c_int] * 2 + [C.c_float] * 2
+                              + [C.c_void_p]),
+        "lbm2p_op_target": (C.c_int, [C.c_void_p] * 5 + [C.c_int] * 2 + [C.c_void_p]),
+        "lbm2p_op_predict": (C.c_int, [C.c_void_p] * 5 + [C.c_int] * 2 + [C.c_void_p]),
+        "lbm2p_op_mse_grad": (C.c_int, [C.c_void_p] * 4 + [C.c_longlong, C.c_int, C.c_void_p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -236,6 +253,50 @@ def lbm2p_pressure_sweep_noalloc(nx, ny, pitch, bc, n_in, n_out, R, inv_tau, Fp,
     return r.value
 
 
+# ---- the pressure operator (include/lbm2p_operator.h): device pointers as ints ----------
+def lbm2p_op_conv3x3(x, w, bias, mask, y, y0, n_img, H, W, c_in, c_out, act, err, stream=0):
+    _check(_lib_or_raise().lbm2p_op_conv3x3(x, w, bias or None, mask or None, y or None,
+                                            y0 or None, n_img, H, W, c_in, c_out, act, err,
+                                            stream or None))
+
+
+def lbm2p_op_conv3x3_wgrad(x, g, dw, dbias, n_img, H, W, c_in, c_out, accumulate, err, stream=0):
+    _check(_lib_or_raise().lbm2p_op_conv3x3_wgrad(x, g, dw, dbias or None, n_img, H, W, c_in,
+                                                  c_out, int(bool(accumulate)), err,
+                                                  stream or None))
+
+
+def lbm2p_op_flip_weights(w, wt, c_in, c_out, stream=0):
+    _check(_lib_or_raise().lbm2p_op_flip_weights(w, wt, c_in, c_out, stream or None))
+
+
+def lbm2p_op_adam(p, g, m, v, pb, n, lr, beta1, beta2, eps, t, stream=0):
+    _check(_lib_or_raise().lbm2p_op_adam(p, g, m, v, pb or None, n, lr, beta1, beta2, eps, t,
+                                         stream or None))
+
+
+def lbm2p_op_diff_stats(a, b, n, stats, stream=0):
+    _check(_lib_or_raise().lbm2p_op_diff_stats(a, b, n, stats, stream or None))
+
+
+def lbm2p_op_features(lnK, S, S_prev, P, P_prev, ds_stats, dp_stats, feat, H, W, s_mean, s_scale,
+                      stream=0):
+    _check(_lib_or_raise().lbm2p_op_features(lnK, S, S_prev, P, P_prev, ds_stats, dp_stats, feat,
+                                             H, W, s_mean, s_scale, stream or None))
+
+
+def lbm2p_op_target(P_next, P, P_prev, dp_stats, tgt, H, W, stream=0):
+    _check(_lib_or_raise().lbm2p_op_target(P_next, P, P_prev, dp_stats, tgt, H, W, stream or None))
+
+
+def lbm2p_op_predict(P, P_prev, d, dp_stats, P_pred, H, W, stream=0):
+    _check(_lib_or_raise().lbm2p_op_predict(P, P_prev, d, dp_stats, P_pred, H, W, stream or None))
+
+
+def lbm2p_op_mse_grad(y0, tgt, g, loss, npix, c_out, stream=0):
+    _check(_lib_or_raise().lbm2p_op_mse_grad(y0, tgt, g, loss, npix, c_out, stream or None))
+
+
 FUSED_NONE, FUSED_STAGES, FUSED_STAGED_ROWS, FUSED_DIRECT = 0, 1, 2, 3
 
 
@@ -324,6 +385,12 @@ def _dp(a):
 
 def _fp(a):
     return None if a is None else a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+def _dev_fp(t):
+    """A float32 device tensor's address as a float pointer (shape and dtype checked by the
+    caller)."""
+    return None if t is None else C.cast(C.c_void_p(t.data_ptr()), C.POINTER(C.c_float))
 
 
 class _TorchMemory:
@@ -514,6 +581,22 @@ class Solver:
                     raise ValueError("out arrays must be C-contiguous float32 of shape (ny, nx)")
         lbm2p_fields(self.h, _fp(P), _fp(S), int(bool(mean_free_P)), 0)
         return P, S
+
+    def fields_device(self, P, S, mean_free_P=False):
+        """P and S of the current time level into float32 [ny, nx] contiguous device tensors
+        (either may be None); the copy is queued on the solver's stream."""
+        for t in (P, S):
+            if t is not None and (str(t.dtype) != "torch.float32" or not t.is_cuda or
+                                  tuple(t.shape) != (self.ny, self.nx) or not t.is_contiguous()):
+                raise ValueError("fields_device wants contiguous float32 (ny, nx) CUDA tensors")
+        lbm2p_fields(self.h, _dev_fp(P), _dev_fp(S), int(bool(mean_free_P)), 1)
+
+    def warm_start_device(self, P_guess):
+        """Start the next pressure solve from a float32 [ny, nx] device tensor."""
+        if (str(P_guess.dtype) != "torch.float32" or not P_guess.is_cuda or
+                tuple(P_guess.shape) != (self.ny, self.nx) or not P_guess.is_contiguous()):
+            raise ValueError("warm_start_device wants a contiguous float32 (ny, nx) CUDA tensor")
+        _check(_lib_or_raise().lbm2p_warm_start(self.h, _dev_fp(P_guess), 1), self.h)
 
     def velocity(self):
         ux = np.empty((self.ny, self.nx), np.float32)
