@@ -30,8 +30,9 @@
  *
  * Errors.  Every call returns an lbm2p_status; lbm2p_last_error(handle) (or
  * lbm2p_last_error(NULL) after a failed create) gives a one-line description.
- * LBM2P_ENOTCONVERGED still advances the state; LBM2P_ENONFINITE leaves the state as
- * the failing sweep produced it (the caller may restore a checkpoint).
+ * LBM2P_ENOTCONVERGED still advances the state.  LBM2P_ENONFINITE from lbm2p_step rolls
+ * the failing step back: the state after the call (lbm2p_get_state, the fields) is the state
+ * before that step, bit for bit, so the caller may fix its inputs and step again.
  */
 #ifndef LBM2P_H
 #define LBM2P_H
@@ -54,7 +55,8 @@ typedef enum {
     LBM2P_ENOMEM = 2,          /* device or host allocation failed */
     LBM2P_ECUDA = 3,           /* a CUDA call failed; the handle should be destroyed */
     LBM2P_ENOTCONVERGED = 4,   /* max_sub_iters reached before the residual met tol */
-    LBM2P_ENONFINITE = 5,      /* the pressure residual became NaN (e.g. NaN sources) */
+    LBM2P_ENONFINITE = 5,      /* the pressure residual became NaN (e.g. NaN sources); a
+                                  step that meets it is rolled back */
     LBM2P_ENOTIMPL = 6         /* requested option is not implemented by the library */
 } lbm2p_status;
 
@@ -211,11 +213,19 @@ lbm2p_status lbm2p_set_dirichlet(lbm2p *h, int side, const double *P_b, const do
  *     r_k = ||dP - mean(dP)||_2 / ||P^k - mean(P^k)||_2,   dP = P^k - P^{k-1},
  * and the iteration stops when r_k <= tol, or at max_sub_iters (ENOTCONVERGED).
  * replay: NULL, or nsteps sweep counts (>= 0) to run exactly instead.
- * stats: NULL or nsteps entries.  Returns the worst status over the steps. */
+ * stats: NULL or nsteps entries.  Returns the worst status over the steps.
+ * A step reads the state and writes spare buffers (a third set of pressure populations, a
+ * second set of R, 1/tau_f and the warm start's previous pressure), which become the state
+ * when the step ends.  When a residual check finds a value that is not a number the step
+ * stops: no saturation update runs, the state stays the one before the step, and the call
+ * returns LBM2P_ENONFINITE without running the remaining steps (a replayed count detects
+ * it only when it is >= 2, at the final check). */
 lbm2p_status lbm2p_step(lbm2p *h, int nsteps, const int *replay, lbm2p_step_stats *stats);
 
 /* Run exactly nsweeps pressure sweeps (Eq. 3-1) with the current tau_f and sources, no
-   stopping test; residual (may be NULL) receives r of the last sweep when nsweeps >= 2. */
+   stopping test; residual (may be NULL) receives r of the last sweep when nsweeps >= 2.
+   The populations after the call are those the sweeps produced, also when they are not
+   finite (ENONFINITE): no rollback here. */
 lbm2p_status lbm2p_pressure_sweeps(lbm2p *h, int nsweeps, double *residual);
 
 /* Darcy velocity u = -K lambda_t(S) grad P (Eq. 3-10b) of the current time level into

@@ -31,7 +31,7 @@ namespace {
 // nodes: rpt rows of a (1 << wshift)-wide row segment, so lattices narrower than kBlock
 // still fill the block.
 struct Member {
-    PressureArgs pa[2];          // sweep reading f buffer 0 / 1
+    PressureArgs pa[2];          // sweep from the current f buffer A into B / from B into A
     RefreshArgs ra[2];           // batch step parity 0 / 1
     SaturationArgs sa[2];
     RebaseArgs rb;
@@ -39,7 +39,7 @@ struct Member {
     float *shift;                // the handle's residual conditioning constants
     long long nnodes;
     int nx, ny;
-    int pf;                      // f buffer holding the state between steps
+    int pf;                      // which of pa reads the buffer holding the state (0)
     int every;                   // sweeps between mid-solve rebases
     int wshift, rpt, seg_x;      // segment width 2^wshift, rows per tile, segments per row
     int tile0, ntiles;           // range in the batch tile list
@@ -291,7 +291,7 @@ __global__ void __launch_bounds__(kBlock) kb_rebase(const Member *__restrict__ m
 
 struct lbm2p_batch {
     std::vector<lbm2p *> members;
-    std::vector<int> pf, pg0;            // buffer parities the graphs were built for
+    std::vector<int> pf, pg0, pr;        // member buffers the graphs were built for
     int count = 0, total = 0, body = 0, grid = 0, grid_check = 0;
     void *stream = nullptr;
     Member *d_mem = nullptr;
@@ -531,20 +531,25 @@ lbm2p_status lbm2p_batch_create(lbm2p_batch **out, lbm2p *const *members, int co
     for (int i = 0; i < count; ++i) {
         lbm2p *h = members[i];
         Member &M = hm[(size_t)i];
+        // the batch ping-pongs each member between its current f buffer A and the next one
+        // of the rotation, B (a loop body is an even number of sweeps, so a step ends in A),
+        // and updates R, 1/tau_f and P^{n-1} in place
+        const int A = h->cur_f, B = lbm2p_internal::fnext(A, 1);
+        M.pa[0] = lbm2p_internal::pressure_args(h, A, B, false);
+        M.pa[1] = lbm2p_internal::pressure_args(h, B, A, false);
         for (int q = 0; q < 2; ++q) {
-            M.pa[q] = lbm2p_internal::pressure_args(h, q);
             M.pa[q].partials = nullptr;
-            M.ra[q] = lbm2p_internal::refresh_args(h, h->cur_g ^ q);
-            M.sa[q] = lbm2p_internal::saturation_args(h, h->cur_f, h->cur_g ^ q);
+            M.ra[q] = lbm2p_internal::refresh_args(h, h->cur_g ^ q, true);
+            M.sa[q] = lbm2p_internal::saturation_args(h, A, h->cur_g ^ q, false);
         }
-        M.rb = lbm2p_internal::rebase_args(h, h->cur_f);
-        M.rm = lbm2p_internal::rebase_mid_args(h, h->cur_f);
+        M.rb = lbm2p_internal::rebase_args(h, A, false);
+        M.rm = lbm2p_internal::rebase_mid_args(h, A, false);
         M.every = h->rebase_every;
         M.shift = h->shift;
         M.nnodes = h->nnodes;
         M.nx = h->nx;
         M.ny = h->ny;
-        M.pf = h->cur_f;
+        M.pf = 0;                      // pa[0] reads A
         int w = 32;
         while (w < h->nx && w < kBlock)
             w *= 2;
@@ -559,6 +564,7 @@ lbm2p_status lbm2p_batch_create(lbm2p_batch **out, lbm2p *const *members, int co
         tile_member.insert(tile_member.end(), (size_t)M.ntiles, i);
         b->pf.push_back(h->cur_f);
         b->pg0.push_back(h->cur_g);
+        b->pr.push_back(h->cur_r);
     }
     b->total = total;
     int dev = 0, sms = 0, per = 0, perc = 0;
@@ -631,7 +637,8 @@ lbm2p_status lbm2p_batch_step(lbm2p_batch *b, int nsteps, const int *replay,
                              b->body, i, replay[i]);
     for (int m = 0; m < b->count; ++m) {
         const lbm2p *h = b->members[(size_t)m];
-        if (h->cur_f != b->pf[(size_t)m] || h->cur_g != (b->pg0[(size_t)m] ^ b->gstep))
+        if (h->cur_f != b->pf[(size_t)m] || h->cur_r != b->pr[(size_t)m] ||
+            h->cur_g != (b->pg0[(size_t)m] ^ b->gstep))
             return bfail(b, LBM2P_EINVAL,
                          "member %d was stepped outside the batch (buffer parity changed)", m);
     }

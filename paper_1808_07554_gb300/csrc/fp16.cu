@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(kBlock) k_widen(const __grid_constant__ HalfCo
 #pragma unroll
             for (int i = 0; i < 8; ++i)
                 a.n32w[i][o] = __half2float(a.n16[i][o]) * inv_s;
-            a.R[o] = a.Rh[o];
+            a.Rw[o] = a.Rh[o];
         }
     }
 }

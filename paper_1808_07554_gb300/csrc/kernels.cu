@@ -609,6 +609,13 @@ __global__ void k_loop_reset(LoopCtl *ctl)
     ctl->r = nan("");
 }
 
+// After the loop: the step goes on (saturation update, rebase) only when the last residual is
+// a number; otherwise the step's inputs stay as they were and the host reports ENONFINITE.
+__global__ void k_if_finite(const LoopCtl *ctl, cudaGraphConditionalHandle h)
+{
+    cudaGraphSetConditional(h, isnan(ctl->r) ? 0u : 1u);
+}
+
 // --------------------------------------------------------------------------------------
 // a1: stream g, S^n (Eq. 3-9b), 1/tau_f (Eq. 3-11a with D_p = K lambda_t(S))
 // --------------------------------------------------------------------------------------
@@ -1066,6 +1073,13 @@ cudaError_t node_loop_reset(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNo
 {
     void *args[] = {(void *)&ctl};
     return add_kernel(n, g, dep, (void *)k_loop_reset, 1, 1, args);
+}
+
+cudaError_t node_if_finite(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
+                           const LoopCtl *ctl, cudaGraphConditionalHandle h)
+{
+    void *args[] = {(void *)&ctl, (void *)&h};
+    return add_kernel(n, g, dep, (void *)k_if_finite, 1, 1, args);
 }
 
 cudaError_t node_refresh(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,

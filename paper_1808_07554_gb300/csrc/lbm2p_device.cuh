@@ -105,8 +105,10 @@ struct PressureArgs {
 
 struct RefreshArgs {        // stream g, S^n, 1/tau_f (and the warm start of the next solve)
     const float *gin[9];
-    float *R;                // warm start: R <- 2 R - Pstep, Pstep <- R  (Pstep NULL: none)
-    float *Pstep;
+    const float *Rin;        // reference pressure of the last step
+    float *Rout;             // that of the coming solve: Rin, or with the warm start
+    const float *Pstep_in;   // 2 Rin - Pstep_in (Pstep_out <- Rin); Pstep_in NULL: no warm
+    float *Pstep_out;        // start (Rout <- Rin, nothing when Rout is Rin)
     const float *K;
     const float *Fs;         // dense F~_s plane or nullptr
     float *inv_tau;
@@ -182,7 +184,8 @@ struct HalfConvertArgs {
     const float *n32[8];     // narrow: FP32 deviations read
     float *n32w[8];          // widen: FP32 deviations written (the same planes)
     __half *n16[8];          // FP16 populations, scaled by scale[0]
-    float *R;                // narrow reads it, widen writes it
+    float *R;                // narrow reads it
+    float *Rw;               // widen writes it (may be R)
     float *Rh;               // narrow writes it, widen reads it
     float *scale;            // [0] s, [1] 1/s, [2] max |n_i| (as float bits, for the next s)
     Geom g;
@@ -312,6 +315,9 @@ cudaError_t node_rebase_mid(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNo
                             const RebaseMidArgs &a, int grid);
 cudaError_t node_loop_reset(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
                             LoopCtl *ctl);
+// sets the condition of an IF node: 1 when the loop's last residual is a number
+cudaError_t node_if_finite(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
+                           const LoopCtl *ctl, cudaGraphConditionalHandle h);
 cudaError_t node_refresh(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
                          const RefreshArgs &a, int grid);
 cudaError_t node_saturation(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,

@@ -54,11 +54,18 @@ struct lbm2p {
                                // sweeps (a multiple of check_every)
     void *stream = nullptr;
     std::vector<lbm2p_internal::Alloc> allocs;
-    float *fbuf[2][8] = {};
+    // Pressure populations: three buffers.  A step's solve reads the buffer holding the state
+    // (cur_f) and ping-pongs between the other two, so the state it started from is intact
+    // until the step succeeds (ENONFINITE leaves every input of the step as it was).
+    float *fbuf[3][8] = {};
     float *gbuf[2][9] = {};
-    float *inv_tau = nullptr, *K = nullptr, *S = nullptr, *Pio = nullptr, *tmp = nullptr;
-    float *R = nullptr;                // reference pressure of the pressure populations
-    float *Pstep = nullptr;            // warm start: the node pressure of the previous step
+    float *K = nullptr, *S = nullptr, *Pio = nullptr, *tmp = nullptr;
+    // 1/tau_f, the reference pressure R of the pressure populations, and (warm start) the node
+    // pressure of the previous step: two buffers each, cur_r the current one.  A step's S
+    // refresh writes the other (the "work" buffer), which becomes current when the step ends.
+    float *inv_taub[2] = {};
+    float *Rb[2] = {};
+    float *Pstepb[2] = {};
     float *Fp = nullptr, *Fs = nullptr;
     float *Pb[4] = {}, *Sb[4] = {};
     double *partials = nullptr, *mean = nullptr;
@@ -66,30 +73,39 @@ struct lbm2p {
     lbm2p_dev::ResidualOut *res = nullptr;
     lbm2p_dev::ResidualOut *res_host = nullptr;   // pinned
     float *stage = nullptr;            // compact [ny][nx] device staging plane
-    int cur_f = 0, cur_g = 0;          // buffer holding the current post-collision state
+    int cur_f = 0, cur_g = 0;          // buffers holding the current post-collision state
+    int cur_r = 0;                     // current buffer of 1/tau_f, R and the previous P
     long long launches = 0, sweeps = 0;
     bool timing = false;
     cudaEvent_t ev_step0 = nullptr, ev_step1 = nullptr, ev_sw0 = nullptr, ev_sw1 = nullptr;
     // graph-resident sub-iteration (free-running solves when check_every is even and
-    // divides max_sub_iters): one graph per f parity for a bare solve, and one per
-    // (f parity, g parity) for a whole physical step
+    // divides max_sub_iters): one graph per (f buffer, R buffer) for a bare solve, and one per
+    // (f buffer, g buffer, R buffer) for a whole physical step
     bool graph_ok = false;
     lbm2p_dev::LoopCtl *ctl = nullptr;
     lbm2p_dev::LoopCtl *ctl_host = nullptr;       // pinned
-    cudaGraph_t solve_g[2] = {};
-    cudaGraphExec_t solve_x[2] = {};
-    cudaGraph_t step_g[2][2] = {};
-    cudaGraphExec_t step_x[2][2] = {};
+    cudaGraph_t solve_g[3][2] = {};
+    cudaGraphExec_t solve_x[3][2] = {};
+    cudaGraph_t step_g[3][2][2] = {};
+    cudaGraphExec_t step_x[3][2][2] = {};
     std::string autotune_log;          // one line per candidate timed at create
     std::string err;
 };
 
 
 namespace lbm2p_internal {
-// kernel argument blocks of h for f source parity src / g parity pg (runtime.cu)
-lbm2p_dev::PressureArgs pressure_args(lbm2p *h, int src);
-lbm2p_dev::RefreshArgs refresh_args(lbm2p *h, int pg);
-lbm2p_dev::SaturationArgs saturation_args(lbm2p *h, int pf, int pg);
-lbm2p_dev::RebaseArgs rebase_args(lbm2p *h, int pf);
-lbm2p_dev::RebaseMidArgs rebase_mid_args(lbm2p *h, int pf);
+// the f buffer k places after b in the rotation of three
+inline int fnext(int b, int k) { return (b + k) % 3; }
+// 1/tau_f, R and the previous step's P: the current buffers, or the work buffers of a step
+inline float *itau_of(const lbm2p *h, bool work) { return h->inv_taub[work ? 1 - h->cur_r : h->cur_r]; }
+inline float *R_of(const lbm2p *h, bool work) { return h->Rb[work ? 1 - h->cur_r : h->cur_r]; }
+inline float *Pstep_of(const lbm2p *h, bool work) { return h->Pstepb[work ? 1 - h->cur_r : h->cur_r]; }
+// kernel argument blocks of h (runtime.cu): sweeps from f buffer src into dst, the S refresh
+// of g buffer pg (in place: R, P^{n-1} and 1/tau_f overwritten; otherwise written into the
+// work buffers), saturation update and rebases of f buffer pf; `work`: use the work buffers
+lbm2p_dev::PressureArgs pressure_args(lbm2p *h, int src, int dst, bool work);
+lbm2p_dev::RefreshArgs refresh_args(lbm2p *h, int pg, bool in_place);
+lbm2p_dev::SaturationArgs saturation_args(lbm2p *h, int pf, int pg, bool work);
+lbm2p_dev::RebaseArgs rebase_args(lbm2p *h, int pf, bool work);
+lbm2p_dev::RebaseMidArgs rebase_mid_args(lbm2p *h, int pf, bool work);
 }  // namespace lbm2p_internal

@@ -297,12 +297,15 @@ struct ResAcc {
 // per-node bodies shared by the single-lattice kernels and the batched kernels
 // --------------------------------------------------------------------------------------
 // Warm start of a solve: the equilibrium part of f_i = n_i + w_i R moves with R to the
-// pressure extrapolated in time, R' = R + (R - P^{n-1}); n_i (the rest) is kept.
-__device__ __forceinline__ void extrapolate_node(float *R, float *Pstep, int o)
+// pressure extrapolated in time, R' = R + (R - P^{n-1}); n_i (the rest) is kept.  The inputs
+// may be the outputs (in place).
+__device__ __forceinline__ void extrapolate_node(const float *Rin, float *Rout,
+                                                 const float *Pin, float *Pout, int o)
 {
-    const float r = R[o];
-    R[o] = r + (r - Pstep[o]);
-    Pstep[o] = r;
+    const float r = Rin[o];
+    const float pv = Pin[o];
+    Rout[o] = r + (r - pv);
+    Pout[o] = r;
 }
 
 // a1: S^n (Eq. 3-9b) from the pulled g and 1/tau_f (Eq. 3-11a with D_p = K lambda_t(S)); with
@@ -317,8 +320,10 @@ __device__ __forceinline__ void refresh_node(const RefreshArgs &a, int x, int y,
     float lw, lt;
     mobility(a.m, S, lw, lt);
     a.inv_tau[o] = 1.0f / (0.5f + a.m.s3 * a.K[o] * lt);
-    if (a.Pstep)
-        extrapolate_node(a.R, a.Pstep, o);
+    if (a.Pstep_in)
+        extrapolate_node(a.Rin, a.Rout, a.Pstep_in, a.Pstep_out, o);
+    else if (a.Rout != a.Rin)
+        a.Rout[o] = a.Rin[o];
 }
 
 // a4 + a5: local grad P (Eq. 3-10a), then the saturation collision (Eq. 3-2); also stores

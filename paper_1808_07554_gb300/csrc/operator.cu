@@ -159,33 +159,63 @@ struct ConvArgs {
     int *err;
 };
 
+// ---- convolution on staged rows ----------------------------------------------------------
+// A tile is 128 consecutive pixels of one image row (x0 .. x0 + 127, the last tile of a row
+// ragged).  Its three input rows y - 1 .. y + 1, pixels x0 - 1 .. x0 + 128, are copied once into
+// shared memory as channel-chunk planes: chunk c (channels 8 c .. 8 c + 7) of staged row r is
+// an array of 130 pixels x 16 bytes.  In that layout the A operand of tap (dy, dx) and K-half j
+// is the K-major core-matrix matrix that starts at row dy + 1, chunk 2 j, pixel dx + 1: a shift
+// by one pixel is a shift of the descriptor's start address by 16 bytes, so all 9 x C_in / 16
+// MMAs of a tile read the same staged rows.  Two stage buffers: the rows of the next tile are
+// copied while the tensor core works on the current one.
+constexpr int kRowPix = 130;                        // staged pixels per row
+constexpr uint32_t kChunkBytes = kRowPix * 16;      // one channel chunk of a staged row
+
 template <int CIN, int COUT>
-constexpr size_t conv_smem_bytes()
+constexpr size_t conv_rows_smem_bytes()
 {
-    // weights of every K-step, the A stages, the stage barriers, the tensor-memory slot
-    return (size_t)(9 * CIN / 16) * COUT * 32 + kStages * kABytes + kStages * 8 + 16 + 128;
+    return (size_t)(9 * CIN / 16) * COUT * 32 + 2 * (size_t)3 * (CIN / 8) * kChunkBytes + 8 + 16 + 128;
 }
 
 template <int CIN, int COUT>
-__global__ void __launch_bounds__(kThreads) k_conv3x3(const ConvArgs a)
+__device__ __forceinline__ void stage_rows(const ConvArgs &a, unsigned char *buf, long long tile,
+                                           int tiles_x, int tid)
 {
-    constexpr int KS = 9 * CIN / 16;                  // K-steps of 16
-    constexpr uint32_t kBBytes = COUT * 16 * 2;       // one K-step of weights
+    constexpr int CH = CIN / 8;
+    const int img = (int)(tile / ((long long)a.H * tiles_x));
+    const int rem = (int)(tile - (long long)img * a.H * tiles_x);
+    const int y = rem / tiles_x, x0 = (rem - y * tiles_x) * 128;
+    for (int i = tid; i < 3 * kRowPix * CH; i += kThreads) {
+        const int c = i % CH, px = (i / CH) % kRowPix, r = i / (CH * kRowPix);
+        const int yy = y + r - 1, xx = x0 + px - 1;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (yy >= 0 && yy < a.H && xx >= 0 && xx < a.W)
+            v = *reinterpret_cast<const uint4 *>(a.x + (((size_t)img * a.H + yy) * a.W + xx) * CIN + 8 * c);
+        *reinterpret_cast<uint4 *>(buf + (r * CH + c) * kChunkBytes + px * 16) = v;
+    }
+}
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(kThreads) k_conv3x3_rows(const ConvArgs a)
+{
+    constexpr int CH = CIN / 8;
+    constexpr int KH = CIN / 16;                      // K-halves of 16 channels per tap
+    constexpr int KS = 9 * KH;
+    constexpr uint32_t kBBytes = COUT * 16 * 2;
+    constexpr uint32_t kStageBytes = 3 * CH * kChunkBytes;
     constexpr uint32_t IDESC = idesc_bf16(128, COUT);
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
     unsigned char *wsm = smem;
-    unsigned char *asm_ = smem + KS * kBBytes;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(asm_ + kStages * kABytes);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + kStages);
+    unsigned char *stg = smem + KS * kBBytes;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(stg + 2 * kStageBytes);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    // weights into the per-K-step K-major layout: element (n, k) of K-step s at
-    // s * kBBytes + (k / 8) * (COUT * 16) + n * 16 + (k % 8) * 2, from w[t][n][16 j + k]
     for (int i = tid; i < KS * COUT * 2; i += kThreads) {
         const int s = i / (COUT * 2), rem = i - s * (COUT * 2);
         const int kc = rem / COUT, n = rem - kc * COUT;
-        const int t = s / (CIN / 16), j = s - t * (CIN / 16);
+        const int t = s / KH, j = s - t * KH;
         const uint4 v = *reinterpret_cast<const uint4 *>(a.w + ((size_t)(t * COUT + n) * CIN + 16 * j + 8 * kc));
         *reinterpret_cast<uint4 *>(wsm + s * kBBytes + kc * (COUT * 16) + n * 16) = v;
     }
@@ -194,71 +224,61 @@ __global__ void __launch_bounds__(kThreads) k_conv3x3(const ConvArgs a)
         tmem_relinquish();
     }
     if (tid == 0) {
-        for (int s = 0; s < kStages; ++s)
-            bar_init(bars + s, 1);
+        bar_init(bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    const int tiles_x = (a.W + 127) / 128;
+    const long long tiles = (long long)a.nimg * a.H * tiles_x;
+    long long tile = blockIdx.x;
+    if (tile < tiles)
+        stage_rows<CIN, COUT>(a, stg, tile, tiles_x, tid);
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
-
-    const long long hw = (long long)a.H * a.W;
-    const long long npix = (long long)a.nimg * hw;
-    const long long tiles = (npix + 127) / 128;
-    const int m = tid & 127, kc = tid >> 7;           // this thread's A row and K half
-    unsigned gstep = 0;
+    unsigned phase = 0;
+    int b = 0;
     bool ok = true;
-    for (long long tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
-        const long long p = tile * 128 + m;
-        int img = 0, y = 0, x = 0;
-        if (p < npix) {
-            img = (int)(p / hw);
-            const int r = (int)(p - (long long)img * hw);
-            y = r / a.W;
-            x = r - y * a.W;
-        }
-        for (int s = 0; s < KS; ++s, ++gstep) {
-            const int st = (int)(gstep % kStages);
-            if (gstep >= (unsigned)kStages &&
-                !wait_bounded(bars + st, ((gstep / kStages) + 1u) & 1u)) {
-                ok = false;
-                break;
+    for (; tile < tiles; tile += gridDim.x, b ^= 1) {
+        unsigned char *cur = stg + b * kStageBytes;
+        if (tid == 0) {
+            tc_fence_after();
+            int s = 0;
+#pragma unroll
+            for (int t = 0; t < 9; ++t) {
+#pragma unroll
+                for (int j = 0; j < KH; ++j, ++s) {
+                    const uint32_t start = smem_u32(cur + ((t / 3) * CH + 2 * j) * kChunkBytes +
+                                                    (t % 3) * 16);
+                    const uint64_t ad = sdesc(start, kChunkBytes, 128);
+                    const uint64_t bd = sdesc(smem_u32(wsm + s * kBBytes), COUT * 16, 128);
+                    umma_bf16(tmem, ad, bd, IDESC, s > 0 ? 1u : 0u);
+                }
             }
-            const int t = s / (CIN / 16), j = s - t * (CIN / 16);
-            const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (p < npix && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W)
-                v = *reinterpret_cast<const uint4 *>(
-                    a.x + (((size_t)img * a.H + yy) * a.W + xx) * CIN + 16 * j + 8 * kc);
-            unsigned char *stage = asm_ + st * kABytes;
-            *reinterpret_cast<uint4 *>(stage + kc * 2048 + m * 16) = v;
-            fence_async_smem();
-            __syncthreads();
-            if (tid == 0) {
-                tc_fence_after();
-                const uint64_t ad = sdesc(smem_u32(stage), 2048, 128);
-                const uint64_t bd = sdesc(smem_u32(wsm + s * kBBytes), COUT * 16, 128);
-                umma_bf16(tmem, ad, bd, IDESC, s > 0 ? 1u : 0u);
-                umma_commit(bars + st);
-            }
+            umma_commit(bar);
         }
-        if (!ok)
-            break;
-        const unsigned last = gstep - 1;
-        if (!wait_bounded(bars + last % kStages, (last / kStages) & 1u)) {
+        // the next tile's rows into the other buffer while the tensor core works
+        const long long next = tile + gridDim.x;
+        if (next < tiles)
+            stage_rows<CIN, COUT>(a, stg + (b ^ 1) * kStageBytes, next, tiles_x, tid);
+        fence_async_smem();
+        if (!wait_bounded(bar, phase)) {
             ok = false;
             break;
         }
+        phase ^= 1u;
         tc_fence_after();
-        // epilogue: warp w reads lanes 32 (w % 4) .. (its pixels), columns 16 (w / 4) ..
+        const int img = (int)(tile / ((long long)a.H * tiles_x));
+        const int rem = (int)(tile - (long long)img * a.H * tiles_x);
+        const int y = rem / tiles_x, x0 = (rem - y * tiles_x) * 128;
         const int cb = 16 * (warp >> 2);
         if (cb < COUT) {
             float v[16];
             tmem_ld16(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)cb, v);
-            const long long q = tile * 128 + 32 * (warp & 3) + lane;
-            if (q < npix) {
+            const int x = x0 + 32 * (warp & 3) + lane;
+            if (x < a.W) {
+                const long long q = ((long long)img * a.H + y) * a.W + x;
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
                     float u = v[i] + (a.bias ? a.bias[cb + i] : 0.0f);
@@ -286,15 +306,14 @@ __global__ void __launch_bounds__(kThreads) k_conv3x3(const ConvArgs a)
                     a.y0[q] = v[0];
             }
         }
+        // the accumulator and the buffer just read are free once every thread is past here
         tc_fence_before();
         __syncthreads();
     }
     if (!ok) {
         if (tid == 0)
             atomicExch(a.err, 1);
-        // MMAs of this CTA still in flight: a bounded wait for the most recent commit
-        if (gstep > 0)
-            wait_bounded(bars + (gstep - 1) % kStages, ((gstep - 1) / kStages) & 1u);
+        wait_bounded(bar, phase);
     }
     tc_fence_before();
     __syncthreads();
@@ -618,22 +637,23 @@ int sm_count()
 template <int CIN, int COUT>
 cudaError_t launch_conv(const ConvArgs &a, cudaStream_t s)
 {
-    const size_t smem = conv_smem_bytes<CIN, COUT>();
-    cudaError_t e = cudaFuncSetAttribute(k_conv3x3<CIN, COUT>,
+    const size_t smem = conv_rows_smem_bytes<CIN, COUT>();
+    cudaError_t e = cudaFuncSetAttribute(k_conv3x3_rows<CIN, COUT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv3x3<CIN, COUT>, kThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv3x3_rows<CIN, COUT>, kThreads,
+                                                      smem);
     if (e != cudaSuccess)
         return e;
     // tensor memory: 512 columns per SM, kTmemCols per resident CTA
     per_sm = per_sm < 1 ? 1 : (per_sm > 512 / (int)kTmemCols ? 512 / (int)kTmemCols : per_sm);
-    const long long tiles = ((long long)a.nimg * a.H * a.W + 127) / 128;
+    const long long tiles = (long long)a.nimg * a.H * ((a.W + 127) / 128);
     long long grid = (long long)sm_count() * per_sm;
     if (grid > tiles)
         grid = tiles;
-    k_conv3x3<CIN, COUT><<<(unsigned)grid, kThreads, smem, s>>>(a);
+    k_conv3x3_rows<CIN, COUT><<<(unsigned)grid, kThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 

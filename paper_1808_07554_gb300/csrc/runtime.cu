@@ -27,16 +27,16 @@ using lbm2p_internal::Alloc;
 
 namespace lbm2p_internal {
 
-// ---- kernel argument blocks for the current ping-pong state -----------------------------
-PressureArgs pressure_args(lbm2p *h, int src)
+// ---- kernel argument blocks --------------------------------------------------------------
+PressureArgs pressure_args(lbm2p *h, int src, int dst, bool work)
 {
     PressureArgs a{};
     for (int i = 0; i < 8; ++i) {
         a.fin[i] = h->fbuf[src][i];
-        a.fout[i] = h->fbuf[1 - src][i];
+        a.fout[i] = h->fbuf[dst][i];
     }
-    a.R = h->R;
-    a.inv_tau = h->inv_tau;
+    a.R = R_of(h, work);
+    a.inv_tau = itau_of(h, work);
     a.Fp = h->Fp;
     a.Pio = h->Pio;
     a.partials = h->partials;
@@ -48,16 +48,18 @@ PressureArgs pressure_args(lbm2p *h, int src)
     return a;
 }
 
-RefreshArgs refresh_args(lbm2p *h, int pg)
+RefreshArgs refresh_args(lbm2p *h, int pg, bool in_place)
 {
     RefreshArgs a{};
     for (int i = 0; i < 9; ++i)
         a.gin[i] = h->gbuf[pg][i];
-    a.R = h->R;
-    a.Pstep = h->p.warm_start ? h->Pstep : nullptr;
+    a.Rin = R_of(h, false);
+    a.Rout = R_of(h, !in_place);
+    a.Pstep_in = h->p.warm_start ? Pstep_of(h, false) : nullptr;
+    a.Pstep_out = h->p.warm_start ? Pstep_of(h, !in_place) : nullptr;
     a.K = h->K;
     a.Fs = h->Fs;
-    a.inv_tau = h->inv_tau;
+    a.inv_tau = itau_of(h, !in_place);
     for (int s = 0; s < 4; ++s)
         a.Sb[s] = h->Sb[s];
     a.g = h->geom;
@@ -66,19 +68,19 @@ RefreshArgs refresh_args(lbm2p *h, int pg)
     return a;
 }
 
-SaturationArgs saturation_args(lbm2p *h, int pf, int pg)
+SaturationArgs saturation_args(lbm2p *h, int pf, int pg, bool work)
 {
     SaturationArgs a{};
     for (int i = 0; i < 8; ++i)
         a.fin[i] = h->fbuf[pf][i];
-    a.R = h->R;
+    a.R = R_of(h, work);
     a.Pnew = h->Pio;
     for (int i = 0; i < 9; ++i) {
         a.gin[i] = h->gbuf[pg][i];
         a.gout[i] = h->gbuf[1 - pg][i];
     }
     a.K = h->K;
-    a.inv_tau = h->inv_tau;
+    a.inv_tau = itau_of(h, work);
     a.Fs = h->Fs;
     a.S = h->S;
     for (int s = 0; s < 4; ++s) {
@@ -92,24 +94,24 @@ SaturationArgs saturation_args(lbm2p *h, int pf, int pg)
 }
 
 
-RebaseMidArgs rebase_mid_args(lbm2p *h, int pf)
+RebaseMidArgs rebase_mid_args(lbm2p *h, int pf, bool work)
 {
     RebaseMidArgs a{};
     for (int i = 0; i < 8; ++i)
         a.n[i] = h->fbuf[pf][i];
-    a.R = h->R;
+    a.R = R_of(h, work);
     a.Fp = h->Fp;
     a.g = h->geom;
     a.w = h->wells;
     return a;
 }
 
-RebaseArgs rebase_args(lbm2p *h, int pf)
+RebaseArgs rebase_args(lbm2p *h, int pf, bool work)
 {
     RebaseArgs a{};
     for (int i = 0; i < 8; ++i)
         a.n[i] = h->fbuf[pf][i];
-    a.R = h->R;
+    a.R = R_of(h, work);
     a.Pnew = h->Pio;
     a.g = h->geom;
     return a;
@@ -124,6 +126,10 @@ using lbm2p_internal::refresh_args;
 using lbm2p_internal::saturation_args;
 using lbm2p_internal::rebase_args;
 using lbm2p_internal::rebase_mid_args;
+using lbm2p_internal::fnext;
+using lbm2p_internal::itau_of;
+using lbm2p_internal::R_of;
+using lbm2p_internal::Pstep_of;
 
 lbm2p_status fail(lbm2p *h, lbm2p_status st, const char *fmt, ...)
 {
@@ -184,22 +190,23 @@ void free_all(lbm2p *h)
         else if (!h->p.alloc)
             cudaFree(a.ptr);
     }
-    for (int a = 0; a < 2; ++a) {
-        if (h->solve_x[a])
-            cudaGraphExecDestroy(h->solve_x[a]);
-        if (h->solve_g[a])
-            cudaGraphDestroy(h->solve_g[a]);
-        h->solve_x[a] = nullptr;
-        h->solve_g[a] = nullptr;
-        for (int b = 0; b < 2; ++b) {
-            if (h->step_x[a][b])
-                cudaGraphExecDestroy(h->step_x[a][b]);
-            if (h->step_g[a][b])
-                cudaGraphDestroy(h->step_g[a][b]);
-            h->step_x[a][b] = nullptr;
-            h->step_g[a][b] = nullptr;
+    for (int a = 0; a < 3; ++a)
+        for (int r = 0; r < 2; ++r) {
+            if (h->solve_x[a][r])
+                cudaGraphExecDestroy(h->solve_x[a][r]);
+            if (h->solve_g[a][r])
+                cudaGraphDestroy(h->solve_g[a][r]);
+            h->solve_x[a][r] = nullptr;
+            h->solve_g[a][r] = nullptr;
+            for (int b = 0; b < 2; ++b) {
+                if (h->step_x[a][b][r])
+                    cudaGraphExecDestroy(h->step_x[a][b][r]);
+                if (h->step_g[a][b][r])
+                    cudaGraphDestroy(h->step_g[a][b][r]);
+                h->step_x[a][b][r] = nullptr;
+                h->step_g[a][b][r] = nullptr;
+            }
         }
-    }
     h->allocs.clear();
     if (h->res_host)
         cudaFreeHost(h->res_host);
@@ -282,113 +289,151 @@ int sweep_nparts(const lbm2p *h)
 }
 
 // ---- graph-resident sub-iteration ----------------------------------------------------------
-// Appends to G: reset(ctl) -> event(sw0) -> WHILE{ m sweeps from f parity pf, the last one
-// with residual partials; finalize sets the condition } -> event(sw1).  m is even, so the
-// loop ends on parity pf.  *last receives the final node.
-lbm2p_status add_loop(lbm2p *h, cudaGraph_t G, const cudaGraphNode_t *dep, int pf,
+// Appends to G: reset(ctl) -> event(sw0) -> the first check period -> WHILE{ further check
+// periods } -> event(sw1).  A check period is m = check_every sweeps (single or fused
+// launches), the last with residual partials, then the finalize kernel (it counts the sweeps,
+// keeps r, decides whether the WHILE goes on and whether R first moves to the current P:
+// IF{mid-solve rebase}).  The first period reads f buffer pin and writes the next buffer of the
+// rotation, then ping-pongs between the two buffers other than pin and ends on the third; every
+// later period starts and ends there (m, or m / T fused launches, is even).  So the state the
+// solve starts from is only read, and the solve ends in buffer fnext(pin, 2).  `work`: R and
+// 1/tau_f of the work buffers (a step's solve) or the current ones (a bare solve).
+lbm2p_status add_loop(lbm2p *h, cudaGraph_t G, const cudaGraphNode_t *dep, int pin, bool work,
                       cudaGraphNode_t *last)
 {
     const int m = h->p.check_every;
-    cudaGraphNode_t reset, ev0, wn, ev1;
+    const int b1 = fnext(pin, 1), b2 = fnext(pin, 2);
+    auto dst_of = [&](int src) { return src == b1 ? b2 : b1; };
+    cudaGraphNode_t reset, ev0, first_end, wn, ev1;
     CUDA_TRY(h, lbm2p_launch::node_loop_reset(&reset, G, dep, h->ctl));
     CUDA_TRY(h, cudaGraphAddEventRecordNode(&ev0, G, &reset, 1, h->ev_sw0));
     cudaGraphConditionalHandle hd;
     CUDA_TRY(h, cudaGraphConditionalHandleCreate(&hd, G, 1, cudaGraphCondAssignDefault));
+    // one check period into graph g after node `after` (nullptr: none), its first launch
+    // reading buffer `first`, the mid-solve rebase conditioned on handle hr
+    auto period = [&](cudaGraph_t g, cudaGraphNode_t after, int first,
+                      cudaGraphConditionalHandle hr, cudaGraphNode_t *out) -> lbm2p_status {
+        cudaGraphNode_t prev = after;
+        int src = first;
+        int nparts = sweep_nparts(h);
+        if (h->tb_T_graph > 1) {
+            const int T = h->tb_T_graph;
+            for (int kk = T; kk <= m; kk += T) {
+                cudaGraphNode_t n;
+                PressureArgs a = pressure_args(h, src, dst_of(src), work);
+                if (h->tb_kind == 2)
+                    CUDA_TRY(h, lbm2p_launch::node_pressure_pair_direct(&n, g, prev ? &prev : nullptr,
+                                                                        a, kk == m, h->tb_W / 30,
+                                                                        h->tb_H, h->tb_grid));
+                else if (h->tb_kind == 1)
+                    CUDA_TRY(h, lbm2p_launch::node_pressure_rows2(&n, g, prev ? &prev : nullptr, a,
+                                                                  kk == m, h->tb_W / 30, h->tb_slots,
+                                                                  h->tb_H, h->tb_grid));
+                else
+                    CUDA_TRY(h, lbm2p_launch::node_pressure_fused(&n, g, prev ? &prev : nullptr, a,
+                                                                  T, h->tb_W, h->tb_H, kk == m,
+                                                                  h->tb_grid));
+                prev = n;
+                src = dst_of(src);
+            }
+            nparts = h->tb_grid;
+        } else {
+            for (int kk = 1; kk <= m; ++kk) {
+                cudaGraphNode_t n;
+                PressureArgs a = pressure_args(h, src, dst_of(src), work);
+                CUDA_TRY(h, add_sweep_node(h, &n, g, prev ? &prev : nullptr, a, kk == m,
+                                           kk == m - 1));
+                prev = n;
+                src = dst_of(src);
+            }
+        }
+        // finalize decides whether to continue, and whether R moves to the current P first
+        cudaGraphNode_t fin, ifn, rb;
+        CUDA_TRY(h, lbm2p_launch::node_finalize_loop(&fin, g, &prev, h->partials, nparts,
+                                                     h->nnodes, h->shift, h->res, h->ctl, hd, hr));
+        cudaGraphNodeParams ip{};
+        ip.type = cudaGraphNodeTypeConditional;
+        ip.conditional.handle = hr;
+        ip.conditional.type = cudaGraphCondTypeIf;
+        ip.conditional.size = 1;
+        CUDA_TRY(h, cudaGraphAddNode(&ifn, g, &fin, nullptr, 1, &ip));
+        CUDA_TRY(h, lbm2p_launch::node_rebase_mid(&rb, ip.conditional.phGraph_out[0], nullptr,
+                                                  rebase_mid_args(h, b2, work), h->grid));
+        *out = ifn;
+        return LBM2P_OK;
+    };
+    cudaGraphConditionalHandle hr0;
+    CUDA_TRY(h, cudaGraphConditionalHandleCreate(&hr0, G, 0, 0));
+    lbm2p_status e = period(G, ev0, pin, hr0, &first_end);
+    if (e != LBM2P_OK)
+        return e;
     cudaGraphNodeParams cp{};
     cp.type = cudaGraphNodeTypeConditional;
     cp.conditional.handle = hd;
     cp.conditional.type = cudaGraphCondTypeWhile;
     cp.conditional.size = 1;
-    CUDA_TRY(h, cudaGraphAddNode(&wn, G, &ev0, nullptr, 1, &cp));
+    CUDA_TRY(h, cudaGraphAddNode(&wn, G, &first_end, nullptr, 1, &cp));
     cudaGraph_t body = cp.conditional.phGraph_out[0];
-    cudaGraphNode_t prev = nullptr;
-    int src = pf;
-    int nparts = sweep_nparts(h);
-    if (h->tb_T_graph > 1) {
-        const int T = h->tb_T_graph;
-        for (int kk = T; kk <= m; kk += T) {
-            cudaGraphNode_t n;
-            PressureArgs a = pressure_args(h, src);
-            if (h->tb_kind == 2)
-                CUDA_TRY(h, lbm2p_launch::node_pressure_pair_direct(&n, body, prev ? &prev : nullptr,
-                                                                    a, kk == m, h->tb_W / 30,
-                                                                    h->tb_H, h->tb_grid));
-            else if (h->tb_kind == 1)
-                CUDA_TRY(h, lbm2p_launch::node_pressure_rows2(&n, body, prev ? &prev : nullptr, a,
-                                                              kk == m, h->tb_W / 30, h->tb_slots,
-                                                              h->tb_H, h->tb_grid));
-            else
-                CUDA_TRY(h, lbm2p_launch::node_pressure_fused(&n, body, prev ? &prev : nullptr, a,
-                                                              T, h->tb_W, h->tb_H, kk == m,
-                                                              h->tb_grid));
-            prev = n;
-            src = 1 - src;
-        }
-        nparts = h->tb_grid;
-    } else {
-        for (int kk = 1; kk <= m; ++kk) {
-            cudaGraphNode_t n;
-            PressureArgs a = pressure_args(h, src);
-            CUDA_TRY(h, add_sweep_node(h, &n, body, prev ? &prev : nullptr, a, kk == m,
-                                       kk == m - 1));
-            prev = n;
-            src = 1 - src;
-        }
-    }
-    // finalize decides whether to continue, and whether R moves to the current P first
-    cudaGraphNode_t fin, ifn, rb;
     cudaGraphConditionalHandle hr;
     CUDA_TRY(h, cudaGraphConditionalHandleCreate(&hr, body, 0, 0));
-    CUDA_TRY(h, lbm2p_launch::node_finalize_loop(&fin, body, &prev, h->partials, nparts,
-                                                 h->nnodes, h->shift, h->res, h->ctl, hd, hr));
-    cudaGraphNodeParams ip{};
-    ip.type = cudaGraphNodeTypeConditional;
-    ip.conditional.handle = hr;
-    ip.conditional.type = cudaGraphCondTypeIf;
-    ip.conditional.size = 1;
-    CUDA_TRY(h, cudaGraphAddNode(&ifn, body, &fin, nullptr, 1, &ip));
-    CUDA_TRY(h, lbm2p_launch::node_rebase_mid(&rb, ip.conditional.phGraph_out[0], nullptr,
-                                              rebase_mid_args(h, pf), h->grid));
+    cudaGraphNode_t body_end;
+    if ((e = period(body, nullptr, b2, hr, &body_end)) != LBM2P_OK)
+        return e;
     CUDA_TRY(h, cudaGraphAddEventRecordNode(&ev1, G, &wn, 1, h->ev_sw1));
     *last = ev1;
     return LBM2P_OK;
 }
 
-lbm2p_status solve_graph(lbm2p *h, int pf, cudaGraphExec_t *out)
+// a bare solve (current R and 1/tau_f) from f buffer pin; it ends in fnext(pin, 2)
+lbm2p_status solve_graph(lbm2p *h, int pin, cudaGraphExec_t *out)
 {
-    if (!h->solve_x[pf]) {
+    const int r = h->cur_r;
+    if (!h->solve_x[pin][r]) {
         cudaGraph_t G;
         CUDA_TRY(h, cudaGraphCreate(&G, 0));
-        h->solve_g[pf] = G;
+        h->solve_g[pin][r] = G;
         cudaGraphNode_t last;
-        lbm2p_status e = add_loop(h, G, nullptr, pf, &last);
+        lbm2p_status e = add_loop(h, G, nullptr, pin, false, &last);
         if (e != LBM2P_OK)
             return e;
-        CUDA_TRY(h, cudaGraphInstantiate(&h->solve_x[pf], G, 0));
+        CUDA_TRY(h, cudaGraphInstantiate(&h->solve_x[pin][r], G, 0));
     }
-    *out = h->solve_x[pf];
+    *out = h->solve_x[pin][r];
     return LBM2P_OK;
 }
 
-// one physical step: refresh -> loop -> saturation
-lbm2p_status step_graph(lbm2p *h, int pf, int pg, cudaGraphExec_t *out)
+// one physical step: refresh (into the work buffers) -> loop -> IF{the residual is a number:
+// saturation update -> rebase}; the step's inputs (f buffer pin, g buffer pg, the current R,
+// 1/tau_f and P^{n-1}) are only read, so a step that fails leaves them as they were
+lbm2p_status step_graph(lbm2p *h, int pin, int pg, cudaGraphExec_t *out)
 {
-    if (!h->step_x[pf][pg]) {
+    const int r = h->cur_r;
+    if (!h->step_x[pin][pg][r]) {
         cudaGraph_t G;
         CUDA_TRY(h, cudaGraphCreate(&G, 0));
-        h->step_g[pf][pg] = G;
-        cudaGraphNode_t nr, last, ns;
-        CUDA_TRY(h, lbm2p_launch::node_refresh(&nr, G, nullptr, refresh_args(h, pg), h->grid));
-        lbm2p_status e = add_loop(h, G, &nr, pf, &last);
+        h->step_g[pin][pg][r] = G;
+        cudaGraphNode_t nr, last, nf, ifn, ns, nb;
+        CUDA_TRY(h, lbm2p_launch::node_refresh(&nr, G, nullptr, refresh_args(h, pg, false), h->grid));
+        lbm2p_status e = add_loop(h, G, &nr, pin, true, &last);
         if (e != LBM2P_OK)
             return e;
-        CUDA_TRY(h, lbm2p_launch::node_saturation(&ns, G, &last, saturation_args(h, pf, pg),
-                                                  h->grid));
-        cudaGraphNode_t nb;
-        CUDA_TRY(h, lbm2p_launch::node_rebase(&nb, G, &ns, rebase_args(h, pf), h->grid));
-        CUDA_TRY(h, cudaGraphInstantiate(&h->step_x[pf][pg], G, 0));
+        cudaGraphConditionalHandle hok;
+        CUDA_TRY(h, cudaGraphConditionalHandleCreate(&hok, G, 0, 0));
+        CUDA_TRY(h, lbm2p_launch::node_if_finite(&nf, G, &last, h->ctl, hok));
+        cudaGraphNodeParams ip{};
+        ip.type = cudaGraphNodeTypeConditional;
+        ip.conditional.handle = hok;
+        ip.conditional.type = cudaGraphCondTypeIf;
+        ip.conditional.size = 1;
+        CUDA_TRY(h, cudaGraphAddNode(&ifn, G, &nf, nullptr, 1, &ip));
+        cudaGraph_t tail = ip.conditional.phGraph_out[0];
+        const int pout = fnext(pin, 2);
+        CUDA_TRY(h, lbm2p_launch::node_saturation(&ns, tail, nullptr,
+                                                  saturation_args(h, pout, pg, true), h->grid));
+        CUDA_TRY(h, lbm2p_launch::node_rebase(&nb, tail, &ns, rebase_args(h, pout, true), h->grid));
+        CUDA_TRY(h, cudaGraphInstantiate(&h->step_x[pin][pg][r], G, 0));
     }
-    *out = h->step_x[pf][pg];
+    *out = h->step_x[pin][pg][r];
     return LBM2P_OK;
 }
 
@@ -426,23 +471,29 @@ lbm2p_status loop_status(lbm2p *h, int k, double r)
 
 // ---- the pressure sub-iteration (Sec. 3) ------------------------------------------------
 // replay >= 0: exactly that many sweeps; replay < 0: until r <= tol at a check or the cap.
-lbm2p_status pressure_solve_h(lbm2p *h, int replay, int *k_out, double *r_out, float *ms_out);
+lbm2p_status pressure_solve_h(lbm2p *h, int replay, bool work, int *k_out, double *r_out,
+                             float *ms_out, int *pout);
 
-// The sub-iteration with FP16 storage (fp16.cu): narrow the FP32 state, sweep on FP16 with
-// the same stopping rule and replay semantics as pressure_solve, widen the result.
-lbm2p_status pressure_solve_h(lbm2p *h, int replay, int *k_out, double *r_out, float *ms_out)
+// The sub-iteration with FP16 storage (fp16.cu): narrow the FP32 state of f buffer cur_f,
+// sweep on FP16 with the same stopping rule and replay semantics as pressure_solve, widen the
+// result into the next f buffer of the rotation (*pout), so the state it started from is only
+// read.  `work`: R and 1/tau_f of the work buffers (a step's solve) or the current ones.
+lbm2p_status pressure_solve_h(lbm2p *h, int replay, bool work, int *k_out, double *r_out,
+                             float *ms_out, int *pout)
 {
     cudaStream_t st = (cudaStream_t)h->stream;
     const int m = h->p.check_every;
     const int cap = h->p.max_sub_iters;
+    const int pin = h->cur_f, pw = fnext(pin, 1);
     auto convert_args = [&](int hb) {
         HalfConvertArgs a{};
         for (int i = 0; i < 8; ++i) {
-            a.n32[i] = h->fbuf[h->cur_f][i];
-            a.n32w[i] = h->fbuf[h->cur_f][i];
+            a.n32[i] = h->fbuf[pin][i];
+            a.n32w[i] = h->fbuf[pw][i];
             a.n16[i] = h->hbuf[hb][i];
         }
-        a.R = h->R;
+        a.R = R_of(h, work);
+        a.Rw = R_of(h, work);
         a.Rh = h->Rh[hb];
         a.scale = h->hscale;
         a.g = h->geom;
@@ -466,7 +517,7 @@ lbm2p_status pressure_solve_h(lbm2p *h, int replay, int *k_out, double *r_out, f
             }
             a.Rin = h->Rh[h->hcur];
             a.Rout = h->Rh[1 - h->hcur];
-            a.inv_tau = h->inv_tau;
+            a.inv_tau = itau_of(h, work);
             a.Fp = h->Fp;
             a.partials = h->partials;
             a.shift = h->shift;
@@ -576,6 +627,8 @@ lbm2p_status pressure_solve_h(lbm2p *h, int replay, int *k_out, double *r_out, f
     }
     lbm2p_launch::half_widen(convert_args(h->hcur), h->grid, h->stream);
     LAUNCHED(h, "FP16 widen");
+    if (pout)
+        *pout = pw;
     if (k_out)
         *k_out = k;
     if (r_out)
@@ -590,11 +643,20 @@ lbm2p_status pressure_solve_h(lbm2p *h, int replay, int *k_out, double *r_out, f
     return LBM2P_OK;
 }
 
-lbm2p_status pressure_solve(lbm2p *h, int replay, int *k_out, double *r_out, float *ms_out)
+// The pressure sub-iteration from f buffer cur_f.  The first sweep writes the next buffer of
+// the rotation, later sweeps ping-pong between the two buffers other than cur_f, so the state
+// the solve started from is only read; *pout receives the buffer holding the result (cur_f
+// when no sweep ran).  `work`: R and 1/tau_f of the work buffers (a step's solve, after its S
+// refresh) or the current ones (the t = 0 solve, lbm2p_pressure_sweeps).
+lbm2p_status pressure_solve(lbm2p *h, int replay, bool work, int *k_out, double *r_out,
+                            float *ms_out, int *pout)
 {
     if (h->fp16)
-        return pressure_solve_h(h, replay, k_out, r_out, ms_out);
+        return pressure_solve_h(h, replay, work, k_out, r_out, ms_out, pout);
     cudaStream_t st = (cudaStream_t)h->stream;
+    const int pin = h->cur_f, b1 = fnext(pin, 1), b2 = fnext(pin, 2);
+    auto dst_of = [&](int src) { return src == b1 ? b2 : b1; };
+    int src = pin;
     const int m = h->p.check_every;
     const int cap = h->p.max_sub_iters;
     double r = std::nan("");
@@ -623,14 +685,14 @@ lbm2p_status pressure_solve(lbm2p *h, int replay, int *k_out, double *r_out, flo
             const int kk = k + 1 + i;
             const bool check = nf == 0 && is_check(kk) && kk >= 2;
             const bool write_p = nf == 0 && is_check(kk + 1) && kk + 1 >= 2;
-            PressureArgs a = pressure_args(h, h->cur_f);
+            PressureArgs a = pressure_args(h, src, dst_of(src), work);
             launch_sweep(h, a, check, write_p);
             LAUNCHED(h, "pressure sweep");
-            h->cur_f = 1 - h->cur_f;
+            src = dst_of(src);
             h->sweeps += 1;
         }
         for (int q = 0; q < nf; ++q) {
-            PressureArgs a = pressure_args(h, h->cur_f);
+            PressureArgs a = pressure_args(h, src, dst_of(src), work);
             if (h->tb_kind == 2)
                 lbm2p_launch::pressure_sweeps_pair_direct(a, q == nf - 1 && final_check,
                                                           h->tb_W / 30, h->tb_H, h->tb_grid,
@@ -643,7 +705,7 @@ lbm2p_status pressure_solve(lbm2p *h, int replay, int *k_out, double *r_out, flo
                                                     q == nf - 1 && final_check, h->tb_grid,
                                                     h->stream);
             LAUNCHED(h, "fused pressure sweeps");
-            h->cur_f = 1 - h->cur_f;
+            src = dst_of(src);
             h->sweeps += T;
         }
         last_nparts = nf > 0 ? h->tb_grid : sweep_nparts(h);
@@ -672,9 +734,9 @@ lbm2p_status pressure_solve(lbm2p *h, int replay, int *k_out, double *r_out, flo
         return LBM2P_OK;
     };
     lbm2p_status e;
-    if (replay < 0 && h->graph_ok) {
+    if (replay < 0 && h->graph_ok && !work) {
         cudaGraphExec_t x;
-        if ((e = solve_graph(h, h->cur_f, &x)) != LBM2P_OK)
+        if ((e = solve_graph(h, pin, &x)) != LBM2P_OK)
             return e;
         CUDA_TRY(h, cudaGraphLaunch(x, st));
         float ms = -1.0f;
@@ -686,13 +748,15 @@ lbm2p_status pressure_solve(lbm2p *h, int replay, int *k_out, double *r_out, flo
             *r_out = r;
         if (ms_out)
             *ms_out = ms;
+        if (pout)
+            *pout = b2;
         return loop_status(h, k, r);
     }
     // R moves to the current P after sweep k when k is a multiple of rebase_every and the
     // solve goes on (the graph loop applies the same rule)
     const int every = h->rebase_every;
     auto rebase_mid = [&]() -> lbm2p_status {
-        lbm2p_launch::rebase_mid(rebase_mid_args(h, h->cur_f), h->grid, h->stream);
+        lbm2p_launch::rebase_mid(rebase_mid_args(h, src, work), h->grid, h->stream);
         LAUNCHED(h, "mid-solve rebase");
         return LBM2P_OK;
     };
@@ -751,6 +815,8 @@ lbm2p_status pressure_solve(lbm2p *h, int replay, int *k_out, double *r_out, flo
         *r_out = r;
     if (ms_out)
         *ms_out = h->timing ? ms_total : -1.0f;
+    if (pout)
+        *pout = src;
     if (status == LBM2P_ENONFINITE)
         return fail(h, status, "pressure residual is not finite after %d sweeps", k);
     if (status == LBM2P_ENOTCONVERGED)
@@ -759,9 +825,27 @@ lbm2p_status pressure_solve(lbm2p *h, int replay, int *k_out, double *r_out, flo
     return LBM2P_OK;
 }
 
+// One physical step.  Its inputs (f buffer cur_f, g buffer cur_g, the current R, 1/tau_f and
+// P^{n-1}) are only read; the step writes the other buffers and makes them current when it
+// ends.  A step whose pressure residual is not a number (ENONFINITE) runs no saturation update
+// and changes no current buffer: the state is as before the step.
 lbm2p_status one_step(lbm2p *h, int replay, lbm2p_step_stats *stats)
 {
     cudaStream_t st = (cudaStream_t)h->stream;
+    auto fill = [&](int k, lbm2p_status ps, double r, float sw_ms, float step_ms) {
+        if (stats) {
+            stats->sub_iters = k;
+            stats->status = ps;
+            stats->residual = r;
+            stats->sweep_ms = sw_ms;
+            stats->step_ms = step_ms;
+        }
+    };
+    auto advance = [&](int pout) {
+        h->cur_f = pout;
+        h->cur_g = 1 - h->cur_g;
+        h->cur_r = 1 - h->cur_r;
+    };
     if (replay < 0 && h->graph_ok) {
         cudaGraphExec_t x;
         lbm2p_status e = step_graph(h, h->cur_f, h->cur_g, &x);
@@ -777,59 +861,44 @@ lbm2p_status one_step(lbm2p *h, int replay, lbm2p_step_stats *stats)
         float sw_ms = -1.0f, step_ms = -1.0f;
         if ((e = read_loop(h, &k, &r, &sw_ms)) != LBM2P_OK)
             return e;
-        h->launches += 3;                 // refresh (with the warm start), saturation, rebase
-        h->cur_g = 1 - h->cur_g;
+        const bool finite = !std::isnan(r);
+        // refresh and the finiteness test; saturation and rebase when the step goes on
+        h->launches += finite ? 4 : 2;
         if (h->timing)
             CUDA_TRY(h, cudaEventElapsedTime(&step_ms, h->ev_step0, h->ev_step1));
         lbm2p_status ps = loop_status(h, k, r);
-        if (stats) {
-            stats->sub_iters = k;
-            stats->status = ps;
-            stats->residual = r;
-            stats->sweep_ms = sw_ms;
-            stats->step_ms = step_ms;
-        }
+        if (finite)
+            advance(fnext(h->cur_f, 2));
+        fill(k, ps, r, sw_ms, step_ms);
         return ps;
     }
     if (h->timing)
         CUDA_TRY(h, cudaEventRecord(h->ev_step0, st));
-    // a1: stream g, S^n, tau_f
-    lbm2p_launch::refresh(refresh_args(h, h->cur_g), h->grid, h->stream);
+    // a1: stream g, S^n, tau_f (and the warm start) into the work buffers
+    lbm2p_launch::refresh(refresh_args(h, h->cur_g, false), h->grid, h->stream);
     LAUNCHED(h, "refresh");
     // a2/a3: pressure sub-iteration
-    int k = 0;
+    int k = 0, pout = h->cur_f;
     double r = std::nan("");
     float sw_ms = -1.0f;
-    lbm2p_status ps = pressure_solve(h, replay, &k, &r, &sw_ms);
+    lbm2p_status ps = pressure_solve(h, replay, true, &k, &r, &sw_ms, &pout);
     if (ps != LBM2P_OK && ps != LBM2P_ENOTCONVERGED) {
-        if (stats) {
-            stats->sub_iters = k;
-            stats->status = ps;
-            stats->residual = r;
-            stats->sweep_ms = sw_ms;
-            stats->step_ms = -1.0f;
-        }
+        fill(k, ps, r, sw_ms, -1.0f);
         return ps;
     }
     // a4/a5: grad P and the saturation update
-    lbm2p_launch::saturation(saturation_args(h, h->cur_f, h->cur_g), h->grid, h->stream);
+    lbm2p_launch::saturation(saturation_args(h, pout, h->cur_g, true), h->grid, h->stream);
     LAUNCHED(h, "saturation");
-    lbm2p_launch::rebase(rebase_args(h, h->cur_f), h->grid, h->stream);
+    lbm2p_launch::rebase(rebase_args(h, pout, true), h->grid, h->stream);
     LAUNCHED(h, "rebase");
-    h->cur_g = 1 - h->cur_g;
+    advance(pout);
     float step_ms = -1.0f;
     if (h->timing) {
         CUDA_TRY(h, cudaEventRecord(h->ev_step1, st));
         CUDA_TRY(h, cudaEventSynchronize(h->ev_step1));
         CUDA_TRY(h, cudaEventElapsedTime(&step_ms, h->ev_step0, h->ev_step1));
     }
-    if (stats) {
-        stats->sub_iters = k;
-        stats->status = ps;
-        stats->residual = r;
-        stats->sweep_ms = sw_ms;
-        stats->step_ms = step_ms;
-    }
+    fill(k, ps, r, sw_ms, step_ms);
     return ps;
 }
 
@@ -1003,12 +1072,12 @@ lbm2p_status autotune_sweeps(lbm2p *h)
                 last_grid = grid;
                 float ms = 0.0f, mc = 0.0f;
                 if (!timed([&](int k) {
-                        PressureArgs a = pressure_args(h, k % 2);
+                        PressureArgs a = pressure_args(h, k % 2, 1 - k % 2, false);
                         lbm2p_launch::pressure_sweep(a, false, false, grid, h->stream, kind);
                     }, &ms))
                     goto done;
                 if (!timed_check([&](int k) {
-                        PressureArgs a = pressure_args(h, k % 2);
+                        PressureArgs a = pressure_args(h, k % 2, 1 - k % 2, false);
                         lbm2p_launch::pressure_sweep(a, true, false, h->grid_check_k[kind], h->stream,
                                                      kind);
                     }, h->grid_check_k[kind], ms, &mc))
@@ -1055,13 +1124,13 @@ lbm2p_status autotune_sweeps(lbm2p *h)
                 const int grid = (int)lbm2p_launch::rows_grid(width, H, h->nx, h->ny);
                 float ms = 0.0f, mc = 0.0f;
                 if (!timed([&](int k) {
-                        PressureArgs a = pressure_args(h, k % 2);
+                        PressureArgs a = pressure_args(h, k % 2, 1 - k % 2, false);
                         lbm2p_launch::pressure_sweep_rows(a, false, false, width, slots, H, grid,
                                                           h->stream);
                     }, &ms))
                     goto done;
                 if (!timed_check([&](int k) {
-                        PressureArgs a = pressure_args(h, k % 2);
+                        PressureArgs a = pressure_args(h, k % 2, 1 - k % 2, false);
                         lbm2p_launch::pressure_sweep_rows(a, true, false, width, slots, H, grid,
                                                           h->stream);
                     }, grid, ms, &mc))
@@ -1118,13 +1187,13 @@ lbm2p_status autotune_sweeps(lbm2p *h)
                         continue;
                     float ms = 0.0f, mc = 0.0f;
                     if (!timed([&](int k) {
-                            PressureArgs a = pressure_args(h, k % 2);
+                            PressureArgs a = pressure_args(h, k % 2, 1 - k % 2, false);
                             lbm2p_launch::pressure_sweeps_fused(a, T, W, H, false, (int)blocks,
                                                                 h->stream);
                         }, &ms))
                         goto done;
                     if (!timed_check([&](int k) {
-                            PressureArgs a = pressure_args(h, k % 2);
+                            PressureArgs a = pressure_args(h, k % 2, 1 - k % 2, false);
                             lbm2p_launch::pressure_sweeps_fused(a, T, W, H, true, (int)blocks,
                                                                 h->stream);
                         }, blocks, ms, &mc))
@@ -1159,13 +1228,13 @@ lbm2p_status autotune_sweeps(lbm2p *h)
                         continue;
                     float ms = 0.0f, mc = 0.0f;
                     if (!timed([&](int k) {
-                            PressureArgs a = pressure_args(h, k % 2);
+                            PressureArgs a = pressure_args(h, k % 2, 1 - k % 2, false);
                             lbm2p_launch::pressure_sweeps_pair_direct(a, false, cw, Hc, (int)blocks,
                                                                       h->stream);
                         }, &ms))
                         goto done;
                     if (!timed_check([&](int k) {
-                            PressureArgs a = pressure_args(h, k % 2);
+                            PressureArgs a = pressure_args(h, k % 2, 1 - k % 2, false);
                             lbm2p_launch::pressure_sweeps_pair_direct(a, true, cw, Hc, (int)blocks,
                                                                       h->stream);
                         }, blocks, ms, &mc))
@@ -1205,13 +1274,13 @@ lbm2p_status autotune_sweeps(lbm2p *h)
                         continue;
                     float ms = 0.0f, mc = 0.0f;
                     if (!timed([&](int k) {
-                            PressureArgs a = pressure_args(h, k % 2);
+                            PressureArgs a = pressure_args(h, k % 2, 1 - k % 2, false);
                             lbm2p_launch::pressure_sweeps_rows2(a, false, cw, slots, Hc,
                                                                 (int)blocks, h->stream);
                         }, &ms))
                         goto done;
                     if (!timed_check([&](int k) {
-                            PressureArgs a = pressure_args(h, k % 2);
+                            PressureArgs a = pressure_args(h, k % 2, 1 - k % 2, false);
                             lbm2p_launch::pressure_sweeps_rows2(a, true, cw, slots, Hc,
                                                                 (int)blocks, h->stream);
                         }, blocks, ms, &mc))
@@ -1259,7 +1328,7 @@ lbm2p_status autotune_h(lbm2p *h, int sms)
         }
         a.Rin = h->Rh[k & 1];
         a.Rout = h->Rh[1 - (k & 1)];
-        a.inv_tau = h->inv_tau;
+        a.inv_tau = itau_of(h, false);
         a.Fp = h->Fp;
         a.partials = h->partials;
         a.shift = h->shift;
@@ -1464,16 +1533,20 @@ lbm2p_status build(lbm2p *h, const lbm2p_inputs *in, lbm2p_step_stats *init_stat
         return *dst != nullptr;
     };
     bool ok = true;
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < 3; ++b)
         for (int i = 0; i < 8; ++i)
             ok = ok && plane_alloc(&h->fbuf[b][i]);
+    for (int b = 0; b < 2; ++b) {
         for (int i = 0; i < 9; ++i)
             ok = ok && plane_alloc(&h->gbuf[b][i]);
     }
-    ok = ok && plane_alloc(&h->inv_tau) && plane_alloc(&h->K) && plane_alloc(&h->S) &&
-         plane_alloc(&h->Pio) && plane_alloc(&h->tmp) && plane_alloc(&h->R);
-    if (p.warm_start)
-        ok = ok && plane_alloc(&h->Pstep);
+    for (int b = 0; b < 2; ++b) {
+        ok = ok && plane_alloc(&h->inv_taub[b]) && plane_alloc(&h->Rb[b]);
+        if (p.warm_start)
+            ok = ok && plane_alloc(&h->Pstepb[b]);
+    }
+    ok = ok && plane_alloc(&h->K) && plane_alloc(&h->S) && plane_alloc(&h->Pio) &&
+         plane_alloc(&h->tmp);
     if (in->Fp)
         ok = ok && plane_alloc(&h->Fp);
     if (in->Fs)
@@ -1601,11 +1674,12 @@ lbm2p_status build(lbm2p *h, const lbm2p_inputs *in, lbm2p_step_stats *init_stat
     if ((e = upload_plane(h, h->tmp, in->S0, 1.0)) != LBM2P_OK)   // tmp holds S0
         return e;
     // f^+ = f^eq(P0): reference R = P0 and zero deviations (the planes are zeroed above)
-    if (in->P0 && (e = upload_plane(h, h->R, in->P0, 1.0)) != LBM2P_OK)
+    if (in->P0 && (e = upload_plane(h, R_of(h, false), in->P0, 1.0)) != LBM2P_OK)
         return e;
     h->cur_f = 0;
     h->cur_g = 0;
-    lbm2p_launch::tau_from_S(h->inv_tau, h->tmp, h->K, g, m, h->grid, h->stream);
+    h->cur_r = 0;
+    lbm2p_launch::tau_from_S(itau_of(h, false), h->tmp, h->K, g, m, h->grid, h->stream);
     LAUNCHED(h, "tau from S");
     int k0 = 0;
     double r0 = std::nan("");
@@ -1613,7 +1687,10 @@ lbm2p_status build(lbm2p *h, const lbm2p_inputs *in, lbm2p_step_stats *init_stat
     // the t = 0 solve is timed on the device on its own (the autotuning above and the
     // uploads are outside the two events)
     CUDA_TRY(h, cudaEventRecord(h->ev_step0, st));
-    lbm2p_status ps = pressure_solve(h, in->init_replay ? *in->init_replay : -1, &k0, &r0, &ms0);
+    int pout = h->cur_f;
+    lbm2p_status ps = pressure_solve(h, in->init_replay ? *in->init_replay : -1, false, &k0, &r0,
+                                     &ms0, &pout);
+    h->cur_f = pout;
     if (cudaEventRecord(h->ev_step1, st) == cudaSuccess &&
         cudaEventSynchronize(h->ev_step1) == cudaSuccess)
         cudaEventElapsedTime(&solve_ms, h->ev_step0, h->ev_step1);
@@ -1629,12 +1706,12 @@ lbm2p_status build(lbm2p *h, const lbm2p_inputs *in, lbm2p_step_stats *init_stat
     InitGArgs a{};
     for (int i = 0; i < 8; ++i)
         a.fin[i] = h->fbuf[h->cur_f][i];
-    a.R = h->R;
+    a.R = R_of(h, false);
     a.Pnew = h->Pio;
     for (int i = 0; i < 9; ++i)
         a.gout[i] = h->gbuf[0][i];
     a.K = h->K;
-    a.inv_tau = h->inv_tau;
+    a.inv_tau = itau_of(h, false);
     a.Fs = h->Fs;
     a.S0 = h->tmp;
     a.S = h->S;
@@ -1647,11 +1724,11 @@ lbm2p_status build(lbm2p *h, const lbm2p_inputs *in, lbm2p_step_stats *init_stat
     a.w = w;
     lbm2p_launch::init_g(a, h->grid, h->stream);
     LAUNCHED(h, "init g");
-    lbm2p_launch::rebase(rebase_args(h, h->cur_f), h->grid, h->stream);
+    lbm2p_launch::rebase(rebase_args(h, h->cur_f, false), h->grid, h->stream);
     LAUNCHED(h, "rebase");
-    if (h->Pstep)                      // no history yet: the first step extrapolates nothing
-        CUDA_TRY(h, cudaMemcpyAsync(h->Pstep, h->R, (size_t)h->plane * sizeof(float),
-                                    cudaMemcpyDeviceToDevice, st));
+    if (h->p.warm_start)               // no history yet: the first step extrapolates nothing
+        CUDA_TRY(h, cudaMemcpyAsync(Pstep_of(h, false), R_of(h, false),
+                                    (size_t)h->plane * sizeof(float), cudaMemcpyDeviceToDevice, st));
     h->cur_g = 0;
     CUDA_TRY(h, cudaStreamSynchronize(st));
     return ps;
@@ -1803,7 +1880,9 @@ lbm2p_status lbm2p_pressure_sweeps(lbm2p *h, int nsweeps, double *residual)
     if (nsweeps < 0)
         return fail(h, LBM2P_EINVAL, "nsweeps must be >= 0");
     double r = std::nan("");
-    lbm2p_status st = pressure_solve(h, nsweeps, nullptr, &r, nullptr);
+    int pout = h->cur_f;
+    lbm2p_status st = pressure_solve(h, nsweeps, false, nullptr, &r, nullptr, &pout);
+    h->cur_f = pout;
     if (residual)
         *residual = r;
     return st;
@@ -1824,8 +1903,8 @@ static lbm2p_status run_fields(lbm2p *h, float *P, float *S, float *ux, float *u
     FieldsArgs a{};
     for (int i = 0; i < 8; ++i)
         a.fin[i] = h->fbuf[h->cur_f][i];
-    a.R = h->R;
-    a.inv_tau = h->inv_tau;
+    a.R = R_of(h, false);
+    a.inv_tau = itau_of(h, false);
     a.K = h->K;
     a.S = h->S;
     for (int s = 0; s < 4; ++s)
@@ -1882,9 +1961,9 @@ static lbm2p_status state_copy(lbm2p *h, float *buf, size_t count, int on_device
         planes[i] = h->fbuf[h->cur_f][i];
     for (int i = 0; i < 9; ++i)
         planes[8 + i] = h->gbuf[h->cur_g][i];
-    planes[17] = h->inv_tau;
+    planes[17] = itau_of(h, false);
     planes[18] = h->S;
-    planes[19] = h->R;
+    planes[19] = R_of(h, false);
     const size_t row = (size_t)h->nx * sizeof(float);
     const size_t dpitch = (size_t)h->pitch * sizeof(float);
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice
@@ -1896,9 +1975,9 @@ static lbm2p_status state_copy(lbm2p *h, float *buf, size_t count, int on_device
         else
             CUDA_TRY(h, cudaMemcpy2DAsync(planes[c], dpitch, hb, row, row, (size_t)h->ny, kind, st));
     }
-    if (!out && h->Pstep)              // a new state has no history: no extrapolation next step
-        CUDA_TRY(h, cudaMemcpyAsync(h->Pstep, h->R, (size_t)h->plane * sizeof(float),
-                                    cudaMemcpyDeviceToDevice, st));
+    if (!out && h->p.warm_start)       // a new state has no history: no extrapolation next step
+        CUDA_TRY(h, cudaMemcpyAsync(Pstep_of(h, false), R_of(h, false),
+                                    (size_t)h->plane * sizeof(float), cudaMemcpyDeviceToDevice, st));
     CUDA_TRY(h, cudaStreamSynchronize(st));
     return LBM2P_OK;
 }
@@ -1911,7 +1990,7 @@ lbm2p_status lbm2p_warm_start(lbm2p *h, const float *P_guess, int on_device)
         return fail(h, LBM2P_EINVAL, "P_guess must not be NULL");
     cudaStream_t st = (cudaStream_t)h->stream;
     const size_t row = (size_t)h->nx * sizeof(float);
-    CUDA_TRY(h, cudaMemcpy2DAsync(h->R, (size_t)h->pitch * sizeof(float), P_guess, row, row,
+    CUDA_TRY(h, cudaMemcpy2DAsync(R_of(h, false), (size_t)h->pitch * sizeof(float), P_guess, row, row,
                                   (size_t)h->ny,
                                   on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                                   st));

@@ -202,23 +202,40 @@ def train(op: PressureOperator, runs, epochs=1, batch=16, lr=1e-3, s_mean=0.2, s
     stats = torch.zeros((batch, 2, 2), dtype=torch.float64, device=op.device)
     s = op._stream()
     t0 = time.perf_counter()
+
+    def fill(idx):
+        stats.zero_()
+        for i, k in enumerate(idx):
+            r, n = items[k]
+            lnK, P, S = runs[r]
+            ds, dp = stats[i, 0], stats[i, 1]
+            lbm2p_op_diff_stats(S[n].data_ptr(), S[n - 1].data_ptr(), H * W, ds.data_ptr(), s)
+            lbm2p_op_diff_stats(P[n].data_ptr(), P[n - 1].data_ptr(), H * W, dp.data_ptr(), s)
+            lbm2p_op_features(lnK.data_ptr(), S[n].data_ptr(), S[n - 1].data_ptr(),
+                              P[n].data_ptr(), P[n - 1].data_ptr(), ds.data_ptr(),
+                              dp.data_ptr(), feat[i].data_ptr(), H, W, s_mean, s_scale, s)
+            lbm2p_op_target(P[n + 1].data_ptr(), P[n].data_ptr(), P[n - 1].data_ptr(),
+                            dp.data_ptr(), tgt[i].data_ptr(), H, W, s)
+
+    # the loss of the zero prediction (the plain extrapolation) on a sample of batches: the
+    # share of the target's mean square that the operator removes is what it learned
+    zero = torch.zeros((batch, H, W), dtype=torch.float32, device=op.device)
+    gbuf = torch.empty((batch, H, W, 16), dtype=torch.bfloat16, device=op.device)
+    zl = torch.zeros(1, dtype=torch.float64, device=op.device)
+    sample = rng.permutation(len(items))[:batch * 16]
+    for b0 in range(0, len(sample) - batch + 1, batch):
+        fill(sample[b0:b0 + batch])
+        lbm2p_op_mse_grad(zero.data_ptr(), tgt.data_ptr(), gbuf.data_ptr(), zl.data_ptr(),
+                          batch * H * W, 16, s)
+    zero_loss = float(zl.item()) / max(1, len(sample) // batch)
+    if log is not None:
+        log.append({"zero_prediction_loss": zero_loss})
     losses = []
     for ep in range(epochs):
         order = rng.permutation(len(items))
         total, count = 0.0, 0
         for b0 in range(0, len(order) - batch + 1, batch):
-            stats.zero_()
-            for i, k in enumerate(order[b0:b0 + batch]):
-                r, n = items[k]
-                lnK, P, S = runs[r]
-                ds, dp = stats[i, 0], stats[i, 1]
-                lbm2p_op_diff_stats(S[n].data_ptr(), S[n - 1].data_ptr(), H * W, ds.data_ptr(), s)
-                lbm2p_op_diff_stats(P[n].data_ptr(), P[n - 1].data_ptr(), H * W, dp.data_ptr(), s)
-                lbm2p_op_features(lnK.data_ptr(), S[n].data_ptr(), S[n - 1].data_ptr(),
-                                  P[n].data_ptr(), P[n - 1].data_ptr(), ds.data_ptr(),
-                                  dp.data_ptr(), feat[i].data_ptr(), H, W, s_mean, s_scale, s)
-                lbm2p_op_target(P[n + 1].data_ptr(), P[n].data_ptr(), P[n - 1].data_ptr(),
-                                dp.data_ptr(), tgt[i].data_ptr(), H, W, s)
+            fill(order[b0:b0 + batch])
             loss = op.train_step(feat, tgt, batch, H, W, lr=lr)
             total += float(loss.item())
             count += 1
