@@ -27,7 +27,8 @@ together by one lbm2p_batch per step; the line also reports the same members ste
 after another.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload five_spot_4096|five_spot_1024|manufactured_64|batch_five_spot_64]
+                    [--workload five_spot_4096|five_spot_1024|manufactured_64|batch_five_spot_64|
+                                batch_five_spot_mixed]
 """
 from __future__ import annotations
 
@@ -63,6 +64,8 @@ WORKLOADS = {
     "manufactured_64": dict(kind="manufactured", n=64),
     # independent five-spot realisations of uneven sizes advanced by one batch (lbm2p_batch)
     "batch_five_spot_64": dict(kind="batch", count=64, sizes=(128, 256, 512)),
+    # the batched workload's full size set, 1024^2 members included (64 realisations)
+    "batch_five_spot_mixed": dict(kind="batch", count=64, sizes=(128, 256, 512, 1024)),
 }
 DEFAULT_WORKLOAD = "five_spot_4096"
 SWEEP_KERNEL_NAMES = {1: "four nodes per thread (128-bit accesses)", 2: "one node per thread",
@@ -231,7 +234,8 @@ class ClockSampler:
 # sweeps per sample step of the oracle: (all host cores, one thread); fixed counts, so that
 # every run times the same work (a step = S refresh + the sweeps + the saturation update)
 CPU_SAMPLE_SWEEPS = {"five_spot_4096": (48, 4), "five_spot_1024": (400, 40),
-                     "manufactured_64": (4000, 2000), "batch_five_spot_64": (400, 40)}
+                     "manufactured_64": (4000, 2000), "batch_five_spot_64": (400, 40),
+                     "batch_five_spot_mixed": (400, 40)}
 
 
 def cpu_model() -> str:

@@ -43,7 +43,7 @@
 extern "C" {
 #endif
 
-#define LBM2P_ABI_VERSION 6
+#define LBM2P_ABI_VERSION 7
 /* Sparse wells passed to the sweep kernels as launch arguments (more wells: error). */
 #define LBM2P_MAX_WELLS 16
 
@@ -276,6 +276,17 @@ typedef enum {
 } lbm2p_fused_form;
 int lbm2p_fused_form_of(const lbm2p *h);
 
+/* Pin the two-sweep launch shape instead of the one create chose: form STAGED_ROWS (warps 4
+   or 8 consumer warps; slots 6 or 8 with 4 warps, 4 or 6 with 8, or 6 + LBM2P_ROWS2_DENSE: 4
+   warps and 6 slots with the register cap that keeps seven plain blocks per SM; rows 16, 32, 64
+   or 128) or DIRECT (warps 4 or 8, slots 0, rows 2, 4, 8, 16 or 32); rows above ny mean ny.
+   Every shape computes the same populations bit for bit; only the speed differs.  The lattice
+   needs walls on every side and FP32 storage, and check_every a multiple of 4.  Waits for the
+   handle's stream and drops its solve graphs (rebuilt on the next solve); a batch created
+   before keeps the shape it was built with.  EINVAL (handle unchanged) for any other value. */
+#define LBM2P_ROWS2_DENSE 16
+lbm2p_status lbm2p_set_fused_shape(lbm2p *h, int form, int warps, int slots, int rows);
+
 /* The candidates create timed to choose the sweep kernel, one line each:
  *   "single_vec4 <grid> 0 0 0 <us>", "single_scalar <grid> 0 0 0 <us>",
  *   "single_rows <strip width> <ring slots> <rows per block> <grid> <us>",
@@ -297,7 +308,9 @@ lbm2p_status lbm2p_counters(const lbm2p *h, long long *launches, long long *swee
  * all members, and the sub-iteration continues while any member is still above its
  * tolerance (members that met theirs stop sweeping).  The paper solves one realisation at
  * a time; this is the same per-member computation scheduled so that small lattices fill
- * the GPU together.
+ * the GPU together: they share one sweep kernel over a tile list, while a member of 512^2
+ * nodes or more whose handle runs two sweeps per launch keeps its own launches, in a branch
+ * of the loop body that runs beside the shared sweep while that member is still iterating.
  *
  * members: count handles made by lbm2p_create on the current device, all on one stream,
  * all with one even check_every that divides each member's max_sub_iters; each handle

@@ -108,6 +108,7 @@ def load_library(path: str = LIB_PATH):
         "lbm2p_counters": (C.c_int, [H, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
         "lbm2p_sweep_config": (C.c_int, [H] + [C.POINTER(C.c_int)] * 4),
         "lbm2p_fused_form_of": (C.c_int, [H]),
+        "lbm2p_set_fused_shape": (C.c_int, [H, C.c_int, C.c_int, C.c_int, C.c_int]),
         "lbm2p_autotune_report": (C.c_char_p, [H]),
         "lbm2p_warm_start": (C.c_int, [H, fp, C.c_int]),
         "lbm2p_pressure_sweep_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int),
@@ -298,11 +299,17 @@ def lbm2p_op_mse_grad(y0, tgt, g, loss, npix, c_out, stream=0):
 
 
 FUSED_NONE, FUSED_STAGES, FUSED_STAGED_ROWS, FUSED_DIRECT = 0, 1, 2, 3
+ROWS2_DENSE = 16
 
 
 def lbm2p_fused_form_of(h):
     """Which fused kernel runs the sweeps (FUSED_*)."""
     return _lib_or_raise().lbm2p_fused_form_of(h)
+
+
+def lbm2p_set_fused_shape(h, form, warps, slots, rows):
+    return _check(_lib_or_raise().lbm2p_set_fused_shape(h, int(form), int(warps), int(slots),
+                                                        int(rows)), h)
 
 
 def lbm2p_sweep_config(h):
@@ -551,6 +558,10 @@ class Solver:
 
     def counters(self):
         return lbm2p_counters(self.h)
+
+    def set_fused_shape(self, form, warps, slots, rows):
+        """Pin the two-sweep launch shape (see lbm2p_set_fused_shape)."""
+        return lbm2p_set_fused_shape(self.h, form, warps, slots, rows)
 
     def sweep_config(self):
         return lbm2p_sweep_config(self.h)

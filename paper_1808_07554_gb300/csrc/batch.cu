@@ -43,6 +43,14 @@ struct Member {
     int every;                   // sweeps between mid-solve rebases
     int wshift, rpt, seg_x;      // segment width 2^wshift, rows per tile, segments per row
     int tile0, ntiles;           // range in the batch tile list
+    // A member of 512^2 nodes or more whose handle sweeps two at a time ("own" member) runs
+    // its handle's own two-sweep launches in a branch of the loop body, under an IF node (its
+    // handle in the graph's array of own-member handles, by member index), instead of joining
+    // the batched sweep; its residual partials are then the handle's (nparts of them),
+    // otherwise the batch's own, one per tile.
+    int own;
+    const double *pparts;
+    int nparts;
 };
 
 // per-member loop state of the current step
@@ -76,8 +84,9 @@ __global__ void __launch_bounds__(kBlock) kb_refresh(const Member *__restrict__ 
     }
 }
 
-__global__ void kb_reset(MemberCtl *ctl, const int *__restrict__ caps,
-                         const double *__restrict__ tols, int count, int *active_count)
+__global__ void kb_reset(const Member *__restrict__ mem, MemberCtl *ctl,
+                         const int *__restrict__ caps, const double *__restrict__ tols, int count,
+                         int *active_count, const cudaGraphConditionalHandle *__restrict__ hown)
 {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m == 0)
@@ -89,6 +98,8 @@ __global__ void kb_reset(MemberCtl *ctl, const int *__restrict__ caps,
         ctl[m].active = caps[m] > 0 ? 1 : 0;
         ctl[m].rebase = 0;
         ctl[m].r = nan("");
+        if (mem[m].own)
+            cudaGraphSetConditional(hown[m], caps[m] > 0 ? 1u : 0u);
     }
 }
 
@@ -140,7 +151,8 @@ __global__ void __launch_bounds__(kBlock) kb_sweep(const Member *__restrict__ me
 // the members still active, counts[1] those to rebase.
 __global__ void __launch_bounds__(256) kb_finalize(const Member *__restrict__ mem,
                                                    const double *__restrict__ partials,
-                                                   MemberCtl *ctl, int body, int *counts)
+                                                   MemberCtl *ctl, int body, int *counts,
+                                                   const cudaGraphConditionalHandle *__restrict__ hown)
 {
     const int mi = blockIdx.x;
     MemberCtl &c = ctl[mi];
@@ -149,10 +161,11 @@ __global__ void __launch_bounds__(256) kb_finalize(const Member *__restrict__ me
     const Member &M = mem[mi];
     __shared__ double red[256][4];
     double s[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int i = threadIdx.x; i < M.ntiles; i += 256)
+    (void)partials;
+    for (int i = threadIdx.x; i < M.nparts; i += 256)
 #pragma unroll
         for (int q = 0; q < 4; ++q)
-            s[q] += partials[4 * (size_t)(M.tile0 + i) + q];
+            s[q] += M.pparts[4 * (size_t)i + q];
 #pragma unroll
     for (int q = 0; q < 4; ++q)
         red[threadIdx.x][q] = s[q];
@@ -185,6 +198,8 @@ __global__ void __launch_bounds__(256) kb_finalize(const Member *__restrict__ me
         const bool rebase = more && M.every > 0 && c.k % M.every == 0;
         c.active = more ? 1 : 0;
         c.rebase = rebase ? 1 : 0;
+        if (M.own)
+            cudaGraphSetConditional(hown[mi], more ? 1u : 0u);
         if (more)
             atomicAdd(&counts[0], 1);
         if (rebase)
@@ -215,7 +230,7 @@ __global__ void __launch_bounds__(256) kb_prefix(const Member *__restrict__ mem,
     __syncthreads();
     for (int base = 0; base < count; base += 256) {
         const int m = base + (int)threadIdx.x;
-        const int v = (m < count && ctl[m].active) ? mem[m].ntiles : 0;
+        const int v = (m < count && ctl[m].active && !mem[m].own) ? mem[m].ntiles : 0;
         scan[threadIdx.x] = v;
         __syncthreads();
         for (int off = 1; off < 256; off <<= 1) {        // inclusive scan
@@ -235,14 +250,15 @@ __global__ void __launch_bounds__(256) kb_prefix(const Member *__restrict__ mem,
         counts[2] = carry;
 }
 
-// one block per member: list the tiles of an active member at its prefix offset
+// one block per member: list the tiles of an active member of the batched sweep at its prefix
+// offset
 __global__ void __launch_bounds__(256) kb_scatter(const Member *__restrict__ mem,
                                                   const MemberCtl *__restrict__ ctl,
                                                   const int *__restrict__ prefix,
                                                   int2 *__restrict__ act)
 {
     const int m = blockIdx.x;
-    if (!ctl[m].active)
+    if (!ctl[m].active || mem[m].own)           // own members sweep with their own launches
         return;
     const int base = prefix[m], n = mem[m].ntiles;
     for (int i = threadIdx.x; i < n; i += 256)
@@ -307,6 +323,8 @@ struct lbm2p_batch {
     int *d_prefix = nullptr;             // first compacted tile of each active member
     int2 *d_act = nullptr;               // compacted (member, tile) list
     double *d_partials = nullptr;
+    cudaGraphConditionalHandle *d_hown[2] = {};   // per graph: IF handle of each own member
+    std::vector<lbm2p *> own_h;          // the handles of the own members (index = member)
     cudaGraph_t graph[2] = {};
     cudaGraphExec_t exec[2] = {};
     int gstep = 0;                       // parity of the steps run by the batch
@@ -354,6 +372,8 @@ void batch_free(lbm2p_batch *b)
     cudaFree(b->d_prefix);
     cudaFree(b->d_act);
     cudaFree(b->d_partials);
+    cudaFree(b->d_hown[0]);
+    cudaFree(b->d_hown[1]);
     if (b->h_ctl)
         cudaFreeHost(b->h_ctl);
     if (b->h_caps)
@@ -412,8 +432,17 @@ lbm2p_status build_graph(lbm2p_batch *b, int q)
         void *args[] = {(void *)&mem, (void *)&tm, (void *)&total, (void *)&q};
         BTRY(b, add_k(&nr, G, nullptr, (void *)kb_refresh, b->grid, kBlock, args));
     }
+    // IF handles of the own members (created in the step graph, used inside the loop body)
+    std::vector<cudaGraphConditionalHandle> hown((size_t)count, cudaGraphConditionalHandle{});
+    for (int m = 0; m < count; ++m)
+        if (b->own_h[(size_t)m])
+            BTRY(b, cudaGraphConditionalHandleCreate(&hown[(size_t)m], G, 0, 0));
+    BTRY(b, cudaMemcpy(b->d_hown[q], hown.data(), sizeof(cudaGraphConditionalHandle) * (size_t)count,
+                       cudaMemcpyHostToDevice));
+    const cudaGraphConditionalHandle *chown = b->d_hown[q];
     {
-        void *args[] = {(void *)&ctl, (void *)&caps, (void *)&tols, (void *)&count, (void *)&act};
+        void *args[] = {(void *)&mem, (void *)&ctl, (void *)&caps, (void *)&tols, (void *)&count,
+                        (void *)&act, (void *)&chown};
         BTRY(b, add_k(&nreset, G, &nr, (void *)kb_reset, (count + 255) / 256, 256, args));
     }
     cudaGraphConditionalHandle hd, hnone{};
@@ -445,10 +474,52 @@ lbm2p_status build_graph(lbm2p_batch *b, int q)
                       check ? b->grid_check : b->grid, kBlock, args));
         prev = n;
     }
+    // the own members' two-sweep launches, each under its IF node, beside the batched sweeps
+    std::vector<cudaGraphNode_t> ends{prev};
+    for (int m = 0; m < count; ++m) {
+        lbm2p *h = b->own_h[(size_t)m];
+        if (!h)
+            continue;
+        cudaGraphNodeParams ip{};
+        ip.type = cudaGraphNodeTypeConditional;
+        ip.conditional.handle = hown[(size_t)m];
+        ip.conditional.type = cudaGraphCondTypeIf;
+        ip.conditional.size = 1;
+        cudaGraphNode_t nifm;
+        BTRY(b, cudaGraphAddNode(&nifm, bg, nullptr, nullptr, 0, &ip));
+        cudaGraph_t ig = ip.conditional.phGraph_out[0];
+        const int A = h->cur_f, B = lbm2p_internal::fnext(A, 1);
+        cudaGraphNode_t p2 = nullptr;
+        int src = A;
+        for (int kk = 2; kk <= body; kk += 2) {
+            PressureArgs a = lbm2p_internal::pressure_args(h, src, src == A ? B : A, false);
+            cudaGraphNode_t n;
+            const bool chk = kk == body;
+            if (h->tb_kind == 2)
+                BTRY(b, lbm2p_launch::node_pressure_pair_direct(&n, ig, p2 ? &p2 : nullptr, a, chk,
+                                                                h->tb_W / 30, h->tb_H, h->tb_grid));
+            else if (h->tb_kind == 1)
+                BTRY(b, lbm2p_launch::node_pressure_rows2(&n, ig, p2 ? &p2 : nullptr, a, chk,
+                                                          h->tb_W / 30, h->tb_slots, h->tb_H,
+                                                          h->tb_grid));
+            else
+                BTRY(b, lbm2p_launch::node_pressure_fused(&n, ig, p2 ? &p2 : nullptr, a, 2, h->tb_W,
+                                                          h->tb_H, chk, h->tb_grid));
+            p2 = n;
+            src = src == A ? B : A;
+        }
+        ends.push_back(nifm);
+    }
     cudaGraphNode_t nf, nc, nsc2, nif, nrm;
     {
-        void *args[] = {(void *)&mem, (void *)&cpartials, (void *)&ctl, (void *)&body, (void *)&act};
-        BTRY(b, add_k(&nf, bg, &prev, (void *)kb_finalize, count, 256, args));
+        void *args[] = {(void *)&mem, (void *)&cpartials, (void *)&ctl, (void *)&body, (void *)&act,
+                        (void *)&chown};
+        cudaKernelNodeParams kp{};
+        kp.func = (void *)kb_finalize;
+        kp.gridDim = dim3((unsigned)count);
+        kp.blockDim = dim3(256u);
+        kp.kernelParams = args;
+        BTRY(b, cudaGraphAddKernelNode(&nf, bg, ends.data(), ends.size(), &kp));
     }
     cudaGraphConditionalHandle hr;
     BTRY(b, cudaGraphConditionalHandleCreate(&hr, bg, 0, 0));
@@ -562,6 +633,13 @@ lbm2p_status lbm2p_batch_create(lbm2p_batch **out, lbm2p *const *members, int co
         M.ntiles = M.seg_x * ((h->ny + M.rpt - 1) / M.rpt);
         total += M.ntiles;
         tile_member.insert(tile_member.end(), (size_t)M.ntiles, i);
+        // large members keep the two-sweep launches their handle chose (a body of check_every
+        // sweeps is then check_every / 2 launches, an even number, ending in buffer A)
+        M.own = (!h->fp16 && h->tb_T_graph == 2 && h->nnodes >= 512LL * 512 &&
+                 b->body % 4 == 0 && h->tb_grid > 0 && h->partials) ? 1 : 0;
+        M.pparts = M.own ? h->partials : nullptr;
+        M.nparts = M.own ? h->tb_grid : M.ntiles;
+        b->own_h.push_back(M.own ? h : nullptr);
         b->pf.push_back(h->cur_f);
         b->pg0.push_back(h->cur_g);
         b->pr.push_back(h->cur_r);
@@ -595,6 +673,10 @@ lbm2p_status lbm2p_batch_create(lbm2p_batch **out, lbm2p *const *members, int co
             ok(cudaMalloc(&b->d_prefix, sizeof(int) * (size_t)count), "cudaMalloc") &&
             ok(cudaMalloc(&b->d_act, sizeof(int2) * (size_t)total), "cudaMalloc") &&
             ok(cudaMalloc(&b->d_partials, sizeof(double) * 4 * (size_t)total), "cudaMalloc") &&
+            ok(cudaMalloc(&b->d_hown[0], sizeof(cudaGraphConditionalHandle) * (size_t)count),
+               "cudaMalloc") &&
+            ok(cudaMalloc(&b->d_hown[1], sizeof(cudaGraphConditionalHandle) * (size_t)count),
+               "cudaMalloc") &&
             ok(cudaMallocHost(&b->h_ctl, sizeof(MemberCtl) * (size_t)count), "cudaMallocHost") &&
             ok(cudaMallocHost(&b->h_caps, sizeof(int) * (size_t)count), "cudaMallocHost") &&
             ok(cudaMallocHost(&b->h_tols, sizeof(double) * (size_t)count), "cudaMallocHost") &&
@@ -602,6 +684,10 @@ lbm2p_status lbm2p_batch_create(lbm2p_batch **out, lbm2p *const *members, int co
             ok(cudaEventCreate(&b->ev1), "cudaEventCreate");
     }
     if (st == LBM2P_OK) {
+        // the batched sweep's residual partials: one per tile of each member it sweeps
+        for (int i = 0; i < count; ++i)
+            if (!hm[(size_t)i].own)
+                hm[(size_t)i].pparts = b->d_partials + 4 * (size_t)hm[(size_t)i].tile0;
         cudaStream_t cs = (cudaStream_t)b->stream;
         ok(cudaMemcpyAsync(b->d_mem, hm.data(), sizeof(Member) * (size_t)count,
                            cudaMemcpyHostToDevice, cs), "cudaMemcpyAsync") &&
@@ -696,6 +782,9 @@ lbm2p_status lbm2p_batch_step(lbm2p_batch *b, int nsteps, const int *replay,
         const int passes = kmax > 0 ? kmax / b->body : 1;
         const int every = b->body * ((1024 + b->body - 1) / b->body);
         b->launches += 6 + (long long)passes * (b->body + 3) + (kmax > 0 ? (kmax - 1) / every : 0);
+        for (int m = 0; m < b->count; ++m)     // own members: two sweeps per launch
+            if (b->own_h[(size_t)m])
+                b->launches += b->h_ctl[m].k / 2;
         if (worst == LBM2P_ENONFINITE)
             return bfail(b, worst, "a member's pressure residual is not finite (step %d)", s);
     }

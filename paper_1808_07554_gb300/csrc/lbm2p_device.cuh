@@ -264,6 +264,8 @@ cudaError_t node_pressure_rows(cudaGraphNode_t *n, cudaGraph_t g, const cudaGrap
 // two sweeps per launch on staged rows (sweep_rows.cu), lattices without periodic sides:
 // cw consumer warps of 30 owned columns each (4 or 8), ring slots (6/8 with 4 warps, 4/6
 // with 8), H output rows per block; grid = rows2_grid(...)
+// slots + kRows2Dense: the (4 warps, 6 slots) shape whose plain launch keeps seven blocks per SM
+constexpr int kRows2Dense = LBM2P_ROWS2_DENSE;
 bool rows2_shape_ok(int cw, int slots);
 int rows2_width(int cw);
 size_t rows2_smem_bytes(int cw, int slots, bool has_fp);

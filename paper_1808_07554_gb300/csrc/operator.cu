@@ -640,6 +640,11 @@ cudaError_t launch_conv(const ConvArgs &a, cudaStream_t s)
     const size_t smem = conv_rows_smem_bytes<CIN, COUT>();
     cudaError_t e = cudaFuncSetAttribute(k_conv3x3_rows<CIN, COUT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // all of the unified L1/shared storage as shared memory, so that several CTAs (each ~69 KB
+    // for 32 input channels) fit on an SM
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_conv3x3_rows<CIN, COUT>,
+                                 cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess)
         return e;
     int per_sm = 0;
@@ -663,6 +668,9 @@ cudaError_t launch_wgrad(const WgradArgs &a, cudaStream_t s)
     const size_t smem = wgrad_smem_bytes<CIN, COUT>();
     cudaError_t e = cudaFuncSetAttribute(k_conv3x3_wgrad<CIN, COUT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_conv3x3_wgrad<CIN, COUT>,
+                                 cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess)
         return e;
     int per_sm = 0;

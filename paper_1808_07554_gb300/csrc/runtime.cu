@@ -182,14 +182,9 @@ void *dev_alloc(lbm2p *h, size_t bytes)
     return ptr;
 }
 
-void free_all(lbm2p *h)
+// destroy the instantiated solve and step graphs (they are rebuilt on first use)
+void drop_graphs(lbm2p *h)
 {
-    for (auto &a : h->allocs) {
-        if (h->p.alloc && h->p.release)
-            h->p.release(a.ptr, a.bytes, h->p.alloc_ctx);
-        else if (!h->p.alloc)
-            cudaFree(a.ptr);
-    }
     for (int a = 0; a < 3; ++a)
         for (int r = 0; r < 2; ++r) {
             if (h->solve_x[a][r])
@@ -207,6 +202,17 @@ void free_all(lbm2p *h)
                 h->step_g[a][b][r] = nullptr;
             }
         }
+}
+
+void free_all(lbm2p *h)
+{
+    for (auto &a : h->allocs) {
+        if (h->p.alloc && h->p.release)
+            h->p.release(a.ptr, a.bytes, h->p.alloc_ctx);
+        else if (!h->p.alloc)
+            cudaFree(a.ptr);
+    }
+    drop_graphs(h);
     h->allocs.clear();
     if (h->res_host)
         cudaFreeHost(h->res_host);
@@ -1255,7 +1261,7 @@ lbm2p_status autotune_sweeps(lbm2p *h)
         }
         if (walls && !direct_only && (h->p.fuse_sweeps == 0 || h->p.fuse_sweeps == 2) &&
             (forced == LBM2P_SWEEP_AUTO || forced == LBM2P_SWEEP_ROWS)) {
-            const int shapes2[4][2] = {{4, 6}, {4, 8}, {8, 4}, {8, 6}};
+            const int shapes2[5][2] = {{4, 6}, {4, 8}, {8, 4}, {8, 6}, {4, 6 + lbm2p_launch::kRows2Dense}};
             for (const auto &sh : shapes2) {
                 const int cw = sh[0], slots = sh[1];
                 if (lbm2p_launch::rows2_prepare(cw, slots) != cudaSuccess ||
@@ -2037,6 +2043,59 @@ lbm2p_status lbm2p_sweep_config(const lbm2p *h, int *fused, int *kind, int *tile
         *tile_w = h->tb_T > 1 ? h->tb_W : (h->sweep_kind == 2 ? h->rows_w : 0);
     if (tile_h)
         *tile_h = h->tb_T > 1 ? h->tb_H : (h->sweep_kind == 2 ? h->rows_H : 0);
+    return LBM2P_OK;
+}
+
+lbm2p_status lbm2p_set_fused_shape(lbm2p *h, int form, int warps, int slots, int rows)
+{
+    if (!h)
+        return fail(nullptr, LBM2P_EINVAL, "NULL handle");
+    if (h->fp16)
+        return fail(h, LBM2P_EINVAL, "FP16 storage sweeps one sweep per launch");
+    for (int sd = 0; sd < 4; ++sd)
+        if (h->p.bc[sd] == LBM2P_BC_PERIODIC)
+            return fail(h, LBM2P_EINVAL, "the two-sweep row-walking kernels need walls on every side");
+    if (h->p.check_every % 4 != 0)
+        return fail(h, LBM2P_EINVAL, "check_every %d is not a multiple of 4 (two launches of two "
+                    "sweeps per loop body at least)", h->p.check_every);
+    // rows per block: a size the create-time tuning tries (clamped to ny as it is there)
+    auto rows_ok = [&](std::initializer_list<int> tried) {
+        for (int H : tried)
+            if (rows == (H < h->ny ? H : h->ny))
+                return true;
+        return false;
+    };
+    long long grid = 0;
+    if ((form == LBM2P_FUSED_STAGED_ROWS && !rows_ok({16, 32, 64, 128})) ||
+        (form == LBM2P_FUSED_DIRECT && !rows_ok({2, 4, 8, 16, 32})))
+        return fail(h, LBM2P_EINVAL, "rows %d: not a block height of this form for ny = %d", rows,
+                    h->ny);
+    if (form == LBM2P_FUSED_STAGED_ROWS) {
+        if (!lbm2p_launch::rows2_shape_ok(warps, slots))
+            return fail(h, LBM2P_EINVAL, "no staged-rows shape with %d consumer warps and %d slots",
+                        warps, slots);
+        CUDA_TRY(h, lbm2p_launch::rows2_prepare(warps, slots));
+        if (lbm2p_launch::rows2_blocks_per_sm(warps, slots, h->Fp != nullptr) < 1)
+            return fail(h, LBM2P_EINVAL, "the staged-rows shape does not fit on an SM");
+        grid = lbm2p_launch::rows2_grid(warps, rows, h->nx, h->ny);
+    } else if (form == LBM2P_FUSED_DIRECT) {
+        if ((warps != 4 && warps != 8) || slots != 0)
+            return fail(h, LBM2P_EINVAL, "the direct-load form takes 4 or 8 warps and 0 slots");
+        grid = lbm2p_launch::pair_direct_grid(warps, rows, h->nx, h->ny);
+    } else {
+        return fail(h, LBM2P_EINVAL, "form %d cannot be pinned (STAGED_ROWS or DIRECT)", form);
+    }
+    if (grid > h->partials_cap)
+        return fail(h, LBM2P_EINVAL, "%lld blocks exceed the %lld residual partials held", grid,
+                    h->partials_cap);
+    CUDA_TRY(h, cudaStreamSynchronize((cudaStream_t)h->stream));
+    drop_graphs(h);
+    h->tb_T = h->tb_T_graph = 2;
+    h->tb_kind = form == LBM2P_FUSED_STAGED_ROWS ? 1 : 2;
+    h->tb_W = 30 * warps;
+    h->tb_slots = form == LBM2P_FUSED_STAGED_ROWS ? slots : 0;
+    h->tb_H = rows;
+    h->tb_grid = (int)grid;
     return LBM2P_OK;
 }
 

@@ -423,8 +423,8 @@ struct Rows2Interior {
     }
 };
 
-template <bool CHECK, int CW, int S>
-__global__ void __launch_bounds__(32 * (CW + 1), CW == 4 ? 6 : 3) k_pressure_rows2(const __grid_constant__ PressureArgs a,
+template <bool CHECK, int CW, int S, int MINB>
+__global__ void __launch_bounds__(32 * (CW + 1), MINB) k_pressure_rows2(const __grid_constant__ PressureArgs a,
                                                                   int H)
 {
     constexpr int W = 30 * CW;
@@ -895,18 +895,26 @@ void *pair_direct_func(int cw, bool check)
     return check ? (void *)k_pressure_pair_direct<true, 8> : (void *)k_pressure_pair_direct<false, 8>;
 }
 
-template <int CW, int S>
+// Register caps (blocks per SM the compiler must allow): six 4-warp blocks (64 registers) or
+// three 8-warp ones; the dense variant's plain launch allows seven 4-warp blocks (56 registers,
+// a few bytes spilled) while its checking launch keeps six (no spills).
+template <int CW, int S, bool DENSE>
 void *rows2_func_t(bool check)
 {
-    return check ? (void *)k_pressure_rows2<true, CW, S> : (void *)k_pressure_rows2<false, CW, S>;
+    constexpr int base = CW == 4 ? 6 : 3;
+    return check ? (void *)k_pressure_rows2<true, CW, S, base>
+                 : (void *)k_pressure_rows2<false, CW, S, DENSE ? base + 1 : base>;
 }
 
-// the two-sweep shapes built: (consumer warps, ring slots)
+// the two-sweep shapes built: (consumer warps, ring slots [+ kRows2Dense])
 void *rows2_func(int cw, int slots, bool check)
 {
-    if (cw == 4)
-        return slots == 6 ? rows2_func_t<4, 6>(check) : rows2_func_t<4, 8>(check);
-    return slots == 4 ? rows2_func_t<8, 4>(check) : rows2_func_t<8, 6>(check);
+    if (cw == 4) {
+        if (slots == 6 + lbm2p_launch::kRows2Dense)
+            return rows2_func_t<4, 6, true>(check);
+        return slots == 6 ? rows2_func_t<4, 6, false>(check) : rows2_func_t<4, 8, false>(check);
+    }
+    return slots == 4 ? rows2_func_t<8, 4, false>(check) : rows2_func_t<8, 6, false>(check);
 }
 
 template <int CW, int S>
@@ -1009,6 +1017,8 @@ cudaError_t node_pressure_rows(cudaGraphNode_t *n, cudaGraph_t g, const cudaGrap
 // ---- two sweeps per launch on staged rows ----------------------------------------------
 bool rows2_shape_ok(int cw, int slots)
 {
+    if (cw == 4 && slots == 6 + kRows2Dense)
+        return true;
     return (cw == 4 && (slots == 6 || slots == 8)) || (cw == 8 && (slots == 4 || slots == 6));
 }
 
@@ -1019,6 +1029,7 @@ int rows2_width(int cw)
 
 size_t rows2_smem_bytes(int cw, int slots, bool has_fp)
 {
+    slots &= kRows2Dense - 1;
     const size_t rw = (size_t)rows2_width(cw) + 2 * lbm2p_dev::kRowsHalo;
     return 128 + lbm2p_dev::kRowsBarBytes + (size_t)slots * (has_fp ? 11 : 10) * rw * sizeof(float);
 }

@@ -37,7 +37,7 @@ def test_every_declared_function_is_exported(lib):
 
 def test_abi_version_and_defaults(lib):
     import paper_1808_07554_gb300 as pkg
-    assert pkg.lbm2p_abi_version() == 6
+    assert pkg.lbm2p_abi_version() == 7
     p = pkg.lbm2p_default_params()
     assert (p.phi, p.beta, p.mu_w, p.mu_n, p.D_s, p.tau_p, p.tol) == (0.2, 0.4, 1.0, 2.0, 0.01, 1.0, 1e-8)
     assert p.check_every == 8 and list(p.bc) == [1, 1, 1, 1] and p.fuse_sweeps == 0
@@ -103,6 +103,7 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.lbm2p_fields(None, None, None, 0, 0) == pkg.EINVAL
     assert lib.lbm2p_state_count(None) == 0
     assert lib.lbm2p_fused_form_of(None) == pkg.FUSED_NONE
+    assert lib.lbm2p_set_fused_shape(None, pkg.FUSED_STAGED_ROWS, 4, 6, 16) == pkg.EINVAL
     lib.lbm2p_destroy(None)
 
 
@@ -114,6 +115,8 @@ def test_binding_constants_match_the_header():
     assert "row tile of 1024" in text and pkg.NOALLOC_TILE_NODES == 1024
     m = re.search(r"#define\s+LBM2P_MAX_WELLS\s+(\d+)", text)
     assert m and int(m.group(1)) == pkg.MAX_WELLS
+    m = re.search(r"#define\s+LBM2P_ROWS2_DENSE\s+(\d+)", text)
+    assert m and int(m.group(1)) == pkg.ROWS2_DENSE
 
 
 def _cuda_present():

@@ -258,3 +258,28 @@ def test_nonfinite_member_is_reported():
         assert e.value.status == pkg.ENONFINITE
     P, S = g.fields()
     assert np.isfinite(P).all() and np.isfinite(S).all()
+
+
+def test_batch_against_oracle_with_a_1024_member():
+    """A batch holding a 1024^2 five-spot member (the largest size of the batched workload)
+    and a 128^2 one, both started from 64 t = 0 sweeps and stepped twice with 40 replayed
+    sweeps: every field of both members within relative L2 1e-5 of the FP64 oracle run the
+    same counts."""
+    pkg = _pkg()
+    probs = [W.quarter_five_spot(1024, seed=33), W.quarter_five_spot(128, seed=34)]
+    orcs = [O.Oracle(p, tol=1e-8, check_every=CHECK, init_replay=64) for p in probs]
+    sols = [_solver(p, init_replay=64) for p in probs]
+    with pkg.Batch(sols) as batch:
+        for _ in range(2):
+            for o in orcs:
+                st, k, r = o.step(1, replay=[40])
+                assert st == O.OK
+            batch.step(1, replay=[40, 40])
+    for p, o, s in zip(probs, orcs, sols):
+        ref = o.fields()
+        P, S = s.fields(mean_free_P=True)
+        ux, uy = s.velocity()
+        err = {"P": W.rel_l2(P, W.mean_free(ref["P"])), "S": W.rel_l2(S, ref["S"]),
+               "ux": W.rel_l2(ux, ref["ux"]), "uy": W.rel_l2(uy, ref["uy"])}
+        o.close()
+        assert all(v <= 1e-5 for v in err.values()), (p.nx, err)

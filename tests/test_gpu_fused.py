@@ -89,6 +89,49 @@ def test_fused_equals_single_sweeps(kind, T):
     fused.close()
 
 
+ROWS2_SHAPES = [(4, 6), (4, 8), (8, 4), (8, 6), (4, 6 + 16)]
+
+
+@pytest.mark.parametrize("kind", ["five_spot_ragged", "wide_dirichlet", "dirichlet", "tall"])
+def test_every_pinned_two_sweep_shape_equals_single_sweeps(kind):
+    """Each shape of the two two-sweep row-walking kernels (consumer warps x ring slots x rows
+    per block for the staged-rows kernel, including the seven-blocks-per-SM register cap;
+    warps x rows for the direct-load kernel), pinned with lbm2p_set_fused_shape, against one
+    sweep per launch, bit for bit, in bare sweeps and through a graph-resident step."""
+    import paper_1808_07554_gb300 as pkg
+    prob = _problem(kind)
+    single = pkg.Solver.from_problem(prob, init_replay=0, fuse_sweeps=1)
+    fused = pkg.Solver.from_problem(prob, init_replay=0, fuse_sweeps=2, sweep_kernel=pkg.SWEEP_ROWS)
+    rng = np.random.default_rng(11)
+    state = single.get_state()
+    state[:8] = 0.01 * rng.standard_normal(state[:8].shape)
+    state[17] = 1.0 / (0.55 + 2.0 * rng.random(state[17].shape))
+    state[19] = rng.standard_normal(state[19].shape)
+    shapes = [(pkg.FUSED_STAGED_ROWS, w, s, H) for (w, s) in ROWS2_SHAPES for H in (16, 128)]
+    shapes += [(pkg.FUSED_DIRECT, w, 0, H) for w in (4, 8) for H in (2, 32)]
+    for form, w, sl, H in shapes:
+        H = min(H, prob.ny)
+        fused.set_fused_shape(form, w, sl, H)
+        assert fused.fused_form() == form and fused.sweep_config()[2:] == (30 * w, H)
+        single.set_state(state)
+        fused.set_state(state)
+        for n in (5, 2):
+            single.pressure_sweeps(n)
+            fused.pressure_sweeps(n)
+            a, b = single.get_state(), fused.get_state()
+            assert np.array_equal(a, b), (kind, form, w, sl, H, n, float(np.max(np.abs(a - b))))
+        single.step(1, replay=[16])
+        fused.step(1, replay=[16])
+        assert np.array_equal(single.get_state(), fused.get_state()), (kind, form, w, sl, H)
+    for bad in ((pkg.FUSED_STAGED_ROWS, 4, 7, 16), (pkg.FUSED_STAGED_ROWS, 4, 6, 24),
+                (pkg.FUSED_DIRECT, 4, 6, 8), (pkg.FUSED_STAGES, 4, 6, 16)):
+        with pytest.raises(pkg.LBM2PError) as e:
+            fused.set_fused_shape(*bad)
+        assert e.value.status == pkg.EINVAL
+    single.close()
+    fused.close()
+
+
 @pytest.mark.parametrize("kind", ["five_spot_ragged", "wide_ragged", "periodic", "dirichlet",
                                   "mixed", "tiny", "column", "tall"])
 def test_single_sweep_kernels_agree(kind):
