@@ -61,6 +61,8 @@ BYTES_PER_SWEEP_NODE_FP16 = 44
 WORKLOADS = {
     "five_spot_4096": dict(kind="five_spot", n=4096),
     "five_spot_1024": dict(kind="five_spot", n=1024),
+    # larger than L2 but a fraction of the 4096^2 footprint: the size of the ncu captures
+    "five_spot_2048": dict(kind="five_spot", n=2048),
     "manufactured_64": dict(kind="manufactured", n=64),
     # independent five-spot realisations of uneven sizes advanced by one batch (lbm2p_batch)
     "batch_five_spot_64": dict(kind="batch", count=64, sizes=(128, 256, 512)),

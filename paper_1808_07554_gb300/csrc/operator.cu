@@ -177,6 +177,21 @@ constexpr size_t conv_rows_smem_bytes()
     return (size_t)(9 * CIN / 16) * COUT * 32 + 2 * (size_t)3 * (CIN / 8) * kChunkBytes + 8 + 16 + 128;
 }
 
+// 16 bytes global -> shared without a register round trip (cp.async); a source outside the
+// image (valid false) reads nothing and fills zeros.  Complete after cp_async_wait_all.
+__device__ __forceinline__ void cp_async16(unsigned char *dst, const void *src, bool valid)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
+                 :: "r"(smem_u32(dst)), "l"(src), "r"(valid ? 16 : 0) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// the three input rows of a tile into a stage buffer (asynchronous: every copy is in flight
+// at once; the caller waits with cp_async_wait_all)
 template <int CIN, int COUT>
 __device__ __forceinline__ void stage_rows(const ConvArgs &a, unsigned char *buf, long long tile,
                                            int tiles_x, int tid)
@@ -188,10 +203,9 @@ __device__ __forceinline__ void stage_rows(const ConvArgs &a, unsigned char *buf
     for (int i = tid; i < 3 * kRowPix * CH; i += kThreads) {
         const int c = i % CH, px = (i / CH) % kRowPix, r = i / (CH * kRowPix);
         const int yy = y + r - 1, xx = x0 + px - 1;
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (yy >= 0 && yy < a.H && xx >= 0 && xx < a.W)
-            v = *reinterpret_cast<const uint4 *>(a.x + (((size_t)img * a.H + yy) * a.W + xx) * CIN + 8 * c);
-        *reinterpret_cast<uint4 *>(buf + (r * CH + c) * kChunkBytes + px * 16) = v;
+        const bool valid = yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
+        const bf16 *src = valid ? a.x + (((size_t)img * a.H + yy) * a.W + xx) * CIN + 8 * c : a.x;
+        cp_async16(buf + (r * CH + c) * kChunkBytes + px * 16, src, valid);
     }
 }
 
@@ -232,6 +246,7 @@ __global__ void __launch_bounds__(kThreads) k_conv3x3_rows(const ConvArgs a)
     long long tile = blockIdx.x;
     if (tile < tiles)
         stage_rows<CIN, COUT>(a, stg, tile, tiles_x, tid);
+    cp_async_wait_all();
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
@@ -262,7 +277,6 @@ __global__ void __launch_bounds__(kThreads) k_conv3x3_rows(const ConvArgs a)
         const long long next = tile + gridDim.x;
         if (next < tiles)
             stage_rows<CIN, COUT>(a, stg + (b ^ 1) * kStageBytes, next, tiles_x, tid);
-        fence_async_smem();
         if (!wait_bounded(bar, phase)) {
             ok = false;
             break;
@@ -306,10 +320,14 @@ __global__ void __launch_bounds__(kThreads) k_conv3x3_rows(const ConvArgs a)
                     a.y0[q] = v[0];
             }
         }
-        // the accumulator and the buffer just read are free once every thread is past here
+        // the next tile's rows are in place, and the accumulator and the buffer just read are
+        // free, once every thread is past here
+        cp_async_wait_all();
+        fence_async_smem();
         tc_fence_before();
         __syncthreads();
     }
+    cp_async_wait_all();
     if (!ok) {
         if (tid == 0)
             atomicExch(a.err, 1);
