@@ -652,6 +652,28 @@ int sm_count()
     return g_sms;
 }
 
+// CTAs of `func` that fit on one SM by its registers, threads and `smem` bytes of dynamic
+// shared memory (the occupancy rule written out from the device attributes), and by the tensor
+// memory (kTmemCols of the 512 columns per CTA)
+int resident_per_sm(const void *func, size_t smem)
+{
+    int dev = 0, smem_sm = 0, reserved = 0, regs_sm = 0, thr_sm = 0;
+    cudaFuncAttributes fa{};
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaFuncGetAttributes(&fa, func) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev) != cudaSuccess)
+        return 1;
+    const long long per_smem = (long long)smem_sm / ((long long)smem + fa.sharedSizeBytes + reserved);
+    const int regs_cta = ((fa.numRegs * 32 + 255) / 256) * 256 * (kThreads / 32);
+    const long long per_regs = regs_cta > 0 ? regs_sm / regs_cta : 1;
+    long long per = per_smem < per_regs ? per_smem : per_regs;
+    per = per < thr_sm / kThreads ? per : thr_sm / kThreads;
+    per = per < 512 / (long long)kTmemCols ? per : 512 / (long long)kTmemCols;
+    return per < 1 ? 1 : (int)per;
+}
+
 template <int CIN, int COUT>
 cudaError_t launch_conv(const ConvArgs &a, cudaStream_t s)
 {
@@ -665,13 +687,9 @@ cudaError_t launch_conv(const ConvArgs &a, cudaStream_t s)
                                  cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess)
         return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv3x3_rows<CIN, COUT>, kThreads,
-                                                      smem);
-    if (e != cudaSuccess)
-        return e;
-    // tensor memory: 512 columns per SM, kTmemCols per resident CTA
-    per_sm = per_sm < 1 ? 1 : (per_sm > 512 / (int)kTmemCols ? 512 / (int)kTmemCols : per_sm);
+    // the runtime's occupancy query answered one CTA per SM for this kernel, where its
+    // registers and shared memory allow three (ncu's occupancy limits agree with the latter)
+    const int per_sm = resident_per_sm((const void *)k_conv3x3_rows<CIN, COUT>, smem);
     const long long tiles = (long long)a.nimg * a.H * ((a.W + 127) / 128);
     long long grid = (long long)sm_count() * per_sm;
     if (grid > tiles)
