@@ -408,13 +408,8 @@ def run_ours(args):
     sweep_cfg = solver.sweep_config()
     fform = solver.fused_form()
     # the autotuner's candidates (us per sweep in the solve loop), fastest first
-    full_report = solver.autotune_report()
-    report = sorted((r for r in full_report if not r[0].startswith("step_kernels")),
-                    key=lambda r: r[-1])
+    report = sorted(solver.autotune_report(), key=lambda r: r[-1])
     autotune_best = [" ".join(str(v) for v in r) for r in report[:8]]
-    # refresh + saturation with one and with four nodes per thread (us per pair of launches)
-    step_kernels = {r[0]: {"grid": r[1], "nodes_per_thread": r[3], "us": r[5]}
-                    for r in full_report if r[0].startswith("step_kernels")}
 
     # problems with time-dependent sources get them uploaded every step (host buffers)
     def upload(n):
@@ -523,7 +518,6 @@ def run_ours(args):
                    "sweep_kernel": sweep_cfg[1], "sweep_tile": [sweep_cfg[2], sweep_cfg[3]],
                    "fused_form": FUSED_FORM_NAMES.get(fform, "none"),
                    "autotune_best": autotune_best,
-                   "step_kernels": step_kernels,
                    "l2": "flushed before every timed step (256 MB write)",
                    "sub_iters_per_step": ksub, "sub_iters_histogram": hist,
                    "statuses": statuses,

@@ -292,11 +292,8 @@ lbm2p_status lbm2p_set_fused_shape(lbm2p *h, int form, int warps, int slots, int
  *   "single_rows <strip width> <ring slots> <rows per block> <grid> <us>",
  *   "fused <sweeps per launch> <threads per block> <rows per block> <grid> <us>",
  *   "fused_rows <consumer warps> <ring slots> <rows per block> <grid> <us>",
- *   "fused_direct <warps> 0 <rows per block> <grid> <us>",
- *   "step_kernels <grid> <threads per block> 1 0 <us>",
- *   "step_kernels_quad <grid> <threads per block> 4 0 <us>"
- * with <us> the time per sweep inside the solve loop (for the last two: the time of one
- * refresh and one saturation launch, with one or four nodes per thread): a check period of check_every sweeps
+ *   "fused_direct <warps> 0 <rows per block> <grid> <us>"
+ * with <us> the time per sweep inside the solve loop: a check period of check_every sweeps
  * timed as its plain launches plus the one launch that also sums the residual (the first two
  * kinds once per grid tried: the resident-block capacity of the GPU down to half of it).  Owned by h; valid until the next create-time tuning. */
 const char *lbm2p_autotune_report(const lbm2p *h);

@@ -645,186 +645,6 @@ __global__ void __launch_bounds__(kBlock) k_saturation(const __grid_constant__ S
 }
 
 // --------------------------------------------------------------------------------------
-// a1 and a4 + a5 with four consecutive nodes per thread, one float4 per plane row (the
-// layout of k_pressure): pulls with c_x = +1 take the element left of the float4 from lane - 1
-// (lane 0 loads it), pulls with c_x = -1 the element right of it from lane + 1 (lane 31 loads
-// it).  Threads whose four nodes are not all interior, whole edge rows and the ragged tail
-// use refresh_node / saturation_node.  Per node the arithmetic is that of the scalar kernels
-// (refresh_tau, saturation_collide), so the results are the same bit for bit.
-// --------------------------------------------------------------------------------------
-struct Quad {                 // a thread's four nodes in an inner row
-    int x0, o, lane;
-    bool in_row;              // the float4 lies inside the padded row
-    bool hl, hr;              // a node left of x0 / right of x0 + 3 exists in the lattice
-    bool fast;                // all four nodes interior
-};
-
-__device__ __forceinline__ Quad quad_at(const Geom &g, int t, int tiles_x)
-{
-    Quad q;
-    const int y = t / tiles_x;
-    q.x0 = ((t - y * tiles_x) * kBlock + (int)threadIdx.x) * 4;
-    q.o = y * g.pitch + q.x0;
-    q.lane = threadIdx.x & 31;
-    q.in_row = q.x0 < g.pitch;
-    q.hl = q.x0 >= 1 && q.in_row;
-    q.hr = q.x0 + 4 < g.nx;
-    q.fast = q.hl && q.x0 + 4 <= g.nx - 1;
-    return q;
-}
-
-__device__ __forceinline__ float4 ld4z(const float *p, int o, bool ok)
-{
-    return ok ? ld4(p, o) : make_float4(0.f, 0.f, 0.f, 0.f);
-}
-
-__device__ __forceinline__ float ld1z(const float *p, int o, bool ok)
-{
-    return ok ? __ldg(p + o) : 0.0f;
-}
-
-// g_0 .. g_8 pulled into the quad (inner row; every lane of the warp calls it)
-__device__ __forceinline__ void gather_g4(const float *const *gin, int qs, int p, const Quad &u,
-                                          float4 (&q)[9])
-{
-    const int o = u.o;
-    const bool l0 = u.lane == 0 && u.hl, l31 = u.lane == 31 && u.hr;
-    q[0] = ld4z(gin[0], o, u.in_row);
-    q[1] = shl(ld4z(gin[1], o, u.in_row), ld1z(gin[1], o - 1, l0), u.lane);
-    q[2] = ld4z(gin[2], o - p, u.in_row);
-    q[3] = shr(ld4z(gin[3], o, u.in_row), ld1z(gin[3], o + 4, l31), u.lane);
-    q[4] = ld4z(gin[4], o + p, u.in_row);
-    if (qs == 9) {
-        q[5] = shl(ld4z(gin[5], o - p, u.in_row), ld1z(gin[5], o - p - 1, l0), u.lane);
-        q[6] = shr(ld4z(gin[6], o - p, u.in_row), ld1z(gin[6], o - p + 4, l31), u.lane);
-        q[7] = shr(ld4z(gin[7], o + p, u.in_row), ld1z(gin[7], o + p + 4, l31), u.lane);
-        q[8] = shl(ld4z(gin[8], o + p, u.in_row), ld1z(gin[8], o + p - 1, l0), u.lane);
-    } else {
-        q[5] = q[6] = q[7] = q[8] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-}
-
-// a_1 .. a_8 (relative to R at each node, r0) pulled into the quad (inner row; every lane)
-__device__ __forceinline__ void gather_a4(const float *const *fin, const float *R, int p,
-                                          const Quad &u, float4 (&f)[8], float4 &r0)
-{
-    const int o = u.o;
-    const bool l0 = u.lane == 0 && u.hl, l31 = u.lane == 31 && u.hr;
-    const float4 rm = ld4z(R, o - p, u.in_row), rc = ld4z(R, o, u.in_row),
-                 rp = ld4z(R, o + p, u.in_row);
-    r0 = rc;
-    const float4 rl = shl(rc, ld1z(R, o - 1, l0), u.lane), rr = shr(rc, ld1z(R, o + 4, l31), u.lane);
-    const float4 rml = shl(rm, ld1z(R, o - p - 1, l0), u.lane),
-                 rmr = shr(rm, ld1z(R, o - p + 4, l31), u.lane);
-    const float4 rpl = shl(rp, ld1z(R, o + p - 1, l0), u.lane),
-                 rpr = shr(rp, ld1z(R, o + p + 4, l31), u.lane);
-    f[0] = dev4(shl(ld4z(fin[0], o, u.in_row), ld1z(fin[0], o - 1, l0), u.lane), wgt(1), rl, rc);
-    f[1] = dev4(ld4z(fin[1], o - p, u.in_row), wgt(2), rm, rc);
-    f[2] = dev4(shr(ld4z(fin[2], o, u.in_row), ld1z(fin[2], o + 4, l31), u.lane), wgt(3), rr, rc);
-    f[3] = dev4(ld4z(fin[3], o + p, u.in_row), wgt(4), rp, rc);
-    f[4] = dev4(shl(ld4z(fin[4], o - p, u.in_row), ld1z(fin[4], o - p - 1, l0), u.lane), wgt(5),
-                rml, rc);
-    f[5] = dev4(shr(ld4z(fin[5], o - p, u.in_row), ld1z(fin[5], o - p + 4, l31), u.lane), wgt(6),
-                rmr, rc);
-    f[6] = dev4(shr(ld4z(fin[6], o + p, u.in_row), ld1z(fin[6], o + p + 4, l31), u.lane), wgt(7),
-                rpr, rc);
-    f[7] = dev4(shl(ld4z(fin[7], o + p, u.in_row), ld1z(fin[7], o + p - 1, l0), u.lane), wgt(8),
-                rpl, rc);
-}
-
-__device__ __forceinline__ float el4(const float4 &v, int c) { return (&v.x)[c]; }
-
-__global__ void __launch_bounds__(kBlock, 2) k_refresh4(const __grid_constant__ RefreshArgs a)
-{
-    const Geom &g = a.g;
-    const int p = g.pitch;
-    const int tiles_x = (g.nx + 4 * kBlock - 1) / (4 * kBlock);
-    const int ntiles = tiles_x * g.ny;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const Quad u = quad_at(g, t, tiles_x);
-        const int y = t / tiles_x;
-        if (y > 0 && y < g.ny - 1) {                     // uniform over the block
-            float4 q[9];
-            gather_g4(a.gin, a.m.qs, p, u, q);
-            if (u.fast) {
-                const float4 K = ld4(a.K, u.o);
-                const float4 F = a.Fs ? ld4(a.Fs, u.o) : make_float4(0.f, 0.f, 0.f, 0.f);
-                float4 it;
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    float qc[9];
-#pragma unroll
-                    for (int i = 0; i < 9; ++i)
-                        qc[i] = el4(q[i], c);
-                    (&it.x)[c] = refresh_tau(a, u.o + c, qc, el4(K, c), el4(F, c));
-                }
-                st4(a.inv_tau, u.o, it);
-                if (a.Pstep_in) {
-                    const float4 r = ld4(a.Rin, u.o), pv = ld4(a.Pstep_in, u.o);
-                    st4(a.Rout, u.o, make_float4(r.x + (r.x - pv.x), r.y + (r.y - pv.y),
-                                                 r.z + (r.z - pv.z), r.w + (r.w - pv.w)));
-                    st4(a.Pstep_out, u.o, r);
-                } else if (a.Rout != a.Rin) {
-                    st4(a.Rout, u.o, ld4(a.Rin, u.o));
-                }
-                continue;
-            }
-        }
-        for (int c = 0; c < 4; ++c)
-            if (u.in_row && u.x0 + c < g.nx)
-                refresh_node(a, u.x0 + c, y, u.o + c);
-    }
-}
-
-__global__ void __launch_bounds__(kBlock, 2) k_saturation4(const __grid_constant__ SaturationArgs a)
-{
-    const Geom &g = a.g;
-    const int p = g.pitch;
-    const int qs = a.m.qs;
-    const int tiles_x = (g.nx + 4 * kBlock - 1) / (4 * kBlock);
-    const int ntiles = tiles_x * g.ny;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const Quad u = quad_at(g, t, tiles_x);
-        const int y = t / tiles_x;
-        if (y > 0 && y < g.ny - 1) {                     // uniform over the block
-            float4 f[8], q[9], r0;
-            gather_a4(a.fin, a.R, p, u, f, r0);
-            gather_g4(a.gin, qs, p, u, q);
-            if (u.fast) {
-                const float4 it = ld4(a.inv_tau, u.o), K = ld4(a.K, u.o);
-                const float4 F = a.Fs ? ld4(a.Fs, u.o) : make_float4(0.f, 0.f, 0.f, 0.f);
-                float4 P, S, go[9];
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    float fc[8], qc[9], gc[9];
-#pragma unroll
-                    for (int i = 0; i < 8; ++i)
-                        fc[i] = el4(f[i], c);
-#pragma unroll
-                    for (int i = 0; i < 9; ++i)
-                        qc[i] = el4(q[i], c);
-                    saturation_collide(a, u.o + c, fc, qc, el4(r0, c), el4(it, c), el4(K, c),
-                                       el4(F, c), (&P.x)[c], (&S.x)[c], gc);
-#pragma unroll
-                    for (int i = 0; i < 9; ++i)
-                        (&go[i].x)[c] = gc[i];
-                }
-                st4(a.Pnew, u.o, P);
-#pragma unroll
-                for (int i = 0; i < 9; ++i)
-                    if (i < qs)
-                        st4(a.gout[i], u.o, go[i]);
-                st4(a.S, u.o, S);
-                continue;
-            }
-        }
-        for (int c = 0; c < 4; ++c)
-            if (u.in_row && u.x0 + c < g.nx)
-                saturation_node(a, u.x0 + c, y, u.o + c);
-    }
-}
-
-// --------------------------------------------------------------------------------------
 // a6: initial g (Eqs. gini, gneq) followed by the t = 0 collision
 // --------------------------------------------------------------------------------------
 __device__ __forceinline__ float s_at(const float *S, const Geom &g, int x, int y)
@@ -1146,28 +966,14 @@ void residual_finalize(const double *partials, int nparts, long long nnodes, flo
     k_residual_finalize<<<1, 256, 0, S(stream)>>>(partials, nparts, nnodes, shift, out);
 }
 
-void refresh(const RefreshArgs &a, int grid, void *stream, bool quad)
+void refresh(const RefreshArgs &a, int grid, void *stream)
 {
-    if (quad)
-        k_refresh4<<<grid, kBlock, 0, S(stream)>>>(a);
-    else
-        k_refresh<<<grid, kBlock, 0, S(stream)>>>(a);
+    k_refresh<<<grid, kBlock, 0, S(stream)>>>(a);
 }
 
-void saturation(const SaturationArgs &a, int grid, void *stream, bool quad)
+void saturation(const SaturationArgs &a, int grid, void *stream)
 {
-    if (quad)
-        k_saturation4<<<grid, kBlock, 0, S(stream)>>>(a);
-    else
-        k_saturation<<<grid, kBlock, 0, S(stream)>>>(a);
-}
-
-int step_quad_blocks_per_sm()
-{
-    int b1 = 0, b2 = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_refresh4, kBlock, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_saturation4, kBlock, 0);
-    return b1 < b2 ? b1 : b2;
+    k_saturation<<<grid, kBlock, 0, S(stream)>>>(a);
 }
 
 void init_g(const InitGArgs &a, int grid, void *stream)
@@ -1277,18 +1083,17 @@ cudaError_t node_if_finite(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNod
 }
 
 cudaError_t node_refresh(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
-                         const RefreshArgs &a, int grid, bool quad)
+                         const RefreshArgs &a, int grid)
 {
     void *args[] = {(void *)&a};
-    return add_kernel(n, g, dep, quad ? (void *)k_refresh4 : (void *)k_refresh, grid, kBlock, args);
+    return add_kernel(n, g, dep, (void *)k_refresh, grid, kBlock, args);
 }
 
 cudaError_t node_saturation(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
-                            const SaturationArgs &a, int grid, bool quad)
+                            const SaturationArgs &a, int grid)
 {
     void *args[] = {(void *)&a};
-    return add_kernel(n, g, dep, quad ? (void *)k_saturation4 : (void *)k_saturation, grid, kBlock,
-                      args);
+    return add_kernel(n, g, dep, (void *)k_saturation, grid, kBlock, args);
 }
 
 cudaError_t node_rebase(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,

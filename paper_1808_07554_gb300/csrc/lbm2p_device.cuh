@@ -296,11 +296,8 @@ cudaError_t rows_h_prepare(int width, int slots);
 int rows_h_blocks_per_sm(int width, int slots, bool has_fp);
 void pressure_sweep_rows_h(const HalfSweepArgs &a, bool check, int width, int slots, int H,
                            int grid, void *stream);
-// a1 and a4 + a5: one node per thread (grid-stride over row tiles of kBlock nodes), or four
-// (quad: float4 rows, tiles of 4 kBlock nodes; blocks per SM from step_quad_blocks_per_sm)
-void refresh(const RefreshArgs &a, int grid, void *stream, bool quad = false);
-void saturation(const SaturationArgs &a, int grid, void *stream, bool quad = false);
-int step_quad_blocks_per_sm();
+void refresh(const RefreshArgs &a, int grid, void *stream);
+void saturation(const SaturationArgs &a, int grid, void *stream);
 void init_g(const InitGArgs &a, int grid, void *stream);
 void rebase(const RebaseArgs &a, int grid, void *stream);
 void tau_from_S(float *inv_tau, const float *S, const float *K, Geom g, Model m, int grid,
@@ -324,9 +321,9 @@ cudaError_t node_loop_reset(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNo
 cudaError_t node_if_finite(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
                            const LoopCtl *ctl, cudaGraphConditionalHandle h);
 cudaError_t node_refresh(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
-                         const RefreshArgs &a, int grid, bool quad = false);
+                         const RefreshArgs &a, int grid);
 cudaError_t node_saturation(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
-                            const SaturationArgs &a, int grid, bool quad = false);
+                            const SaturationArgs &a, int grid);
 cudaError_t node_rebase(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
                         const RebaseArgs &a, int grid);
 void sum_compact(const float *x, long long n, double *partials, int grid, void *stream);

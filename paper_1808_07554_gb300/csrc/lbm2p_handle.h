@@ -26,8 +26,6 @@ struct lbm2p {
     lbm2p_dev::Wells wells{};
     double s = 0, tau_g = 0, D_ref = 0;
     int grid = 0;              // blocks of every grid-stride lattice launch
-    bool step_quad = false;    // refresh and saturation four nodes per thread (timed at create)
-    int grid_quad = 0;         // their blocks then
     int grid_check = 0;        // blocks of a pressure sweep that accumulates the residual
     int sweep_kind = 0;        // single-sweep kernel: 0 = four nodes per thread, 1 = one
                                // node per thread, 2 = staged rows

@@ -206,10 +206,10 @@ __device__ __forceinline__ void mobility(const Model &m, float S, float &lw, flo
 }
 
 // dt F_s at node o: dense part plus wells; the producer uses S* = sum g / phi.
-__device__ __forceinline__ float source_at(const Model &m, const Wells &w, float Fdense, int o,
-                                           float Sstar)
+__device__ __forceinline__ float saturation_source(const Model &m, const Wells &w,
+                                                   const float *Fs, int o, float Sstar)
 {
-    float F = Fdense;
+    float F = Fs ? Fs[o] : 0.0f;
     for (int k = 0; k < w.n; ++k) {
         if (o == w.idx[k]) {
             if (w.producer[k]) {
@@ -222,12 +222,6 @@ __device__ __forceinline__ float source_at(const Model &m, const Wells &w, float
         }
     }
     return F;
-}
-
-__device__ __forceinline__ float saturation_source(const Model &m, const Wells &w,
-                                                   const float *Fs, int o, float Sstar)
-{
-    return source_at(m, w, Fs ? Fs[o] : 0.0f, o, Sstar);
 }
 
 __device__ __forceinline__ float warp_sum(float v)
@@ -316,23 +310,16 @@ __device__ __forceinline__ void extrapolate_node(const float *Rin, float *Rout,
 
 // a1: S^n (Eq. 3-9b) from the pulled g and 1/tau_f (Eq. 3-11a with D_p = K lambda_t(S)); with
 // a warm start also the extrapolation of the node's reference pressure for the coming solve
-// 1/tau_f at node o from the pulled g, K and the dense source there
-__device__ __forceinline__ float refresh_tau(const RefreshArgs &a, int o, const float (&q)[9],
-                                             float K, float Fdense)
-{
-    const float sum = (q[0] + ((q[1] + q[2]) + (q[3] + q[4]))) + ((q[5] + q[6]) + (q[7] + q[8]));
-    const float Fs = source_at(a.m, a.w, Fdense, o, sum * a.m.inv_phi);
-    const float S = (sum + 0.5f * Fs) * a.m.inv_phi;
-    float lw, lt;
-    mobility(a.m, S, lw, lt);
-    return 1.0f / (0.5f + a.m.s3 * K * lt);
-}
-
 __device__ __forceinline__ void refresh_node(const RefreshArgs &a, int x, int y, int o)
 {
     float q[9];
     gather_g(a.gin, a.g, a.m, a.Sb, x, y, o, q);
-    a.inv_tau[o] = refresh_tau(a, o, q, a.K[o], a.Fs ? a.Fs[o] : 0.0f);
+    const float sum = (q[0] + ((q[1] + q[2]) + (q[3] + q[4]))) + ((q[5] + q[6]) + (q[7] + q[8]));
+    const float Fs = saturation_source(a.m, a.w, a.Fs, o, sum * a.m.inv_phi);
+    const float S = (sum + 0.5f * Fs) * a.m.inv_phi;
+    float lw, lt;
+    mobility(a.m, S, lw, lt);
+    a.inv_tau[o] = 1.0f / (0.5f + a.m.s3 * a.K[o] * lt);
     if (a.Pstep_in)
         extrapolate_node(a.Rin, a.Rout, a.Pstep_in, a.Pstep_out, o);
     else if (a.Rout != a.Rin)
@@ -341,24 +328,25 @@ __device__ __forceinline__ void refresh_node(const RefreshArgs &a, int x, int y,
 
 // a4 + a5: local grad P (Eq. 3-10a), then the saturation collision (Eq. 3-2); also stores
 // S^n and the pressure of the pulled state (for the rebase)
-// the node arithmetic after the gathers: f pulled (relative to R(x) = r0), g pulled, 1/tau_f,
-// K and the dense source at node o give P, S^n and the post-collision g (entries >= qs unset)
-__device__ __forceinline__ void saturation_collide(const SaturationArgs &a, int o,
-                                                   const float (&f)[8], const float (&q)[9],
-                                                   float r0, float it, float K, float Fdense,
-                                                   float &P, float &S, float (&gout)[9])
+__device__ __forceinline__ void saturation_node(const SaturationArgs &a, int x, int y, int o)
 {
+    const Geom &g = a.g;
     const Model &m = a.m;
-    P = r0 + pressure_of(f);
+    float f[8], q[9];
+    gather_a(a.fin, a.R, g, a.Pb, x, y, o, f);
+    a.Pnew[o] = a.R[o] + pressure_of(f);
+    gather_g(a.gin, g, m, a.Sb, x, y, o, q);
     const float sum = (q[0] + ((q[1] + q[2]) + (q[3] + q[4]))) + ((q[5] + q[6]) + (q[7] + q[8]));
-    const float Fs = source_at(m, a.w, Fdense, o, sum * m.inv_phi);
-    S = (sum + 0.5f * Fs) * m.inv_phi;
+    const float Fs = saturation_source(m, a.w, a.Fs, o, sum * m.inv_phi);
+    const float S = (sum + 0.5f * Fs) * m.inv_phi;
     // grad_X P = -3 sum_i c_i f_i / tau_f  (lattice units, Eq. 3-10a)
     float mx, my;
     first_moment(f, mx, my);
+    const float it = a.inv_tau[o];
     const float gx = -3.0f * mx * it, gy = -3.0f * my * it;
     float lw, lt;
     mobility(m, S, lw, lt);
+    const float K = a.K[o];
     float inv_tg, src_g;
     tau_g_node(m, K, lw, lt, inv_tg, src_g);
     // gamma~ = -3 lambda_w K dt / dx^2 (Eq. 3-8 in lattice units), pre-divided by tau_g
@@ -371,22 +359,7 @@ __device__ __forceinline__ void saturation_collide(const SaturationArgs &a, int 
         const float wi = m.wg[i];
         const float cg = (float)cx(i) * gx + (float)cy(i) * gy;
         const float eq = m.Gam[i] * S;
-        gout[i] = fmaf(eq - q[i], inv_tg, q[i]) + wi * src + gam * wi * cg;
-    }
-}
-
-__device__ __forceinline__ void saturation_node(const SaturationArgs &a, int x, int y, int o)
-{
-    float f[8], q[9], go[9], P, S;
-    gather_a(a.fin, a.R, a.g, a.Pb, x, y, o, f);
-    gather_g(a.gin, a.g, a.m, a.Sb, x, y, o, q);
-    saturation_collide(a, o, f, q, a.R[o], a.inv_tau[o], a.K[o], a.Fs ? a.Fs[o] : 0.0f, P, S, go);
-    a.Pnew[o] = P;
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        if (i >= a.m.qs)
-            break;
-        a.gout[i][o] = go[i];
+        a.gout[i][o] = fmaf(eq - q[i], inv_tg, q[i]) + wi * src + gam * wi * cg;
     }
     a.S[o] = S;
 }

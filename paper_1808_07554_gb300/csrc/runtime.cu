@@ -267,12 +267,6 @@ lbm2p_status upload_trace(lbm2p *h, float *dst, const double *src, int n)
     return LBM2P_OK;
 }
 
-// blocks of the refresh and saturation launches (one or four nodes per thread)
-int step_grid(const lbm2p *h)
-{
-    return h->step_quad ? h->grid_quad : h->grid;
-}
-
 // ---- single pressure sweeps with the kernel chosen at create ---------------------------
 void launch_sweep(lbm2p *h, const PressureArgs &a, bool check, bool write_p)
 {
@@ -425,8 +419,7 @@ lbm2p_status step_graph(lbm2p *h, int pin, int pg, cudaGraphExec_t *out)
         CUDA_TRY(h, cudaGraphCreate(&G, 0));
         h->step_g[pin][pg][r] = G;
         cudaGraphNode_t nr, last, nf, ifn, ns, nb;
-        CUDA_TRY(h, lbm2p_launch::node_refresh(&nr, G, nullptr, refresh_args(h, pg, false),
-                                               step_grid(h), h->step_quad));
+        CUDA_TRY(h, lbm2p_launch::node_refresh(&nr, G, nullptr, refresh_args(h, pg, false), h->grid));
         lbm2p_status e = add_loop(h, G, &nr, pin, true, &last);
         if (e != LBM2P_OK)
             return e;
@@ -442,8 +435,7 @@ lbm2p_status step_graph(lbm2p *h, int pin, int pg, cudaGraphExec_t *out)
         cudaGraph_t tail = ip.conditional.phGraph_out[0];
         const int pout = fnext(pin, 2);
         CUDA_TRY(h, lbm2p_launch::node_saturation(&ns, tail, nullptr,
-                                                  saturation_args(h, pout, pg, true), step_grid(h),
-                                                  h->step_quad));
+                                                  saturation_args(h, pout, pg, true), h->grid));
         CUDA_TRY(h, lbm2p_launch::node_rebase(&nb, tail, &ns, rebase_args(h, pout, true), h->grid));
         CUDA_TRY(h, cudaGraphInstantiate(&h->step_x[pin][pg][r], G, 0));
     }
@@ -889,7 +881,7 @@ lbm2p_status one_step(lbm2p *h, int replay, lbm2p_step_stats *stats)
     if (h->timing)
         CUDA_TRY(h, cudaEventRecord(h->ev_step0, st));
     // a1: stream g, S^n, tau_f (and the warm start) into the work buffers
-    lbm2p_launch::refresh(refresh_args(h, h->cur_g, false), step_grid(h), h->stream, h->step_quad);
+    lbm2p_launch::refresh(refresh_args(h, h->cur_g, false), h->grid, h->stream);
     LAUNCHED(h, "refresh");
     // a2/a3: pressure sub-iteration
     int k = 0, pout = h->cur_f;
@@ -901,8 +893,7 @@ lbm2p_status one_step(lbm2p *h, int replay, lbm2p_step_stats *stats)
         return ps;
     }
     // a4/a5: grad P and the saturation update
-    lbm2p_launch::saturation(saturation_args(h, pout, h->cur_g, true), step_grid(h), h->stream,
-                             h->step_quad);
+    lbm2p_launch::saturation(saturation_args(h, pout, h->cur_g, true), h->grid, h->stream);
     LAUNCHED(h, "saturation");
     lbm2p_launch::rebase(rebase_args(h, pout, true), h->grid, h->stream);
     LAUNCHED(h, "rebase");
@@ -1000,59 +991,6 @@ lbm2p_status check_params(const lbm2p_params *p, const lbm2p_inputs *in)
 // counts.  Runs on the zeroed buffers before initialisation; they are zeroed again after.
 // a fused form must take at most this fraction of the best single sweep's time per sweep
 constexpr float kFusedMargin = 0.95f;
-
-// The per-step kernels a1 (refresh) and a4 + a5 (saturation) with one node per thread or four:
-// both timed on this lattice (buffers as they are; zeroed afterwards), the faster kept.  The
-// two compute the same values bit for bit.
-lbm2p_status autotune_step(lbm2p *h, int sms)
-{
-    cudaStream_t st = (cudaStream_t)h->stream;
-    h->step_quad = false;
-    const int per = lbm2p_launch::step_quad_blocks_per_sm();
-    const long long tiles = (long long)((h->nx + 4 * kBlock - 1) / (4 * kBlock)) * h->ny;
-    long long gq = (long long)sms * (per > 0 ? per : 1);
-    h->grid_quad = (int)(gq < tiles ? gq : tiles);
-    if (per < 1 || h->grid < 1 || h->nx < 8 || h->ny < 3)
-        return LBM2P_OK;
-    cudaEvent_t e0, e1;
-    CUDA_TRY(h, cudaEventCreate(&e0));
-    CUDA_TRY(h, cudaEventCreate(&e1));
-    float best[2] = {1e30f, 1e30f};
-    const RefreshArgs ra = refresh_args(h, 0, false);
-    const SaturationArgs sa = saturation_args(h, 0, 0, false);
-    for (int trial = 0; trial < 3; ++trial)
-        for (int quad = 0; quad < 2; ++quad) {
-            const int grid = quad ? h->grid_quad : h->grid;
-            cudaEventRecord(e0, st);
-            for (int rep = 0; rep < 4; ++rep) {
-                lbm2p_launch::refresh(ra, grid, h->stream, quad != 0);
-                lbm2p_launch::saturation(sa, grid, h->stream, quad != 0);
-            }
-            cudaEventRecord(e1, st);
-            cudaError_t e = cudaEventSynchronize(e1);
-            float ms = 0.0f;
-            if (e == cudaSuccess)
-                e = cudaEventElapsedTime(&ms, e0, e1);
-            if (e != cudaSuccess) {
-                cudaEventDestroy(e0);
-                cudaEventDestroy(e1);
-                return fail(h, LBM2P_ECUDA, "step kernel timing failed: %s", cudaGetErrorString(e));
-            }
-            if (trial > 0)                               // the first round warms up
-                best[quad] = ms < best[quad] ? ms : best[quad];
-        }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    h->step_quad = best[1] < best[0];
-    char line[160];
-    snprintf(line, sizeof line, "step_kernels %d %d %d 0 %.3f\nstep_kernels_quad %d %d %d 0 %.3f\n",
-             h->grid, kBlock, 1, best[0] * 250.0f, h->grid_quad, kBlock, 4, best[1] * 250.0f);
-    h->autotune_log += line;
-    for (auto &a : h->allocs)
-        CUDA_TRY(h, cudaMemsetAsync(a.ptr, 0, a.bytes, st));
-    CUDA_TRY(h, cudaStreamSynchronize(st));
-    return LBM2P_OK;
-}
 
 lbm2p_status autotune_sweeps(lbm2p *h)
 {
@@ -1668,11 +1606,6 @@ lbm2p_status build(lbm2p *h, const lbm2p_inputs *in, lbm2p_step_stats *init_stat
     // grid-stride lattice kernels keep the one-node-per-thread capacity when the staged
     // sweep is chosen
     h->grid = h->grid_cap_k[h->sweep_kind < 2 ? h->sweep_kind : 1];
-    {
-        lbm2p_status e = autotune_step(h, sms);
-        if (e != LBM2P_OK)
-            return e;
-    }
     h->grid_sweep = h->grid_k[h->sweep_kind < 2 ? h->sweep_kind : 1];
     h->grid_check = h->grid_check_k[h->sweep_kind < 2 ? h->sweep_kind : 1];
     {
