@@ -89,6 +89,12 @@ FUSED_FORM_TEXT = {1: "on shared-memory stages", 2: "on rows staged by bulk copi
                    3: "with direct loads"}
 
 
+def log(msg: str) -> None:
+    """Progress of the set-up and of long phases, on stderr (the JSON line stays alone on
+    stdout)."""
+    print(f"[bench {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
+
+
 def kernel_source_hash(form: str) -> str:
     import hashlib
     h = hashlib.sha256()
@@ -599,7 +605,8 @@ def run_batch(args):
     stream = torch.cuda.current_stream()
     t_setup = time.perf_counter()
     solvers, init_sweeps = [], 0
-    for p in probs:
+    for i, p in enumerate(probs):
+        t_m = time.perf_counter()
         if not args.cold_start:
             P0 = coarse_initial_pressure(p, pkg)
             if P0 is not None:
@@ -610,11 +617,16 @@ def run_batch(args):
                                     warm_start=1 if args.warm_start == "extrapolate" else 0)
         init_sweeps += s.init_stats.sub_iters
         solvers.append(s)
+        log(f"member {i}: {p.nx}x{p.ny}, t = 0 solve {s.init_stats.sub_iters} sweeps, "
+            f"{time.perf_counter() - t_m:.1f} s")
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t_setup
     batch = pkg.Batch(solvers)
-    for _ in range(args.warmup):
-        batch.step(1)
+    for w in range(args.warmup):
+        t_w = time.perf_counter()
+        st, stats = batch.step(1)
+        log(f"warm-up step {w}: {time.perf_counter() - t_w:.2f} s, status {st}, "
+            f"sweeps max {max(x.sub_iters for x in stats[0])}")
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -662,6 +674,7 @@ def run_batch(args):
     e2e_s = time.perf_counter() - t0
     batch.close()
 
+    log(f"batched steps done: {total_ms / 1e3:.2f} s device time, e2e {e2e_s:.2f} s")
     # the same members one after another (each its own graph-resident step)
     seq_steps = max(1, min(args.steps, 3))
     seq_updates = 0
@@ -674,6 +687,7 @@ def run_batch(args):
     ev1.record(stream)
     ev1.synchronize()
     seq_s = ev0.elapsed_time(ev1) / 1e3
+    log(f"one member at a time: {seq_steps} steps in {seq_s:.2f} s")
     for s in solvers:
         s.close()
 
