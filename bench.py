@@ -398,6 +398,10 @@ def run_ours(args):
                                      warm_start=1 if args.warm_start == "extrapolate" else 0)
     torch.cuda.synchronize()
     create_s = time.perf_counter() - t_create
+    if args.fused_shape:
+        # a two-sweep launch shape pinned for the steps (the t = 0 solve ran the tuned one)
+        form, warps, slots, rows = (int(v) for v in args.fused_shape.split(","))
+        solver.set_fused_shape(form, warps, slots, rows)
     do_step = lambda: solver.step(1)          # noqa: E731
     if args.warm_start == "learned":
         from paper_1808_07554_gb300.operator import LearnedWarmStart
@@ -523,6 +527,7 @@ def run_ours(args):
                    "check_every": args.check_every, "fuse_sweeps": args.fuse_sweeps,
                    "sweep_kernel": sweep_cfg[1], "sweep_tile": [sweep_cfg[2], sweep_cfg[3]],
                    "fused_form": FUSED_FORM_NAMES.get(fform, "none"),
+                   "fused_shape_pinned": args.fused_shape,
                    "autotune_best": autotune_best,
                    "l2": "flushed before every timed step (256 MB write)",
                    "sub_iters_per_step": ksub, "sub_iters_histogram": hist,
@@ -767,6 +772,9 @@ def main():
                     help="pressure populations during the sub-iteration: FP32 or FP16 deviations")
     ap.add_argument("--tol", type=float, default=1e-8,
                     help="relative increment that ends a pressure solve")
+    ap.add_argument("--fused-shape", default=None,
+                    help="form,warps,slots,rows: pin the two-sweep launch shape of the steps "
+                         "(lbm2p_set_fused_shape; form 2 = staged rows, 3 = direct loads)")
     ap.add_argument("--sweep-kernel", type=int, default=0, choices=[0, 1, 2, 3],
                     help="single-sweep kernel: 0 = autotuned, 1 = float4, 2 = one node per "
                          "thread, 3 = staged rows")

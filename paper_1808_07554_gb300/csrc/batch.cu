@@ -44,10 +44,10 @@ struct Member {
     int wshift, rpt, seg_x;      // segment width 2^wshift, rows per tile, segments per row
     int tile0, ntiles;           // range in the batch tile list
     // A member of 512^2 nodes or more whose handle sweeps two at a time ("own" member) runs
-    // its handle's own two-sweep launches in a branch of the loop body, under an IF node (its
-    // handle in the graph's array of own-member handles, by member index), instead of joining
-    // the batched sweep; its residual partials are then the handle's (nparts of them),
-    // otherwise the batch's own, one per tile.
+    // its handle's own two-sweep launches in a branch of the loop body instead of joining the
+    // batched sweep; the launches read the member's active flag and return at once after it
+    // has converged.  Its residual partials are then the handle's (nparts of them), otherwise
+    // the batch's own, one per tile.
     int own;
     const double *pparts;
     int nparts;
@@ -84,9 +84,8 @@ __global__ void __launch_bounds__(kBlock) kb_refresh(const Member *__restrict__ 
     }
 }
 
-__global__ void kb_reset(const Member *__restrict__ mem, MemberCtl *ctl,
-                         const int *__restrict__ caps, const double *__restrict__ tols, int count,
-                         int *active_count, const cudaGraphConditionalHandle *__restrict__ hown)
+__global__ void kb_reset(MemberCtl *ctl, const int *__restrict__ caps,
+                         const double *__restrict__ tols, int count, int *active_count)
 {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m == 0)
@@ -98,9 +97,25 @@ __global__ void kb_reset(const Member *__restrict__ mem, MemberCtl *ctl,
         ctl[m].active = caps[m] > 0 ? 1 : 0;
         ctl[m].rebase = 0;
         ctl[m].r = nan("");
-        if (mem[m].own)
-            cudaGraphSetConditional(hown[m], caps[m] > 0 ? 1u : 0u);
     }
+}
+
+// First node of a loop body: the IF node around the own members' launches runs while one of
+// them is still active.
+__global__ void __launch_bounds__(256) kb_own_if(const Member *__restrict__ mem,
+                                                 const MemberCtl *__restrict__ ctl, int count,
+                                                 cudaGraphConditionalHandle h)
+{
+    __shared__ int any;
+    if (threadIdx.x == 0)
+        any = 0;
+    __syncthreads();
+    for (int m = threadIdx.x; m < count; m += blockDim.x)
+        if (mem[m].own && ctl[m].active)
+            any = 1;
+    __syncthreads();
+    if (threadIdx.x == 0)
+        cudaGraphSetConditional(h, any ? 1u : 0u);
 }
 
 // Sweep number idx (0-based) of a loop body over the tiles of the still-active members:
@@ -151,8 +166,7 @@ __global__ void __launch_bounds__(kBlock) kb_sweep(const Member *__restrict__ me
 // the members still active, counts[1] those to rebase.
 __global__ void __launch_bounds__(256) kb_finalize(const Member *__restrict__ mem,
                                                    const double *__restrict__ partials,
-                                                   MemberCtl *ctl, int body, int *counts,
-                                                   const cudaGraphConditionalHandle *__restrict__ hown)
+                                                   MemberCtl *ctl, int body, int *counts)
 {
     const int mi = blockIdx.x;
     MemberCtl &c = ctl[mi];
@@ -198,8 +212,6 @@ __global__ void __launch_bounds__(256) kb_finalize(const Member *__restrict__ me
         const bool rebase = more && M.every > 0 && c.k % M.every == 0;
         c.active = more ? 1 : 0;
         c.rebase = rebase ? 1 : 0;
-        if (M.own)
-            cudaGraphSetConditional(hown[mi], more ? 1u : 0u);
         if (more)
             atomicAdd(&counts[0], 1);
         if (rebase)
@@ -323,7 +335,6 @@ struct lbm2p_batch {
     int *d_prefix = nullptr;             // first compacted tile of each active member
     int2 *d_act = nullptr;               // compacted (member, tile) list
     double *d_partials = nullptr;
-    cudaGraphConditionalHandle *d_hown[2] = {};   // per graph: IF handle of each own member
     std::vector<lbm2p *> own_h;          // the handles of the own members (index = member)
     cudaGraph_t graph[2] = {};
     cudaGraphExec_t exec[2] = {};
@@ -372,8 +383,6 @@ void batch_free(lbm2p_batch *b)
     cudaFree(b->d_prefix);
     cudaFree(b->d_act);
     cudaFree(b->d_partials);
-    cudaFree(b->d_hown[0]);
-    cudaFree(b->d_hown[1]);
     if (b->h_ctl)
         cudaFreeHost(b->h_ctl);
     if (b->h_caps)
@@ -432,21 +441,15 @@ lbm2p_status build_graph(lbm2p_batch *b, int q)
         void *args[] = {(void *)&mem, (void *)&tm, (void *)&total, (void *)&q};
         BTRY(b, add_k(&nr, G, nullptr, (void *)kb_refresh, b->grid, kBlock, args));
     }
-    // IF handles of the own members (created in the step graph, used inside the loop body)
-    std::vector<cudaGraphConditionalHandle> hown((size_t)count, cudaGraphConditionalHandle{});
-    for (int m = 0; m < count; ++m)
-        if (b->own_h[(size_t)m])
-            BTRY(b, cudaGraphConditionalHandleCreate(&hown[(size_t)m], G, 0, 0));
-    BTRY(b, cudaMemcpy(b->d_hown[q], hown.data(), sizeof(cudaGraphConditionalHandle) * (size_t)count,
-                       cudaMemcpyHostToDevice));
-    const cudaGraphConditionalHandle *chown = b->d_hown[q];
     {
-        void *args[] = {(void *)&mem, (void *)&ctl, (void *)&caps, (void *)&tols, (void *)&count,
-                        (void *)&act, (void *)&chown};
+        void *args[] = {(void *)&ctl, (void *)&caps, (void *)&tols, (void *)&count, (void *)&act};
         BTRY(b, add_k(&nreset, G, &nr, (void *)kb_reset, (count + 255) / 256, 256, args));
     }
     cudaGraphConditionalHandle hd, hnone{};
     BTRY(b, cudaGraphConditionalHandleCreate(&hd, G, 1, cudaGraphCondAssignDefault));
+    bool any_own = false;
+    for (int m = 0; m < count; ++m)
+        any_own = any_own || b->own_h[(size_t)m] != nullptr;
     {
         void *args[] = {(void *)&mem, (void *)&cctl, (void *)&count, (void *)&prefix,
                         (void *)&act, (void *)&hnone, (void *)&hnone};
@@ -474,25 +477,40 @@ lbm2p_status build_graph(lbm2p_batch *b, int q)
                       check ? b->grid_check : b->grid, kBlock, args));
         prev = n;
     }
-    // the own members' two-sweep launches, each under its IF node, beside the batched sweeps
+    // the own members' two-sweep launches, one chain per member beside the batched sweeps;
+    // each launch reads the member's active flag and does nothing once it has converged
+    // one IF node around all own members' launches, set at the top of the body by kb_own_if,
+    // so that they stop launching once every own member has converged
     std::vector<cudaGraphNode_t> ends{prev};
+    cudaGraph_t og = nullptr;
+    if (any_own) {
+        cudaGraphConditionalHandle hown;
+        BTRY(b, cudaGraphConditionalHandleCreate(&hown, bg, 0, 0));
+        cudaGraphNode_t nset, nown;
+        {
+            void *args[] = {(void *)&mem, (void *)&cctl, (void *)&count, (void *)&hown};
+            BTRY(b, add_k(&nset, bg, nullptr, (void *)kb_own_if, 1, 256, args));
+        }
+        cudaGraphNodeParams op{};
+        op.type = cudaGraphNodeTypeConditional;
+        op.conditional.handle = hown;
+        op.conditional.type = cudaGraphCondTypeIf;
+        op.conditional.size = 1;
+        BTRY(b, cudaGraphAddNode(&nown, bg, &nset, nullptr, 1, &op));
+        og = op.conditional.phGraph_out[0];
+        ends.push_back(nown);
+    }
     for (int m = 0; m < count; ++m) {
         lbm2p *h = b->own_h[(size_t)m];
         if (!h)
             continue;
-        cudaGraphNodeParams ip{};
-        ip.type = cudaGraphNodeTypeConditional;
-        ip.conditional.handle = hown[(size_t)m];
-        ip.conditional.type = cudaGraphCondTypeIf;
-        ip.conditional.size = 1;
-        cudaGraphNode_t nifm;
-        BTRY(b, cudaGraphAddNode(&nifm, bg, nullptr, nullptr, 0, &ip));
-        cudaGraph_t ig = ip.conditional.phGraph_out[0];
+        cudaGraph_t ig = og;
         const int A = h->cur_f, B = lbm2p_internal::fnext(A, 1);
         cudaGraphNode_t p2 = nullptr;
         int src = A;
         for (int kk = 2; kk <= body; kk += 2) {
             PressureArgs a = lbm2p_internal::pressure_args(h, src, src == A ? B : A, false);
+            a.live = &b->d_ctl[m].active;
             cudaGraphNode_t n;
             const bool chk = kk == body;
             if (h->tb_kind == 2)
@@ -508,12 +526,10 @@ lbm2p_status build_graph(lbm2p_batch *b, int q)
             p2 = n;
             src = src == A ? B : A;
         }
-        ends.push_back(nifm);
     }
     cudaGraphNode_t nf, nc, nsc2, nif, nrm;
     {
-        void *args[] = {(void *)&mem, (void *)&cpartials, (void *)&ctl, (void *)&body, (void *)&act,
-                        (void *)&chown};
+        void *args[] = {(void *)&mem, (void *)&cpartials, (void *)&ctl, (void *)&body, (void *)&act};
         cudaKernelNodeParams kp{};
         kp.func = (void *)kb_finalize;
         kp.gridDim = dim3((unsigned)count);
@@ -673,10 +689,6 @@ lbm2p_status lbm2p_batch_create(lbm2p_batch **out, lbm2p *const *members, int co
             ok(cudaMalloc(&b->d_prefix, sizeof(int) * (size_t)count), "cudaMalloc") &&
             ok(cudaMalloc(&b->d_act, sizeof(int2) * (size_t)total), "cudaMalloc") &&
             ok(cudaMalloc(&b->d_partials, sizeof(double) * 4 * (size_t)total), "cudaMalloc") &&
-            ok(cudaMalloc(&b->d_hown[0], sizeof(cudaGraphConditionalHandle) * (size_t)count),
-               "cudaMalloc") &&
-            ok(cudaMalloc(&b->d_hown[1], sizeof(cudaGraphConditionalHandle) * (size_t)count),
-               "cudaMalloc") &&
             ok(cudaMallocHost(&b->h_ctl, sizeof(MemberCtl) * (size_t)count), "cudaMallocHost") &&
             ok(cudaMallocHost(&b->h_caps, sizeof(int) * (size_t)count), "cudaMallocHost") &&
             ok(cudaMallocHost(&b->h_tols, sizeof(double) * (size_t)count), "cudaMallocHost") &&
@@ -782,9 +794,16 @@ lbm2p_status lbm2p_batch_step(lbm2p_batch *b, int nsteps, const int *replay,
         const int passes = kmax > 0 ? kmax / b->body : 1;
         const int every = b->body * ((1024 + b->body - 1) / b->body);
         b->launches += 6 + (long long)passes * (b->body + 3) + (kmax > 0 ? (kmax - 1) / every : 0);
-        for (int m = 0; m < b->count; ++m)     // own members: two sweeps per launch
-            if (b->own_h[(size_t)m])
-                b->launches += b->h_ctl[m].k / 2;
+        // own members: kb_own_if every pass, and body / 2 launches each in every pass while
+        // one of them is still active
+        int kown = 0, nown = 0;
+        for (int m = 0; m < b->count; ++m)
+            if (b->own_h[(size_t)m]) {
+                ++nown;
+                kown = b->h_ctl[m].k > kown ? b->h_ctl[m].k : kown;
+            }
+        if (nown > 0)
+            b->launches += passes + (long long)(kown / b->body) * (b->body / 2) * nown;
         if (worst == LBM2P_ENONFINITE)
             return bfail(b, worst, "a member's pressure residual is not finite (step %d)", s);
     }

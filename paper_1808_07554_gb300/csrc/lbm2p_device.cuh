@@ -101,6 +101,10 @@ struct PressureArgs {
     const float *Pb[4];      // Dirichlet traces (device FP32) or nullptr
     Geom g;
     Wells w;
+    // a batch member's "still sub-iterating" flag, or nullptr: the two-sweep kernels do
+    // nothing when it is 0 (the launch stays in the batch's loop body after the member met
+    // its tolerance)
+    const int *live;
 };
 
 struct RefreshArgs {        // stream g, S^n, 1/tau_f (and the warm start of the next solve)

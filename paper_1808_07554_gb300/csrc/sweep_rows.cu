@@ -427,6 +427,8 @@ template <bool CHECK, int CW, int S, int MINB>
 __global__ void __launch_bounds__(32 * (CW + 1), MINB) k_pressure_rows2(const __grid_constant__ PressureArgs a,
                                                                   int H)
 {
+    if (a.live && *a.live == 0)                       // a converged batch member
+        return;
     constexpr int W = 30 * CW;
     constexpr int RW = W + 2 * kRowsHalo;          // floats per staged plane row
     const int npl = a.Fp ? 11 : 10;
@@ -760,6 +762,8 @@ template <bool CHECK, int CW>
 __global__ void __launch_bounds__(32 * CW) k_pressure_pair_direct(const __grid_constant__ PressureArgs a,
                                                                  int H)
 {
+    if (a.live && *a.live == 0)                       // a converged batch member
+        return;
     constexpr int W = 30 * CW;
     __shared__ double red[CW][4];
     const Geom &g = a.g;
