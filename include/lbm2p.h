@@ -281,7 +281,8 @@ int lbm2p_fused_form_of(const lbm2p *h);
    warps and 6 slots with the register cap that keeps seven plain blocks per SM; rows 16, 32, 64
    or 128) or DIRECT (warps 4 or 8, slots 0, rows 2, 4, 8, 16 or 32); rows above ny mean ny.
    Every shape computes the same populations bit for bit; only the speed differs.  The lattice
-   needs walls on every side and FP32 storage, and check_every a multiple of 4.  Waits for the
+   needs walls on every side and FP32 storage (the graph-resident loop uses the shape when
+   check_every is a multiple of 4, the host-driven loop always).  Waits for the
    handle's stream and drops its solve graphs (rebuilt on the next solve); a batch created
    before keeps the shape it was built with.  EINVAL (handle unchanged) for any other value. */
 #define LBM2P_ROWS2_DENSE 16

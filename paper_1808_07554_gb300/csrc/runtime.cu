@@ -2055,9 +2055,6 @@ lbm2p_status lbm2p_set_fused_shape(lbm2p *h, int form, int warps, int slots, int
     for (int sd = 0; sd < 4; ++sd)
         if (h->p.bc[sd] == LBM2P_BC_PERIODIC)
             return fail(h, LBM2P_EINVAL, "the two-sweep row-walking kernels need walls on every side");
-    if (h->p.check_every % 4 != 0)
-        return fail(h, LBM2P_EINVAL, "check_every %d is not a multiple of 4 (two launches of two "
-                    "sweeps per loop body at least)", h->p.check_every);
     // rows per block: a size the create-time tuning tries (clamped to ny as it is there)
     auto rows_ok = [&](std::initializer_list<int> tried) {
         for (int H : tried)
@@ -2090,7 +2087,10 @@ lbm2p_status lbm2p_set_fused_shape(lbm2p *h, int form, int warps, int slots, int
                     h->partials_cap);
     CUDA_TRY(h, cudaStreamSynchronize((cudaStream_t)h->stream));
     drop_graphs(h);
-    h->tb_T = h->tb_T_graph = 2;
+    h->tb_T = 2;
+    // as at create: the graph loop body runs the fused launches only when check_every is a
+    // multiple of 2 T (an even number of launches per body)
+    h->tb_T_graph = h->p.check_every % 4 == 0 ? 2 : 0;
     h->tb_kind = form == LBM2P_FUSED_STAGED_ROWS ? 1 : 2;
     h->tb_W = 30 * warps;
     h->tb_slots = form == LBM2P_FUSED_STAGED_ROWS ? slots : 0;

@@ -295,11 +295,11 @@ def test_full_size_4096_sweeps(storage):
     orc = O.Oracle(prob, init_replay=0)
     w = np.array([1 / 9] * 4 + [1 / 36] * 4)
     f = n.astype(np.float64) + w[:, None, None] * R.astype(np.float64)[None]
-    del n, g
+    del n
     orc.set_state(f=np.concatenate([np.zeros((1,) + f.shape[1:]), f]),
-                  g=gpu.get_state()[8:17].astype(np.float64),
+                  g=g.astype(np.float64),
                   tau_f=1.0 / inv_tau.astype(np.float64), S=S.astype(np.float64))
-    del f
+    del f, g
     tol = 2e-3 if storage == "fp16" else 2e-6
     for sweeps in (1, 2):
         gpu.pressure_sweeps(sweeps)
