@@ -43,12 +43,13 @@ struct Member {
     int every;                   // sweeps between mid-solve rebases
     int wshift, rpt, seg_x;      // segment width 2^wshift, rows per tile, segments per row
     int tile0, ntiles;           // range in the batch tile list
-    // A member of 512^2 nodes or more whose handle sweeps two at a time ("own" member) runs
-    // its handle's own two-sweep launches in a branch of the loop body instead of joining the
-    // batched sweep; the launches read the member's active flag and return at once after it
-    // has converged.  Its residual partials are then the handle's (nparts of them), otherwise
-    // the batch's own, one per tile.
+    // A member of 512^2 nodes or more on a lattice with walls on every side ("pair" member)
+    // is swept two sweeps per launch by k_pair_batch (blocks of 120 columns x h2 rows, nb2 of
+    // them, residual partials at pb0 in the pair partials) instead of joining the one-sweep
+    // batched sweep.  pparts / nparts: where finalize finds the member's residual partials
+    // (the pair partials, or the batch's per-tile ones).
     int own;
+    int h2, nb2, pb0;
     const double *pparts;
     int nparts;
 };
@@ -98,24 +99,6 @@ __global__ void kb_reset(MemberCtl *ctl, const int *__restrict__ caps,
         ctl[m].rebase = 0;
         ctl[m].r = nan("");
     }
-}
-
-// First node of a loop body: the IF node around the own members' launches runs while one of
-// them is still active.
-__global__ void __launch_bounds__(256) kb_own_if(const Member *__restrict__ mem,
-                                                 const MemberCtl *__restrict__ ctl, int count,
-                                                 cudaGraphConditionalHandle h)
-{
-    __shared__ int any;
-    if (threadIdx.x == 0)
-        any = 0;
-    __syncthreads();
-    for (int m = threadIdx.x; m < count; m += blockDim.x)
-        if (mem[m].own && ctl[m].active)
-            any = 1;
-    __syncthreads();
-    if (threadIdx.x == 0)
-        cudaGraphSetConditional(h, any ? 1u : 0u);
 }
 
 // Sweep number idx (0-based) of a loop body over the tiles of the still-active members:
@@ -228,8 +211,8 @@ __global__ void __launch_bounds__(256) kb_prefix(const Member *__restrict__ mem,
                                                  cudaGraphConditionalHandle h_loop,
                                                  cudaGraphConditionalHandle h_rebase)
 {
-    __shared__ int scan[256];
-    __shared__ int carry;
+    __shared__ int scan[2][256];
+    __shared__ int carry[2];
     if (threadIdx.x == 0) {
         if (SET) {
             const int active = counts[0], rebase = counts[1];
@@ -237,44 +220,57 @@ __global__ void __launch_bounds__(256) kb_prefix(const Member *__restrict__ mem,
             cudaGraphSetConditional(h_loop, active > 0 ? 1u : 0u);
             cudaGraphSetConditional(h_rebase, rebase > 0 ? 1u : 0u);
         }
-        carry = 0;
+        carry[0] = carry[1] = 0;
     }
     __syncthreads();
+    // two exclusive prefixes at once: tiles of the one-sweep members, blocks of the pair
+    // members (a member is one or the other, so one prefix array holds both)
     for (int base = 0; base < count; base += 256) {
         const int m = base + (int)threadIdx.x;
-        const int v = (m < count && ctl[m].active && !mem[m].own) ? mem[m].ntiles : 0;
-        scan[threadIdx.x] = v;
+        const bool on = m < count && ctl[m].active;
+        const int pair = on && mem[m].own;
+        const int v = on ? (pair ? mem[m].nb2 : mem[m].ntiles) : 0;
+        scan[0][threadIdx.x] = pair ? 0 : v;
+        scan[1][threadIdx.x] = pair ? v : 0;
         __syncthreads();
-        for (int off = 1; off < 256; off <<= 1) {        // inclusive scan
-            const int add = (int)threadIdx.x >= off ? scan[threadIdx.x - off] : 0;
+        for (int off = 1; off < 256; off <<= 1) {        // inclusive scans
+            const int a0 = (int)threadIdx.x >= off ? scan[0][threadIdx.x - off] : 0;
+            const int a1 = (int)threadIdx.x >= off ? scan[1][threadIdx.x - off] : 0;
             __syncthreads();
-            scan[threadIdx.x] += add;
+            scan[0][threadIdx.x] += a0;
+            scan[1][threadIdx.x] += a1;
             __syncthreads();
         }
         if (m < count)
-            prefix[m] = carry + scan[threadIdx.x] - v;
+            prefix[m] = carry[pair] + scan[pair][threadIdx.x] - v;
         __syncthreads();
-        if (threadIdx.x == 255)
-            carry += scan[255];
+        if (threadIdx.x == 255) {
+            carry[0] += scan[0][255];
+            carry[1] += scan[1][255];
+        }
         __syncthreads();
     }
-    if (threadIdx.x == 0)
-        counts[2] = carry;
+    if (threadIdx.x == 0) {
+        counts[2] = carry[0];
+        counts[3] = carry[1];
+    }
 }
 
-// one block per member: list the tiles of an active member of the batched sweep at its prefix
-// offset
+// one block per member: list the tiles of an active one-sweep member (act) or the blocks of an
+// active pair member (items) at its prefix offset
 __global__ void __launch_bounds__(256) kb_scatter(const Member *__restrict__ mem,
                                                   const MemberCtl *__restrict__ ctl,
                                                   const int *__restrict__ prefix,
-                                                  int2 *__restrict__ act)
+                                                  int2 *__restrict__ act, int2 *__restrict__ items)
 {
     const int m = blockIdx.x;
-    if (!ctl[m].active || mem[m].own)           // own members sweep with their own launches
+    if (!ctl[m].active)
         return;
-    const int base = prefix[m], n = mem[m].ntiles;
+    const bool pair = mem[m].own != 0;
+    const int base = prefix[m], n = pair ? mem[m].nb2 : mem[m].ntiles;
+    int2 *dst = pair ? items : act;
     for (int i = threadIdx.x; i < n; i += 256)
-        act[base + i] = make_int2(m, i);
+        dst[base + i] = make_int2(m, i);
 }
 
 __global__ void __launch_bounds__(kBlock) kb_rebase_mid(const Member *__restrict__ mem,
@@ -331,11 +327,17 @@ struct lbm2p_batch {
     int *h_caps = nullptr;               // pinned
     double *h_tols = nullptr;            // pinned
     int *d_active = nullptr;             // [0] active members, [1] members to rebase,
-                                         // [2] tiles of the active members
-    int *d_prefix = nullptr;             // first compacted tile of each active member
+                                         // [2] tiles of the active one-sweep members,
+                                         // [3] blocks of the active pair members
+    int *d_prefix = nullptr;             // first compacted tile (block) of each active member
     int2 *d_act = nullptr;               // compacted (member, tile) list
     double *d_partials = nullptr;
-    std::vector<lbm2p *> own_h;          // the handles of the own members (index = member)
+    int npair = 0, pair_total = 0;       // pair members, their blocks
+    int pair_grid = 0;                   // blocks of a k_pair_batch launch
+    PressureArgs *d_pa2 = nullptr;       // [2 count] argument blocks of the pair launches
+    int *d_h2 = nullptr, *d_pb0 = nullptr;   // [count] block height, first partial
+    int2 *d_items = nullptr;             // compacted (member, block) list of the pair members
+    double *d_pparts = nullptr;          // [4 pair_total] their residual partials
     cudaGraph_t graph[2] = {};
     cudaGraphExec_t exec[2] = {};
     int gstep = 0;                       // parity of the steps run by the batch
@@ -382,6 +384,11 @@ void batch_free(lbm2p_batch *b)
     cudaFree(b->d_active);
     cudaFree(b->d_prefix);
     cudaFree(b->d_act);
+    cudaFree(b->d_pa2);
+    cudaFree(b->d_h2);
+    cudaFree(b->d_pb0);
+    cudaFree(b->d_items);
+    cudaFree(b->d_pparts);
     cudaFree(b->d_partials);
     if (b->h_ctl)
         cudaFreeHost(b->h_ctl);
@@ -447,16 +454,15 @@ lbm2p_status build_graph(lbm2p_batch *b, int q)
     }
     cudaGraphConditionalHandle hd, hnone{};
     BTRY(b, cudaGraphConditionalHandleCreate(&hd, G, 1, cudaGraphCondAssignDefault));
-    bool any_own = false;
-    for (int m = 0; m < count; ++m)
-        any_own = any_own || b->own_h[(size_t)m] != nullptr;
+    int2 *items = b->d_items;
     {
         void *args[] = {(void *)&mem, (void *)&cctl, (void *)&count, (void *)&prefix,
                         (void *)&act, (void *)&hnone, (void *)&hnone};
         BTRY(b, add_k(&npre, G, &nreset, (void *)kb_prefix<false>, 1, 256, args));
     }
     {
-        void *args[] = {(void *)&mem, (void *)&cctl, (void *)&cprefix, (void *)&actl};
+        void *args[] = {(void *)&mem, (void *)&cctl, (void *)&cprefix, (void *)&actl,
+                        (void *)&items};
         BTRY(b, add_k(&nsc, G, &npre, (void *)kb_scatter, count, 256, args));
     }
     cudaGraphNodeParams cp{};
@@ -477,55 +483,19 @@ lbm2p_status build_graph(lbm2p_batch *b, int q)
                       check ? b->grid_check : b->grid, kBlock, args));
         prev = n;
     }
-    // the own members' two-sweep launches, one chain per member beside the batched sweeps;
-    // each launch reads the member's active flag and does nothing once it has converged
-    // one IF node around all own members' launches, set at the top of the body by kb_own_if,
-    // so that they stop launching once every own member has converged
+    // the pair members: check_every / 2 launches of k_pair_batch (two sweeps each, over the
+    // blocks of every pair member still iterating), a chain beside the one-sweep chain
     std::vector<cudaGraphNode_t> ends{prev};
-    cudaGraph_t og = nullptr;
-    if (any_own) {
-        cudaGraphConditionalHandle hown;
-        BTRY(b, cudaGraphConditionalHandleCreate(&hown, bg, 0, 0));
-        cudaGraphNode_t nset, nown;
-        {
-            void *args[] = {(void *)&mem, (void *)&cctl, (void *)&count, (void *)&hown};
-            BTRY(b, add_k(&nset, bg, nullptr, (void *)kb_own_if, 1, 256, args));
-        }
-        cudaGraphNodeParams op{};
-        op.type = cudaGraphNodeTypeConditional;
-        op.conditional.handle = hown;
-        op.conditional.type = cudaGraphCondTypeIf;
-        op.conditional.size = 1;
-        BTRY(b, cudaGraphAddNode(&nown, bg, &nset, nullptr, 1, &op));
-        og = op.conditional.phGraph_out[0];
-        ends.push_back(nown);
-    }
-    for (int m = 0; m < count; ++m) {
-        lbm2p *h = b->own_h[(size_t)m];
-        if (!h)
-            continue;
-        cudaGraph_t ig = og;
-        const int A = h->cur_f, B = lbm2p_internal::fnext(A, 1);
+    if (b->npair > 0) {
         cudaGraphNode_t p2 = nullptr;
-        int src = A;
-        for (int kk = 2; kk <= body; kk += 2) {
-            PressureArgs a = lbm2p_internal::pressure_args(h, src, src == A ? B : A, false);
-            a.live = &b->d_ctl[m].active;
+        for (int kk = 0; kk < body / 2; ++kk) {
             cudaGraphNode_t n;
-            const bool chk = kk == body;
-            if (h->tb_kind == 2)
-                BTRY(b, lbm2p_launch::node_pressure_pair_direct(&n, ig, p2 ? &p2 : nullptr, a, chk,
-                                                                h->tb_W / 30, h->tb_H, h->tb_grid));
-            else if (h->tb_kind == 1)
-                BTRY(b, lbm2p_launch::node_pressure_rows2(&n, ig, p2 ? &p2 : nullptr, a, chk,
-                                                          h->tb_W / 30, h->tb_slots, h->tb_H,
-                                                          h->tb_grid));
-            else
-                BTRY(b, lbm2p_launch::node_pressure_fused(&n, ig, p2 ? &p2 : nullptr, a, 2, h->tb_W,
-                                                          h->tb_H, chk, h->tb_grid));
+            BTRY(b, lbm2p_launch::node_pair_batch(&n, bg, p2 ? &p2 : nullptr, b->d_pa2, b->d_h2,
+                                                  b->d_pb0, b->d_items, b->d_active + 3, kk & 1,
+                                                  kk == body / 2 - 1, b->d_pparts, b->pair_grid));
             p2 = n;
-            src = src == A ? B : A;
         }
+        ends.push_back(p2);
     }
     cudaGraphNode_t nf, nc, nsc2, nif, nrm;
     {
@@ -545,7 +515,8 @@ lbm2p_status build_graph(lbm2p_batch *b, int q)
         BTRY(b, add_k(&nc, bg, &nf, (void *)kb_prefix<true>, 1, 256, args));
     }
     {
-        void *args[] = {(void *)&mem, (void *)&cctl, (void *)&cprefix, (void *)&actl};
+        void *args[] = {(void *)&mem, (void *)&cctl, (void *)&cprefix, (void *)&actl,
+                        (void *)&items};
         BTRY(b, add_k(&nsc2, bg, &nc, (void *)kb_scatter, count, 256, args));
     }
     cudaGraphNodeParams ip{};
@@ -613,6 +584,8 @@ lbm2p_status lbm2p_batch_create(lbm2p_batch **out, lbm2p *const *members, int co
     b->body = m0->p.check_every;
     b->stream = m0->stream;
     std::vector<Member> hm((size_t)count);
+    std::vector<PressureArgs> pa2(2 * (size_t)count);
+    std::vector<int> h2v((size_t)count), pb0v((size_t)count);
     std::vector<int> tile_member;
     int total = 0;
     for (int i = 0; i < count; ++i) {
@@ -649,13 +622,29 @@ lbm2p_status lbm2p_batch_create(lbm2p_batch **out, lbm2p *const *members, int co
         M.ntiles = M.seg_x * ((h->ny + M.rpt - 1) / M.rpt);
         total += M.ntiles;
         tile_member.insert(tile_member.end(), (size_t)M.ntiles, i);
-        // large members keep the two-sweep launches their handle chose (a body of check_every
-        // sweeps is then check_every / 2 launches, an even number, ending in buffer A)
-        M.own = (!h->fp16 && h->tb_T_graph == 2 && h->nnodes >= 512LL * 512 &&
-                 b->body % 4 == 0 && h->tb_grid > 0 && h->partials) ? 1 : 0;
-        M.pparts = M.own ? h->partials : nullptr;
-        M.nparts = M.own ? h->tb_grid : M.ntiles;
-        b->own_h.push_back(M.own ? h : nullptr);
+        // members of 512^2 nodes and more with walls on every side sweep two at a time
+        // (k_pair_batch; a body of check_every sweeps is then check_every / 2 launches, an
+        // even number, ending in buffer A), in blocks of the height their handle's tuning
+        // chose for the direct-load form, else 4 rows
+        bool walls = true;
+        for (int sd = 0; sd < 4; ++sd)
+            walls = walls && h->p.bc[sd] != LBM2P_BC_PERIODIC;
+        M.own = (!h->fp16 && walls && h->nnodes >= 512LL * 512 && b->body % 4 == 0) ? 1 : 0;
+        M.h2 = M.nb2 = M.pb0 = 0;
+        if (M.own) {
+            M.h2 = (h->tb_T > 1 && h->tb_kind == 2 && h->tb_W == 120) ? h->tb_H : 4;
+            M.h2 = M.h2 < h->ny ? M.h2 : h->ny;
+            M.nb2 = (int)lbm2p_launch::pair_direct_grid(4, M.h2, h->nx, h->ny);
+            M.pb0 = b->pair_total;
+            b->pair_total += M.nb2;
+            ++b->npair;
+        }
+        pa2[2 * (size_t)i] = M.pa[0];
+        pa2[2 * (size_t)i + 1] = M.pa[1];
+        h2v[(size_t)i] = M.h2;
+        pb0v[(size_t)i] = M.pb0;
+        M.pparts = nullptr;                    // set once the partials are allocated
+        M.nparts = M.own ? M.nb2 : M.ntiles;
         b->pf.push_back(h->cur_f);
         b->pg0.push_back(h->cur_g);
         b->pr.push_back(h->cur_r);
@@ -680,6 +669,8 @@ lbm2p_status lbm2p_batch_create(lbm2p_batch **out, lbm2p *const *members, int co
         const long long g2 = (long long)sms * (perc > 0 ? perc : 1);
         b->grid = (int)(g1 < total ? g1 : total);
         b->grid_check = (int)(g2 < total ? g2 : total);
+        const long long g3 = (long long)sms * lbm2p_launch::pair_batch_blocks_per_sm();
+        b->pair_grid = (int)(g3 < b->pair_total ? g3 : (b->pair_total > 0 ? b->pair_total : 1));
         ok(cudaMalloc(&b->d_mem, sizeof(Member) * (size_t)count), "cudaMalloc") &&
             ok(cudaMalloc(&b->d_tile_member, sizeof(int) * (size_t)total), "cudaMalloc") &&
             ok(cudaMalloc(&b->d_ctl, sizeof(MemberCtl) * (size_t)count), "cudaMalloc") &&
@@ -689,6 +680,14 @@ lbm2p_status lbm2p_batch_create(lbm2p_batch **out, lbm2p *const *members, int co
             ok(cudaMalloc(&b->d_prefix, sizeof(int) * (size_t)count), "cudaMalloc") &&
             ok(cudaMalloc(&b->d_act, sizeof(int2) * (size_t)total), "cudaMalloc") &&
             ok(cudaMalloc(&b->d_partials, sizeof(double) * 4 * (size_t)total), "cudaMalloc") &&
+            ok(cudaMalloc(&b->d_pa2, sizeof(PressureArgs) * 2 * (size_t)count), "cudaMalloc") &&
+            ok(cudaMalloc(&b->d_h2, sizeof(int) * (size_t)count), "cudaMalloc") &&
+            ok(cudaMalloc(&b->d_pb0, sizeof(int) * (size_t)count), "cudaMalloc") &&
+            ok(cudaMalloc(&b->d_items, sizeof(int2) * (size_t)(b->pair_total > 0 ? b->pair_total : 1)),
+               "cudaMalloc") &&
+            ok(cudaMalloc(&b->d_pparts,
+                          sizeof(double) * 4 * (size_t)(b->pair_total > 0 ? b->pair_total : 1)),
+               "cudaMalloc") &&
             ok(cudaMallocHost(&b->h_ctl, sizeof(MemberCtl) * (size_t)count), "cudaMallocHost") &&
             ok(cudaMallocHost(&b->h_caps, sizeof(int) * (size_t)count), "cudaMallocHost") &&
             ok(cudaMallocHost(&b->h_tols, sizeof(double) * (size_t)count), "cudaMallocHost") &&
@@ -696,13 +695,21 @@ lbm2p_status lbm2p_batch_create(lbm2p_batch **out, lbm2p *const *members, int co
             ok(cudaEventCreate(&b->ev1), "cudaEventCreate");
     }
     if (st == LBM2P_OK) {
-        // the batched sweep's residual partials: one per tile of each member it sweeps
-        for (int i = 0; i < count; ++i)
-            if (!hm[(size_t)i].own)
-                hm[(size_t)i].pparts = b->d_partials + 4 * (size_t)hm[(size_t)i].tile0;
+        // residual partials: one per tile of each one-sweep member, one per block of each
+        // pair member
+        for (int i = 0; i < count; ++i) {
+            Member &M = hm[(size_t)i];
+            M.pparts = M.own ? b->d_pparts + 4 * (size_t)M.pb0 : b->d_partials + 4 * (size_t)M.tile0;
+        }
         cudaStream_t cs = (cudaStream_t)b->stream;
         ok(cudaMemcpyAsync(b->d_mem, hm.data(), sizeof(Member) * (size_t)count,
                            cudaMemcpyHostToDevice, cs), "cudaMemcpyAsync") &&
+            ok(cudaMemcpyAsync(b->d_pa2, pa2.data(), sizeof(PressureArgs) * 2 * (size_t)count,
+                               cudaMemcpyHostToDevice, cs), "cudaMemcpyAsync") &&
+            ok(cudaMemcpyAsync(b->d_h2, h2v.data(), sizeof(int) * (size_t)count,
+                               cudaMemcpyHostToDevice, cs), "cudaMemcpyAsync") &&
+            ok(cudaMemcpyAsync(b->d_pb0, pb0v.data(), sizeof(int) * (size_t)count,
+                               cudaMemcpyHostToDevice, cs), "cudaMemcpyAsync") &&
             ok(cudaMemcpyAsync(b->d_tile_member, tile_member.data(), sizeof(int) * (size_t)total,
                                cudaMemcpyHostToDevice, cs), "cudaMemcpyAsync") &&
             ok(cudaMemsetAsync(b->d_ctl, 0, sizeof(MemberCtl) * (size_t)count, cs), "cudaMemsetAsync") &&
@@ -794,16 +801,8 @@ lbm2p_status lbm2p_batch_step(lbm2p_batch *b, int nsteps, const int *replay,
         const int passes = kmax > 0 ? kmax / b->body : 1;
         const int every = b->body * ((1024 + b->body - 1) / b->body);
         b->launches += 6 + (long long)passes * (b->body + 3) + (kmax > 0 ? (kmax - 1) / every : 0);
-        // own members: kb_own_if every pass, and body / 2 launches each in every pass while
-        // one of them is still active
-        int kown = 0, nown = 0;
-        for (int m = 0; m < b->count; ++m)
-            if (b->own_h[(size_t)m]) {
-                ++nown;
-                kown = b->h_ctl[m].k > kown ? b->h_ctl[m].k : kown;
-            }
-        if (nown > 0)
-            b->launches += passes + (long long)(kown / b->body) * (b->body / 2) * nown;
+        if (b->npair > 0)                      // the pair members' body / 2 launches a pass
+            b->launches += (long long)passes * (b->body / 2);
         if (worst == LBM2P_ENONFINITE)
             return bfail(b, worst, "a member's pressure residual is not finite (step %d)", s);
     }

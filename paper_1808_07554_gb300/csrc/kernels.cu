@@ -307,8 +307,6 @@ struct TBRow {
 template <int T, bool CHECK>
 __global__ void __launch_bounds__(128) k_pressure_tb(const __grid_constant__ PressureArgs a, int H)
 {
-    if (a.live && *a.live == 0)                       // a converged batch member
-        return;
     extern __shared__ float sm[];
     const Geom &g = a.g;
     const int Wt = blockDim.x;

@@ -101,10 +101,6 @@ struct PressureArgs {
     const float *Pb[4];      // Dirichlet traces (device FP32) or nullptr
     Geom g;
     Wells w;
-    // a batch member's "still sub-iterating" flag, or nullptr: the two-sweep kernels do
-    // nothing when it is 0 (the launch stays in the batch's loop body after the member met
-    // its tolerance)
-    const int *live;
 };
 
 struct RefreshArgs {        // stream g, S^n, 1/tau_f (and the warm start of the next solve)
@@ -284,6 +280,14 @@ cudaError_t node_pressure_rows2(cudaGraphNode_t *n, cudaGraph_t g, const cudaGra
 // two sweeps per launch with direct loads (sweep_rows.cu), lattices without periodic sides:
 // cw warps of 30 owned columns (4 or 8), H rows per block; grid = pair_direct_grid(...)
 long long pair_direct_grid(int cw, int H, int nx, int ny);
+// the direct-load two-sweep kernel (4 warps) over several lattices: item t of items[0 ..
+// *nitems) = (member m, block b of m's lattice, strips of 120 columns x H[m] rows), argument
+// block pa[2 m + parity]; CHECK: residual sums of the item at parts + 4 (pb0[m] + b)
+int pair_batch_blocks_per_sm();
+cudaError_t node_pair_batch(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
+                            const PressureArgs *pa, const int *H, const int *pb0,
+                            const int2 *items, const int *nitems, int parity, bool check,
+                            double *parts, int grid);
 void pressure_sweeps_pair_direct(const PressureArgs &a, bool check, int cw, int H, int grid,
                                  void *stream);
 cudaError_t node_pressure_pair_direct(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,

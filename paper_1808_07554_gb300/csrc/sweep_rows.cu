@@ -427,8 +427,6 @@ template <bool CHECK, int CW, int S, int MINB>
 __global__ void __launch_bounds__(32 * (CW + 1), MINB) k_pressure_rows2(const __grid_constant__ PressureArgs a,
                                                                   int H)
 {
-    if (a.live && *a.live == 0)                       // a converged batch member
-        return;
     constexpr int W = 30 * CW;
     constexpr int RW = W + 2 * kRowsHalo;          // floats per staged plane row
     const int npl = a.Fp ? 11 : 10;
@@ -758,19 +756,19 @@ __global__ void __launch_bounds__(32 * (CW + 1), MINB) k_pressure_rows2(const __
 // counts (64 instead of 48 for the 8-warp plain launch, 72 instead of 64 for the 4-warp
 // checking one), and these counts set the blocks resident per SM.
 // ---------------------------------------------------------------------------------------
+// Block bidx of the lattice of `a` (strips of W = 30 CW columns by H rows); CHECK: the block's
+// four residual sums go to part[0 .. 3].  Every thread of the block calls it.
 template <bool CHECK, int CW>
-__global__ void __launch_bounds__(32 * CW) k_pressure_pair_direct(const __grid_constant__ PressureArgs a,
-                                                                 int H)
+__device__ __forceinline__ void pair_direct_block(const PressureArgs &a, int H, int bidx,
+                                                  double *part)
 {
-    if (a.live && *a.live == 0)                       // a converged batch member
-        return;
     constexpr int W = 30 * CW;
     __shared__ double red[CW][4];
     const Geom &g = a.g;
     const int p = g.pitch;
     const int strips = (g.nx + W - 1) / W;
-    const int x0 = (blockIdx.x % strips) * W;
-    const int y0 = (blockIdx.x / strips) * H;
+    const int x0 = (bidx % strips) * W;
+    const int y0 = (bidx / strips) * H;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float shift = CHECK ? a.shift[0] : 0.0f;
     const float dshift = CHECK ? a.shift[1] : 0.0f;
@@ -887,8 +885,37 @@ __global__ void __launch_bounds__(32 * CW) k_pressure_pair_direct(const __grid_c
             double sum = 0.0;
             for (int w = 0; w < CW; ++w)
                 sum += red[w][threadIdx.x];
-            a.partials[4 * blockIdx.x + threadIdx.x] = sum;
+            part[threadIdx.x] = sum;
         }
+    }
+}
+
+template <bool CHECK, int CW>
+__global__ void __launch_bounds__(32 * CW) k_pressure_pair_direct(const __grid_constant__ PressureArgs a,
+                                                                 int H)
+{
+    pair_direct_block<CHECK, CW>(a, H, blockIdx.x, CHECK ? a.partials + 4 * blockIdx.x : nullptr);
+}
+
+// Two sweeps with direct loads over several lattices in one launch (the batch's members of
+// 512^2 nodes and more): item t = (member m, block b) runs block b of member m's lattice with
+// the argument block pa[2 m + parity] and H[m] rows per block; CHECK: its residual sums go to
+// parts[4 (pb0[m] + b) ..].  The list holds the blocks of the members still iterating.
+template <bool CHECK>
+__global__ void __launch_bounds__(128) k_pair_batch(const PressureArgs *__restrict__ pa,
+                                                    const int *__restrict__ H,
+                                                    const int *__restrict__ pb0,
+                                                    const int2 *__restrict__ items,
+                                                    const int *__restrict__ nitems, int parity,
+                                                    double *__restrict__ parts)
+{
+    const int n = *nitems;
+    for (int t = blockIdx.x; t < n; t += gridDim.x) {
+        const int2 e = items[t];
+        pair_direct_block<CHECK, 4>(pa[2 * e.x + parity], H[e.x], e.y,
+                                    CHECK ? parts + 4 * ((size_t)pb0[e.x] + e.y) : nullptr);
+        if (CHECK)
+            __syncthreads();                           // the reduction array is reused
     }
 }
 
@@ -1118,6 +1145,32 @@ cudaError_t node_pressure_pair_direct(cudaGraphNode_t *n, cudaGraph_t g, const c
     prm.blockDim = dim3((unsigned)(32 * cw));
     prm.sharedMemBytes = 0;
     void *args[] = {(void *)&a, (void *)&H};
+    prm.kernelParams = args;
+    prm.extra = nullptr;
+    return cudaGraphAddKernelNode(n, g, dep, dep ? 1 : 0, &prm);
+}
+
+int pair_batch_blocks_per_sm()
+{
+    int b1 = 0, b2 = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, lbm2p_dev::k_pair_batch<false>, 128, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, lbm2p_dev::k_pair_batch<true>, 128, 0);
+    const int b = b1 < b2 ? b1 : b2;
+    return b > 0 ? b : 1;
+}
+
+cudaError_t node_pair_batch(cudaGraphNode_t *n, cudaGraph_t g, const cudaGraphNode_t *dep,
+                            const PressureArgs *pa, const int *H, const int *pb0,
+                            const int2 *items, const int *nitems, int parity, bool check,
+                            double *parts, int grid)
+{
+    cudaKernelNodeParams prm{};
+    prm.func = check ? (void *)lbm2p_dev::k_pair_batch<true> : (void *)lbm2p_dev::k_pair_batch<false>;
+    prm.gridDim = dim3((unsigned)grid);
+    prm.blockDim = dim3(128u);
+    prm.sharedMemBytes = 0;
+    void *args[] = {(void *)&pa, (void *)&H, (void *)&pb0, (void *)&items, (void *)&nitems,
+                    (void *)&parity, (void *)&parts};
     prm.kernelParams = args;
     prm.extra = nullptr;
     return cudaGraphAddKernelNode(n, g, dep, dep ? 1 : 0, &prm);
