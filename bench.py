@@ -83,7 +83,13 @@ KERNEL_SOURCES = {
 # width); each entry carries the hash of the kernel sources it was taken from and the
 # summary under profiles/ that holds the command.  A capture whose hash differs from the
 # sources being run is stale and is not reported.
-NCU_TRAFFIC_PER_LAUNCH = {}
+NCU_TRAFFIC_PER_LAUNCH = {
+    # k_pressure_rows2<0, 4, 6, 7> (4 consumer warps, 6 slots, 16 rows, seven-block register
+    # cap), mean of 3 launches: 734.4 + 494.7, 738.9 + 495.4, 734.4 + 491.8 MB
+    ("five_spot_4096", "staged_rows", 120): {
+        "bytes": 1229841323, "sources": "a38cf4db413179c4",
+        "profile": "profiles/pressure_sweeps_fused_rows_five_spot_4096.md"},
+}
 FUSED_FORM_NAMES = {1: "stages", 2: "staged_rows", 3: "direct"}
 FUSED_FORM_TEXT = {1: "on shared-memory stages", 2: "on rows staged by bulk copies",
                    3: "with direct loads"}

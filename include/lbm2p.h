@@ -309,9 +309,9 @@ lbm2p_status lbm2p_counters(const lbm2p *h, long long *launches, long long *swee
  * all members, and the sub-iteration continues while any member is still above its
  * tolerance (members that met theirs stop sweeping).  The paper solves one realisation at
  * a time; this is the same per-member computation scheduled so that small lattices fill
- * the GPU together: they share one sweep kernel over a tile list, while a member of 512^2
- * nodes or more whose handle runs two sweeps per launch keeps its own launches, in a branch
- * of the loop body that runs beside the shared sweep while that member is still iterating.
+ * the GPU together: they share one sweep kernel over a tile list, while the members of 512^2
+ * nodes or more on lattices with walls on every side share a two-sweeps-per-launch kernel
+ * over a list of their blocks, beside the shared sweep (when check_every is a multiple of 4).
  *
  * members: count handles made by lbm2p_create on the current device, all on one stream,
  * all with one even check_every that divides each member's max_sub_iters; each handle
