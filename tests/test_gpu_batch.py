@@ -154,6 +154,38 @@ def test_free_running_matches_single_handles():
                     inb[i].set_state(alone[i].get_state())
 
 
+def test_free_running_with_a_two_sweep_member():
+    """A 512^2 member (swept two sweeps per launch by the batch's direct-load kernel over its
+    blocks) beside a small one, free-running: each stops on its own residual, with the counts,
+    statuses and residuals of its handle stepped alone (up to one body: the residual's partial
+    sums are grouped by the batch's blocks), and equal counts give identical states."""
+    pkg = _pkg()
+    probs = [W.quarter_five_spot(512, seed=21, sigma=1.0, corr_len=16.0),
+             W.quarter_five_spot(48, seed=22, sigma=1.0, corr_len=8)]
+    cap = 40_000
+    alone = [_solver(p, max_sub_iters=cap, init_replay=400) for p in probs]
+    inb = [_solver(p, max_sub_iters=cap, init_replay=400) for p in probs]
+    with pkg.Batch(inb) as batch:
+        for _ in range(3):
+            ka, ra, sa = [], [], []
+            for a in alone:
+                st, s = a.step(1)                   # a cap reached is a status, not an error
+                ka.append(s[0].sub_iters)
+                ra.append(s[0].residual)
+                sa.append(s[0].status)
+            st, stats = batch.step(1)
+            for i in range(len(probs)):
+                kb = stats[0][i].sub_iters
+                assert abs(kb - ka[i]) <= CHECK, (i, ka, kb)
+                assert stats[0][i].residual <= 1e-8 or kb == cap
+                if kb == ka[i]:
+                    assert stats[0][i].status == sa[i]
+                    assert stats[0][i].residual == pytest.approx(ra[i], rel=1e-3)
+                    assert np.array_equal(alone[i].get_state(), inb[i].get_state())
+                else:      # counts differ by one body: carry on from identical states
+                    inb[i].set_state(alone[i].get_state())
+
+
 def test_batch_against_oracle():
     """The oracle decides the counts (free-running, FP64); the batch replays them."""
     pkg = _pkg()
