@@ -48,7 +48,7 @@ struct Member {
     // them, residual partials at pb0 in the pair partials) instead of joining the one-sweep
     // batched sweep.  pparts / nparts: where finalize finds the member's residual partials
     // (the pair partials, or the batch's per-tile ones).
-    int own;
+    int pair;                    // 1: a pair member
     int h2, nb2, pb0;
     const double *pparts;
     int nparts;
@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(256) kb_prefix(const Member *__restrict__ mem,
     for (int base = 0; base < count; base += 256) {
         const int m = base + (int)threadIdx.x;
         const bool on = m < count && ctl[m].active;
-        const int pair = on && mem[m].own;
+        const int pair = on && mem[m].pair;
         const int v = on ? (pair ? mem[m].nb2 : mem[m].ntiles) : 0;
         scan[0][threadIdx.x] = pair ? 0 : v;
         scan[1][threadIdx.x] = pair ? v : 0;
@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(256) kb_scatter(const Member *__restrict__ mem
     const int m = blockIdx.x;
     if (!ctl[m].active)
         return;
-    const bool pair = mem[m].own != 0;
+    const bool pair = mem[m].pair != 0;
     const int base = prefix[m], n = pair ? mem[m].nb2 : mem[m].ntiles;
     int2 *dst = pair ? items : act;
     for (int i = threadIdx.x; i < n; i += 256)
@@ -629,9 +629,9 @@ lbm2p_status lbm2p_batch_create(lbm2p_batch **out, lbm2p *const *members, int co
         bool walls = true;
         for (int sd = 0; sd < 4; ++sd)
             walls = walls && h->p.bc[sd] != LBM2P_BC_PERIODIC;
-        M.own = (!h->fp16 && walls && h->nnodes >= 512LL * 512 && b->body % 4 == 0) ? 1 : 0;
+        M.pair = (!h->fp16 && walls && h->nnodes >= 512LL * 512 && b->body % 4 == 0) ? 1 : 0;
         M.h2 = M.nb2 = M.pb0 = 0;
-        if (M.own) {
+        if (M.pair) {
             M.h2 = (h->tb_T > 1 && h->tb_kind == 2 && h->tb_W == 120) ? h->tb_H : 4;
             M.h2 = M.h2 < h->ny ? M.h2 : h->ny;
             M.nb2 = (int)lbm2p_launch::pair_direct_grid(4, M.h2, h->nx, h->ny);
@@ -644,7 +644,7 @@ lbm2p_status lbm2p_batch_create(lbm2p_batch **out, lbm2p *const *members, int co
         h2v[(size_t)i] = M.h2;
         pb0v[(size_t)i] = M.pb0;
         M.pparts = nullptr;                    // set once the partials are allocated
-        M.nparts = M.own ? M.nb2 : M.ntiles;
+        M.nparts = M.pair ? M.nb2 : M.ntiles;
         b->pf.push_back(h->cur_f);
         b->pg0.push_back(h->cur_g);
         b->pr.push_back(h->cur_r);
@@ -699,7 +699,7 @@ lbm2p_status lbm2p_batch_create(lbm2p_batch **out, lbm2p *const *members, int co
         // pair member
         for (int i = 0; i < count; ++i) {
             Member &M = hm[(size_t)i];
-            M.pparts = M.own ? b->d_pparts + 4 * (size_t)M.pb0 : b->d_partials + 4 * (size_t)M.tile0;
+            M.pparts = M.pair ? b->d_pparts + 4 * (size_t)M.pb0 : b->d_partials + 4 * (size_t)M.tile0;
         }
         cudaStream_t cs = (cudaStream_t)b->stream;
         ok(cudaMemcpyAsync(b->d_mem, hm.data(), sizeof(Member) * (size_t)count,
