@@ -729,8 +729,10 @@ def run_batch(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
                      "traffic": None,
-                     "kernel": "whole batched step (kb_sweep dominant): algorithmic bytes of "
-                               "every kernel / step time",
+                     "kernel": "whole batched step (kb_sweep for the small members, "
+                               "k_pair_batch, two sweeps per launch, for those of 512^2 and "
+                               "up): 72 B per node and sweep + the per-step kernels' bytes / "
+                               "step time",
                      "bytes_per_step": step_bytes / args.steps, "peak_kind": peak_kind},
         "e2e": {"value": e2e_all / e2e_max / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": int(8 * nodes.sum())},
