@@ -110,6 +110,15 @@ def kernel_source_hash(form: str) -> str:
     return h.hexdigest()[:16]
 
 
+def captured_traffic(form, src_hash: str):
+    """(DRAM bytes per launch, profile summary) captured by ncu for this launch form, or
+    (None, None) when there is no capture or the kernel sources changed since it was taken."""
+    cap = NCU_TRAFFIC_PER_LAUNCH.get(form)
+    if cap is None or cap["sources"] != src_hash:
+        return None, None
+    return cap["bytes"], cap["profile"]
+
+
 def batch_members(name: str, rank: int = 0):
     """Realisations of a batch workload: sizes drawn uniformly from the workload's list,
     sigma of ln K in [0.5, 2], correlation length in [8, 32] cells, viscosity ratio
@@ -511,8 +520,7 @@ def run_ours(args):
             else (args.workload, "single", sweep_cfg[1]))
     src_form = "two_sweep" if fused > 1 else "single"
     src_hash = kernel_source_hash(src_form)
-    cap = NCU_TRAFFIC_PER_LAUNCH.get(form) if not fp16 else None
-    traffic = cap["bytes"] if cap is not None and cap["sources"] == src_hash else None
+    traffic, traffic_profile = captured_traffic(form, src_hash) if not fp16 else (None, None)
     hist = {}
     for k in ksub:
         hist[str(k)] = hist.get(str(k), 0) + 1
@@ -565,7 +573,7 @@ def run_ours(args):
                      "dram_bytes_moved_model": (None if fp16 else BYTES_MOVED_PER_NODE * nodes),
                      "dram_frac": (traffic / avg_launch_s / 1e9 / peak
                                    if traffic is not None else None),
-                     "traffic_source": (f"ncu capture, {cap['profile']}" if traffic is not None
+                     "traffic_source": (f"ncu capture, {traffic_profile}" if traffic is not None
                                         else "no ncu capture of these kernel sources"),
                      "kernel_sources": src_hash,
                      "peak_kind": peak_kind},
