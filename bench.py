@@ -317,6 +317,28 @@ def cpu_baseline(name: str, reps: int = 3):
             "seconds": sum(t for _, t in runs) + t1}
 
 
+def cpu_full_run(steps: int = 500):
+    """The whole small configuration on the host: the oracle runs the 64 x 64 manufactured
+    problem for `steps` physical steps, every pressure solve to r <= 1e-8, on all host threads
+    and on one (minutes of CPU time: opt-in, not part of the bounded baseline)."""
+    import oracle as O
+    out = {"workload": "manufactured_64", "steps": steps, "cpu_model": cpu_model()}
+    for label, threads in (("all_cores", os.cpu_count() or 1), ("single_thread", 1)):
+        prob = make_problem("manufactured_64")
+        n = O.set_threads(threads)
+        orc = O.Oracle(prob, tol=1e-8)
+        t0 = time.perf_counter()
+        st, k, r = orc.step(steps)
+        dt = time.perf_counter() - t0
+        orc.close()
+        out[label] = {"threads": n, "seconds": round(dt, 2), "status": int(st),
+                      "sweeps": int(np.sum(k)),
+                      "MLUPS": float((np.sum(k) + steps) * prob.nx * prob.ny / dt / 1e6),
+                      "ms_per_step": dt / steps * 1e3}
+    O.set_threads(os.cpu_count() or 1)
+    return out
+
+
 def aggregate(local_vals, dist=None, device="cpu"):
     """Combine per-rank (updates, seconds, e2e_updates, e2e_seconds): work is summed over
     ranks, time is the maximum over ranks (weak scaling, independent realisations)."""
@@ -585,8 +607,16 @@ def run_ours(args):
         "clocks": clk,
     }
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = {k: v for k, v in cpu_baseline(args.workload).items()
-                                if k != "seconds"}
+        cpu = {k: v for k, v in cpu_baseline(args.workload).items() if k != "seconds"}
+        # the oracle's time per step at this run's own sweep counts, from its sampled rate
+        # (extrapolated: the oracle is not run to convergence on the full lattice)
+        upd = float(np.mean((np.asarray(ksub) + 1) * nodes))
+        cpu["ms_per_step_extrapolated"] = upd / (cpu["value"] * 1e6) * 1e3
+        cpu["ms_per_step_extrapolated_single_thread"] = (
+            upd / (cpu["single_thread"]["value"] * 1e6) * 1e3)
+        line["cpu_baseline"] = cpu
+    if args.cpu_full_run and rank == 0:
+        line["cpu_full_run"] = cpu_full_run()
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -771,6 +801,9 @@ def main():
     ap.add_argument("--cold-start", action="store_true",
                     help="start the t = 0 pressure solve from P0 = 0 instead of a coarse solve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-full-run", action="store_true",
+                    help="also run the 64 x 64 manufactured configuration's 500 steps with the "
+                         "oracle on the host (minutes)")
     ap.add_argument("--fuse-sweeps", type=int, default=0, choices=[0, 1, 2, 4],
                     help="pressure sweeps per launch: 0 = autotuned, 1, 2 or 4")
     ap.add_argument("--warm-start", choices=["none", "extrapolate", "learned"], default="none",

@@ -34,3 +34,16 @@ def test_reference_arm_other_ranks_are_silent():
     r = _run({"RANK": "1"})
     assert r.returncode == 0, r.stderr[-2000:]
     assert r.stdout.strip() == ""
+
+
+def test_cpu_full_run_reports_both_legs():
+    """The opt-in full run of the small configuration (here 3 steps instead of 500): both
+    thread counts, converged statuses, sweep counts and rates."""
+    sys.path.insert(0, ROOT)
+    import bench
+    out = bench.cpu_full_run(steps=3)
+    assert out["workload"] == "manufactured_64" and out["steps"] == 3
+    for leg in ("all_cores", "single_thread"):
+        r = out[leg]
+        assert r["status"] == 0 and r["sweeps"] > 0 and r["MLUPS"] > 0 and r["seconds"] > 0
+    assert out["single_thread"]["threads"] == 1
