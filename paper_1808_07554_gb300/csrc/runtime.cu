@@ -2055,7 +2055,10 @@ lbm2p_status lbm2p_set_fused_shape(lbm2p *h, int form, int warps, int slots, int
     for (int sd = 0; sd < 4; ++sd)
         if (h->p.bc[sd] == LBM2P_BC_PERIODIC)
             return fail(h, LBM2P_EINVAL, "the two-sweep row-walking kernels need walls on every side");
-    // rows per block: a size the create-time tuning tries (clamped to ny as it is there)
+    // rows per block: a size the create-time tuning tries, clamped to ny as it is there (so a
+    // height above ny means ny)
+    if (rows > h->ny)
+        rows = h->ny;
     auto rows_ok = [&](std::initializer_list<int> tried) {
         for (int H : tried)
             if (rows == (H < h->ny ? H : h->ny))
